@@ -1,0 +1,324 @@
+"""Multiscale multigrid (MMG) preconditioner, plain FP64 (oracle, test only).
+
+Follows Sec. 3 of the paper step by step:
+
+* Grid hierarchy (Sec. 3, nested grids K^(0) ⊃ K^(1) ⊃ ...): level 1 cells are
+  blocks of b^3 fine elements; level l >= 2 cells are groups of g^3 level-(l-1)
+  cells.  Fine *nodes* are partitioned among level-1 blocks by
+  block(i) = min(i // b, N/b - 1) per axis (the last block of an axis also
+  takes the closing node plane); Dirichlet nodes belong to no block.
+* Coarse spectral problem, Eq. (8): on each block B, the Neumann form over the
+  faces/couplings internal to B against the kappa-weighted diagonal mass.
+  Algebraically: Ã_B = A_BB - diag(A_BB 1) (couplings leaving B and to
+  Dirichlet nodes removed, so constants are in the null space) and
+  M_B = diag(m_i), m_i = sum_{e ∋ i} kappa_e |e| / 8.  The L_1 eigenvectors of
+  smallest eigenvalue, normalised to Phi^T M Phi = I, are the rows of R_c.
+* Coarse-coarse spectral problem, Eq. (9): on each group G, the same Neumann
+  form (internal to G) restricted to the span of the previous level's basis
+  functions supported in G.  With the M-normalised basis the right-hand side
+  is the identity (the "mass trick" after Eq. (9)), so it is a standard
+  symmetric eigenproblem.  Rows of R_cc R_c are the composite eigenfunctions.
+  Levels beyond the paper's three grids repeat this construction.
+* Galerkin coarse operators A_c = R_c A R_c^T, A_cc = R_cc A_c R_cc^T (Sec. 3).
+* Smoothed V-cycle, Algorithm 1 (generalised to any number of levels, with
+  the coarsest "correction" read as a solve with A_cc, i.e. A_cc^{-1} r_cc).
+  Fine smoother: nu damped-Jacobi sweeps; coarse smoother: l1-block-Jacobi
+  over each cell's L x L block (the paper's block-Jacobi, Sec. 4); both are
+  symmetric, so S^{-T} = S^{-1}.  Coarsest: dense Cholesky (the paper uses a
+  sparse LU; A_cc is SPD so the solves agree).
+
+Parity pins (tests/test_oracle_mmg.py): two-level exactness with a complete
+local basis, M-orthonormality, eigen-residuals, zero row sums / SPSD of the
+local Neumann matrices, V-cycle symmetry and positivity, agreement of the
+algorithmic V-cycle with its closed product form on small grids, and the
+Galerkin-orthogonality invariant of the coarse initial guess.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+import scipy.linalg as sla
+import scipy.sparse as sp
+
+
+@dataclass
+class MMGOptions:
+    block: int = 4                      # b: block edge in fine elements
+    nvec: tuple = (4, 17)               # L_1, L_2, ... (one per coarse level)
+    group: tuple = (2,)                 # g_2, g_3, ... (one per level >= 2)
+    nu_fine: int = 2
+    nu_coarse: int = 1
+    omega: float = 2.0 / 3.0
+
+    def __post_init__(self):
+        self.nvec = tuple(int(v) for v in self.nvec)
+        self.group = tuple(int(v) for v in self.group)
+        if len(self.group) != len(self.nvec) - 1:
+            raise ValueError("need one group size per level >= 2")
+
+
+def default_options(N: int) -> MMGOptions:
+    """Hierarchy used for an N^3 grid: b = 4, L_1 = 4, then groups of 2^3
+    cells down to a 4^3-cell coarsest level with L = 17 (1,088 unknowns);
+    the second level keeps L = 8 when the hierarchy has more than three grids
+    and L = 17 from the third level on."""
+    nb = N // 4
+    levels = []
+    m = nb
+    while m > 4:
+        m //= 2
+        levels.append(m)
+    if not levels:
+        return MMGOptions(block=4, nvec=(4,), group=())
+    nvec = [4]
+    for i, _ in enumerate(levels):
+        nvec.append(8 if (i == 0 and len(levels) > 1) else 17)
+    return MMGOptions(block=4, nvec=tuple(nvec), group=(2,) * len(levels))
+
+
+@dataclass
+class Level:
+    shape: tuple                      # cells per axis at this level
+    L: int                            # vectors per cell
+    P: sp.csr_matrix = None           # prolongation from this level to the previous one
+    A: sp.csr_matrix = None           # Galerkin operator at this level
+    active: np.ndarray = None         # per-dof flag (False: zero basis vector)
+    smoother: list = field(default_factory=list)  # per-cell inverse of the l1 block
+    eigvals: list = field(default_factory=list)
+
+
+def node_blocks(grid, b, mask):
+    """Level-1 cell (block) id of every fine node, -1 for Dirichlet nodes."""
+    Nx, Ny, Nz = grid
+    if Nx % b or Ny % b or Nz % b:
+        raise ValueError("grid must be a multiple of the block size")
+    nbx, nby, nbz = Nx // b, Ny // b, Nz // b
+    bx = np.minimum(np.arange(Nx + 1) // b, nbx - 1)
+    by = np.minimum(np.arange(Ny + 1) // b, nby - 1)
+    bz = np.minimum(np.arange(Nz + 1) // b, nbz - 1)
+    BZ, BY, BX = np.meshgrid(bz, by, bx, indexing="ij")
+    blk = (BX + nbx * (BY + nby * BZ)).reshape(-1)
+    blk = np.where(np.asarray(mask).astype(bool), -1, blk)
+    return blk, (nbx, nby, nbz)
+
+
+def _sign_fix(v):
+    """Make the entry of largest magnitude (lowest index on ties) positive."""
+    k = int(np.argmax(np.abs(v)))
+    return -v if v[k] < 0 else v
+
+
+def _mgs(V, W=None):
+    """Modified Gram-Schmidt of the columns of V in the inner product
+    <a,b> = a^T diag(W) b (Euclidean if W is None), FP64."""
+    V = V.copy()
+    w = np.ones(V.shape[0]) if W is None else W
+    for j in range(V.shape[1]):
+        for i in range(j):
+            V[:, j] -= (V[:, i] * w) @ V[:, j] * V[:, i]
+        nrm = np.sqrt((V[:, j] * w) @ V[:, j])
+        V[:, j] /= nrm
+    return V
+
+
+def level1_basis(prob, opts: MMGOptions):
+    """Eq. (8) on every block: returns (P1 (n0 x n1), active, eigvals, blk)."""
+    A = prob["A"].tocsr()
+    mass = prob["mass"]
+    blk, shape = node_blocks(prob["grid"], opts.block, prob["mask"])
+    nblk = shape[0] * shape[1] * shape[2]
+    L = opts.nvec[0]
+    order = np.argsort(blk, kind="stable")
+    counts = np.bincount(blk[blk >= 0], minlength=nblk)
+    starts = np.concatenate([[0], np.cumsum(counts)])
+    first_free = int(np.sum(blk < 0))
+    rows, cols, vals = [], [], []
+    active = np.zeros(nblk * L, dtype=bool)
+    eigs = []
+    for c in range(nblk):
+        idx = order[first_free + starts[c]: first_free + starts[c + 1]]
+        n = idx.size
+        if n == 0:
+            eigs.append(np.zeros(0))
+            continue
+        ABB = A[idx][:, idx].toarray()
+        At = ABB - np.diag(ABB.sum(axis=1))          # internal Neumann form
+        m = mass[idx]
+        s = 1.0 / np.sqrt(m)
+        C = At * s[:, None] * s[None, :]
+        w, V = np.linalg.eigh(C)
+        k = min(L, n)
+        Phi = V[:, :k] * s[:, None]
+        Phi = _mgs(Phi, m)                           # Phi^T M Phi = I
+        for j in range(k):
+            phi = _sign_fix(Phi[:, j])
+            rows.append(idx)
+            cols.append(np.full(n, c * L + j))
+            vals.append(phi)
+            active[c * L + j] = True
+        eigs.append(w[:k])
+    n0 = A.shape[0]
+    P1 = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                       shape=(n0, nblk * L))
+    return P1, active, eigs, blk, shape
+
+
+def _galerkin(A, P, active):
+    Ac = (P.T @ A @ P).tocsr()
+    Ac = Ac.tolil()
+    for d in np.flatnonzero(~active):
+        Ac[d, d] = 1.0
+    return Ac.tocsr()
+
+
+def coarse_level_basis(prob, Pcomp, fine_cell, prev_shape, prev_L, prev_active,
+                       g, L):
+    """Eq. (9) on every group of g^3 previous-level cells.
+
+    fine_cell: previous-level cell id of each fine node (-1 for Dirichlet).
+    Pcomp: composite prolongation fine <- previous level (n0 x n_prev).
+    Returns (Psi (n_prev x n_new), active_new, eigvals, new fine_cell, shape).
+    """
+    A = prob["A"].tocsr()
+    mx, my, mz = prev_shape
+    if mx % g or my % g or mz % g:
+        raise ValueError("cell counts must be multiples of the group size")
+    sx, sy, sz = mx // g, my // g, mz // g
+    ngrp = sx * sy * sz
+    cx = np.arange(mx * my * mz) % mx
+    cy = (np.arange(mx * my * mz) // mx) % my
+    cz = np.arange(mx * my * mz) // (mx * my)
+    cell_group = (cx // g) + sx * ((cy // g) + sy * (cz // g))
+    fine_group = np.where(fine_cell >= 0, cell_group[np.maximum(fine_cell, 0)], -1)
+    Pc = Pcomp.tocsc()
+    rows, cols, vals = [], [], []
+    active = np.zeros(ngrp * L, dtype=bool)
+    eigs = []
+    for G in range(ngrp):
+        cells = np.flatnonzero(cell_group == G)
+        # local order: lx + g*ly + g^2*lz  (cells are already x-fastest sorted)
+        key = (cx[cells] % g) + g * ((cy[cells] % g) + g * (cz[cells] % g))
+        cells = cells[np.argsort(key)]
+        dofs = (cells[:, None] * prev_L + np.arange(prev_L)[None, :]).reshape(-1)
+        act = prev_active[dofs]
+        fine = np.flatnonzero(fine_group == G)
+        PG = Pc[:, dofs].tocsr()[fine].toarray()     # composite basis on G
+        AGG = A[fine][:, fine]
+        NG = AGG - sp.diags(np.asarray(AGG.sum(axis=1)).ravel())  # Neumann form internal to G
+        At = PG.T @ (NG @ PG)
+        ia = np.flatnonzero(act)
+        Ata = At[np.ix_(ia, ia)]
+        Ata = 0.5 * (Ata + Ata.T)
+        w, V = np.linalg.eigh(Ata)
+        k = min(L, ia.size)
+        Vk = _mgs(V[:, :k])
+        for j in range(k):
+            v = _sign_fix(Vk[:, j])
+            rows.append(dofs[ia])
+            cols.append(np.full(ia.size, G * L + j))
+            vals.append(v)
+            active[G * L + j] = True
+        eigs.append(w[:k])
+    n_prev = mx * my * mz * prev_L
+    Psi = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                        shape=(n_prev, ngrp * L))
+    return Psi, active, eigs, fine_group, (sx, sy, sz)
+
+
+def l1_block_inverses(A, shape, L):
+    """Per cell: inverse of (A_cc + diag(sum over off-cell |a_ij|)) (FP64)."""
+    A = A.tocsr()
+    ncell = shape[0] * shape[1] * shape[2]
+    out = []
+    Aabs = abs(A)
+    rowabs = np.asarray(Aabs.sum(axis=1)).ravel()
+    for c in range(ncell):
+        d = np.arange(c * L, (c + 1) * L)
+        D = A[d][:, d].toarray()
+        inside = np.asarray(Aabs[d][:, d].sum(axis=1)).ravel()
+        D = D + np.diag(rowabs[d] - inside)
+        out.append(np.linalg.inv(D))
+    return out
+
+
+class MMG:
+    """The full hierarchy for one problem; ``apply(r)`` is one V-cycle."""
+
+    def __init__(self, prob, opts: MMGOptions | None = None):
+        N = prob["grid"][0]
+        self.opts = opts or default_options(N)
+        self.prob = prob
+        A = prob["A"].tocsr()
+        self.A0 = A
+        self.D0 = A.diagonal().copy()
+        o = self.opts
+        P1, act, eig, fine_cell, shape = level1_basis(prob, o)
+        self.levels = [Level(shape=shape, L=o.nvec[0], P=P1, active=act, eigvals=eig)]
+        self.levels[0].A = _galerkin(A, P1, act)
+        Pcomp = P1
+        for li, (g, L) in enumerate(zip(o.group, o.nvec[1:])):
+            prev = self.levels[-1]
+            Psi, act, eig, fine_cell, shape = coarse_level_basis(
+                prob, Pcomp, fine_cell, prev.shape, prev.L, prev.active, g, L)
+            lev = Level(shape=shape, L=L, P=Psi, active=act, eigvals=eig)
+            lev.A = _galerkin(prev.A, Psi, act)
+            self.levels.append(lev)
+            Pcomp = (Pcomp @ Psi).tocsr()
+        self.Pcomp = Pcomp
+        for lev in self.levels[:-1]:
+            lev.smoother = l1_block_inverses(lev.A, lev.shape, lev.L)
+        Ac = self.levels[-1].A.toarray()
+        self.coarse_chol = sla.cho_factor(Ac, lower=True)
+
+    # -- pieces of Algorithm 1 -------------------------------------------------
+    def coarse_solve(self, r):
+        return sla.cho_solve(self.coarse_chol, r)
+
+    def _smooth(self, l, r, e):
+        """One sweep e <- e + S^{-1}(r - A_l e) on grid l (0 = fine)."""
+        if l == 0:
+            return e + self.opts.omega * (r - self.A0 @ e) / self.D0
+        lev = self.levels[l - 1]
+        res = r - lev.A @ e
+        out = e.copy()
+        L = lev.L
+        for c, Dinv in enumerate(lev.smoother):
+            s = slice(c * L, (c + 1) * L)
+            out[s] += Dinv @ res[s]
+        return out
+
+    def _A(self, l):
+        return self.A0 if l == 0 else self.levels[l - 1].A
+
+    def vcycle(self, r, l=0):
+        """Algorithm 1 on grids l, l+1, ..., coarsest (recursive)."""
+        nlev = len(self.levels)
+        if l == nlev:
+            return self.coarse_solve(r)
+        nu = self.opts.nu_fine if l == 0 else self.opts.nu_coarse
+        A = self._A(l)
+        e = np.zeros_like(r)
+        for _ in range(nu):                       # pre-smoothing (from e = 0)
+            e = self._smooth(l, r, e)
+        P = self.levels[l].P
+        rc = P.T @ (r - A @ e)                    # restriction of the residual
+        ec = self.vcycle(rc, l + 1)
+        e = e + P @ ec                            # prolongation
+        for _ in range(nu):                       # post-smoothing (S^{-T} = S^{-1})
+            e = self._smooth(l, r, e)
+        return e
+
+    __call__ = vcycle
+
+    def coarse_guess(self, b, u_prev=None):
+        """u0 = P A_L^{-1} P^T b (or the same correction of u_prev): the
+        Galerkin coarsest-level solution interpolated to the fine grid."""
+        P = self.Pcomp
+        if u_prev is None:
+            return P @ self.coarse_solve(P.T @ b)
+        return u_prev + P @ self.coarse_solve(P.T @ (b - self.A0 @ u_prev))
+
+    @property
+    def sizes(self):
+        return [self.A0.shape[0]] + [lev.A.shape[0] for lev in self.levels]

@@ -1,0 +1,215 @@
+"""Pins of the oracle's multiscale multigrid (Sec. 3) against facts fixed by
+the method's definition and by linear algebra:
+
+* node partition (each free node in exactly one block);
+* Eq. (8): the internal Neumann matrices annihilate constants and are SPSD;
+  the basis is M-orthonormal, satisfies the generalised eigen-equation, and
+  with L = 1 reduces to the kappa-mass-normalised block indicator;
+* Eq. (9): mass = identity on every group ("mass trick"), orthonormal Psi,
+  the group's constant function stays in the coarse-coarse space;
+* complete local bases make the V-cycle an exact solver (two- and three-grid);
+* the algorithmic V-cycle (Algorithm 1) equals its closed product form built
+  here from dense matrices, is symmetric and positive definite;
+* the coarse initial guess is Galerkin-orthogonal: P^T (b - A u0) = 0;
+* MMG-PCG reproduces a direct solve.
+"""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+
+import workloads as W
+from oracle import fem, krylov, mmg
+
+
+def _prob(N=8, seed=5, kmin=1e-3, density="rand", mask=None):
+    grid = (N, N, N)
+    if density == "rand":
+        x = W.uniform01(seed, N ** 3)
+    elif density == "chan":
+        x = W.channel_tree_density(N, seed, 0.2)
+    else:
+        x = np.full(N ** 3, 0.5)
+    m = W.dirichlet_patch_mask(grid) if mask is None else mask
+    return fem.build_problem(grid, (1.0 / N,) * 3, x, 3.0, kmin, 1.0, m, W.uniform_source(grid))
+
+
+def test_node_partition_is_disjoint_cover():
+    P = _prob(N=8)
+    blk, shape = mmg.node_blocks(P["grid"], 4, P["mask"])
+    assert shape == (2, 2, 2)
+    free = ~P["mask"]
+    assert np.all(blk[free] >= 0) and np.all(blk[~free] == -1)
+    cnt = np.bincount(blk[free], minlength=8)
+    # last block of each axis takes the closing plane: 4 or 5 planes per axis
+    sizes = sorted(set(cnt.tolist()))
+    assert cnt.sum() == free.sum()
+    assert sizes[-1] <= 125 and sizes[0] >= 64 - 9
+
+
+def test_local_neumann_and_mass_normalisation():
+    P = _prob(N=8)
+    o = mmg.MMGOptions(block=4, nvec=(4,), group=())
+    P1, act, eigs, blk, shape = mmg.level1_basis(P, o)
+    A = P["A"].tocsr()
+    m = P["mass"]
+    # sum_i m_i over all nodes = int kappa dV (kappa-weighted lumped mass)
+    assert abs(m.sum() - P["kappa"].sum() / 8 ** 3) < 1e-13
+    P1d = P1.toarray()
+    for c in range(8):
+        idx = np.flatnonzero(blk == c)
+        ABB = A[idx][:, idx].toarray()
+        At = ABB - np.diag(ABB.sum(axis=1))
+        assert np.max(np.abs(At @ np.ones(idx.size))) < 1e-14 * np.abs(At).max()
+        assert np.linalg.eigvalsh(At)[0] > -1e-13 * np.abs(At).max()
+        Phi = P1d[idx][:, c * 4:(c + 1) * 4]
+        G = Phi.T @ (m[idx][:, None] * Phi)
+        np.testing.assert_allclose(G, np.eye(4), atol=1e-13)
+        lam = eigs[c]
+        R = At @ Phi - (m[idx][:, None] * Phi) * lam[None, :]
+        assert np.abs(R).max() <= 1e-10 * np.abs(At).max()
+        assert abs(lam[0]) < 1e-10 * np.abs(At).max() / m[idx].min()
+        # first vector: constant on the block (null space of the Neumann form)
+        ph0 = Phi[:, 0]
+        np.testing.assert_allclose(ph0, ph0.mean(), rtol=1e-8)
+
+
+def test_single_vector_is_normalised_block_indicator():
+    P = _prob(N=8, seed=9)
+    o = mmg.MMGOptions(block=4, nvec=(1,), group=())
+    P1, _, _, blk, _ = mmg.level1_basis(P, o)
+    m = P["mass"]
+    for c in range(8):
+        idx = np.flatnonzero(blk == c)
+        want = 1.0 / np.sqrt(m[idx].sum())
+        np.testing.assert_allclose(P1[idx, c].toarray().ravel(), want, rtol=1e-12)
+
+
+def test_coarse_coarse_mass_is_identity_and_constants_preserved():
+    P = _prob(N=16, seed=4)
+    o = mmg.MMGOptions(block=4, nvec=(4, 8), group=(2,))
+    H = mmg.MMG(P, o)
+    Pc = H.Pcomp.toarray()                        # fine <- level 2
+    G = Pc.T @ (P["mass"][:, None] * Pc)
+    np.testing.assert_allclose(G, np.eye(G.shape[0]), atol=1e-12)
+    Psi = H.levels[1].P.toarray()
+    np.testing.assert_allclose(Psi.T @ Psi, np.eye(Psi.shape[1]), atol=1e-12)
+    # the indicator of every group (on free nodes) lies in range(Pc)
+    blk, _ = mmg.node_blocks(P["grid"], 4, P["mask"])
+    bx = blk % 4
+    by = (blk // 4) % 4
+    bz = blk // 16
+    grp = (bx // 2) + 2 * ((by // 2) + 2 * (bz // 2))
+    for g in range(8):
+        ind = ((grp == g) & (blk >= 0)).astype(float)
+        coef = np.linalg.lstsq(Pc, ind, rcond=None)[0]
+        assert np.linalg.norm(Pc @ coef - ind) < 1e-9 * np.linalg.norm(ind)
+
+
+def _free_random(P, seed):
+    r = W.uniform01(seed, P["A"].shape[0]) - 0.5
+    r[P["mask"]] = 0.0
+    return r
+
+
+def test_complete_local_basis_gives_exact_two_grid():
+    P = _prob(N=4, seed=3)
+    o = mmg.MMGOptions(block=2, nvec=(27,), group=())
+    H = mmg.MMG(P, o)
+    r = _free_random(P, 1)
+    e = H(r)
+    exact = spla.spsolve(P["A"].tocsc(), r)
+    np.testing.assert_allclose(e, exact, rtol=1e-9, atol=1e-11 * np.abs(exact).max())
+
+
+def test_complete_bases_give_exact_three_grid():
+    P = _prob(N=8, seed=3)
+    o = mmg.MMGOptions(block=2, nvec=(27, 216), group=(2,))
+    H = mmg.MMG(P, o)
+    r = _free_random(P, 2)
+    e = H(r)
+    exact = spla.spsolve(P["A"].tocsc(), r)
+    np.testing.assert_allclose(e, exact, rtol=1e-8, atol=1e-10 * np.abs(exact).max())
+
+
+def _dense_vcycle_matrix(H, P):
+    """Closed product form of the V-cycle: B = (I - E) A^{-1} with
+    E = S^nu (I - P B_c P^T A) S^nu, S = I - W^{-1} A (W the smoother),
+    B_c the coarse V-cycle (recursively) or A_L^{-1} at the coarsest grid."""
+    o = H.opts
+    mats = [P["A"].toarray()] + [lev.A.toarray() for lev in H.levels]
+    Ps = [lev.P.toarray() for lev in H.levels]
+
+    def smoother_inv(l):
+        A = mats[l]
+        if l == 0:
+            return o.omega * np.diag(1.0 / np.diag(A))
+        L = H.levels[l - 1].L
+        n = A.shape[0]
+        Winv = np.zeros((n, n))
+        for c in range(n // L):
+            s = slice(c * L, (c + 1) * L)
+            D = A[s, s].copy()
+            off = np.abs(A[s]).sum(axis=1) - np.abs(A[s, s]).sum(axis=1)
+            Winv[s, s] = np.linalg.inv(D + np.diag(off))
+        return Winv
+
+    def B(l):
+        A = mats[l]
+        if l == len(mats) - 1:
+            return np.linalg.inv(A)
+        nu = o.nu_fine if l == 0 else o.nu_coarse
+        I = np.eye(A.shape[0])
+        S = I - smoother_inv(l) @ A
+        Sn = np.linalg.matrix_power(S, nu)
+        E = Sn @ (I - Ps[l] @ B(l + 1) @ Ps[l].T @ A) @ Sn
+        return (I - E) @ np.linalg.inv(A)
+
+    return B(0)
+
+
+def test_vcycle_equals_closed_product_form():
+    P = _prob(N=8, seed=21)
+    o = mmg.MMGOptions(block=2, nvec=(4, 6), group=(2,))
+    H = mmg.MMG(P, o)
+    Bd = _dense_vcycle_matrix(H, P)
+    n = P["A"].shape[0]
+    rng_cols = [0, 5, 100, 333, n - 1]
+    for j in rng_cols:
+        ej = np.zeros(n)
+        ej[j] = 1.0
+        np.testing.assert_allclose(H(ej), Bd[:, j], rtol=1e-9, atol=1e-12 * np.abs(Bd).max())
+
+
+def test_vcycle_symmetric_positive_definite():
+    P = _prob(N=16, seed=8, density="chan", kmin=1e-6)
+    H = mmg.MMG(P)
+    x = _free_random(P, 11)
+    y = _free_random(P, 12)
+    Bx, By = H(x), H(y)
+    assert abs(Bx @ y - x @ By) <= 1e-12 * np.linalg.norm(Bx) * np.linalg.norm(y)
+    assert x @ Bx > 0 and y @ By > 0
+
+
+def test_coarse_initial_guess_is_galerkin_orthogonal():
+    P = _prob(N=16, seed=6)
+    H = mmg.MMG(P)
+    u0 = H.coarse_guess(P["b"])
+    res = H.Pcomp.T @ (P["b"] - P["A"] @ u0)
+    assert np.abs(res).max() <= 1e-12 * np.abs(H.Pcomp.T @ P["b"]).max()
+    u1 = H.coarse_guess(P["b"], u_prev=0.5 * u0 + 0.01)
+    res1 = H.Pcomp.T @ (P["b"] - P["A"] @ u1)
+    assert np.abs(res1).max() <= 1e-11 * np.abs(H.Pcomp.T @ P["b"]).max()
+
+
+@pytest.mark.parametrize("density,kmin", [("rand", 1e-3), ("chan", 1e-6)])
+def test_mmg_pcg_matches_direct_solve(density, kmin):
+    P = _prob(N=16, seed=2, density=density, kmin=kmin)
+    H = mmg.MMG(P)
+    u, info = krylov.pcg(P["A"], P["b"], precond=H, u0=H.coarse_guess(P["b"]), tol=1e-12)
+    assert info["converged"], info["iters"]
+    ud = spla.spsolve(P["A"].tocsc(), P["b"])
+    assert np.linalg.norm(u - ud) <= 1e-8 * np.linalg.norm(ud)
+    # a robust preconditioner: far fewer iterations than Jacobi-PCG
+    _, ij = krylov.pcg(P["A"], P["b"], precond=krylov.jacobi_precond(P["A"]), tol=1e-12,
+                       maxit=20000)
+    assert info["iters"] * 3 < ij["iters"]
