@@ -1,0 +1,249 @@
+/*
+ * thermo.h — C ABI of libthermo: preconditioned CG for the 3-D steady heat
+ * equation with SIMP conductivity on a structured grid of trilinear (Q1)
+ * elements, preconditioned by the multiscale multigrid (MMG) of
+ * "A robust solver for large-scale heat transfer topology optimization"
+ * (arXiv 2410.06850), and the adjoint compliance sensitivity.
+ *
+ * Paper anchors
+ *   Sec. 2.1 Eq. (1)   SIMP law  kappa_e = kmin + x_e^p (kmax - kmin)
+ *   Sec. 2.2 Eq. (5)   SPD system A t = f (here: Q1 nodal elements)
+ *   Sec. 2.3 Eqs. (6)-(7)  objective and adjoint sensitivity
+ *   Sec. 3  Eq. (8)    local spectral problem on each coarse block
+ *   Sec. 3  Eq. (9)    spectral problem on coarse-coarse blocks in W_c
+ *   Sec. 3  Algorithm 1  smoothed multigrid cycle (generalised to Q grids)
+ *   Sec. 4             PETSc CG with the preconditioner; set-up / LS1 / LS2
+ *
+ * Conventions (all entry points)
+ *   - Grid: Nx x Ny x Nz box elements of size hx x hy x hz.  Nodes
+ *     n = i + (Nx+1)*(j + (Ny+1)*k) (x fastest); elements
+ *     e = ex + Nx*(ey + Ny*ez).  Element e's local node a = ax+2ay+4az is
+ *     node (ex+ax, ey+ay, ez+az).
+ *   - Array arguments are DEVICE pointers owned by the caller, contiguous in
+ *     the layout above, unless a parameter says "host".  The library copies
+ *     into its own padded device layout and owns every internal buffer.
+ *   - All device work is enqueued on the CUDA stream given to thermo_create.
+ *     Calls return after enqueueing, except thermo_setup_precond and
+ *     thermo_solve, which synchronise the stream (status words, convergence
+ *     checks) and thermo_compliance (returns a host scalar).
+ *   - Every call returns a thermo_status; none aborts, asserts or traps.  On
+ *     failure the context stays valid and thermo_last_error() describes it.
+ *   - Call order: create -> set_density -> setup_precond -> solve (any number
+ *     of times) -> sensitivity.  set_density invalidates the preconditioner;
+ *     solve before setup_precond (with pc = MMG) returns THERMO_ESTATE.
+ *   - The context is not thread-safe; use one context per host thread.
+ */
+#ifndef THERMO_H
+#define THERMO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct thermo_ctx thermo_ctx; /* opaque, owned by the library */
+
+typedef enum {
+  THERMO_OK = 0,
+  THERMO_EINVAL = -1,      /* bad argument (sizes, NULL, empty Dirichlet set) */
+  THERMO_ENOMEM = -2,      /* device or host allocation failed */
+  THERMO_ECUDA = -3,       /* a CUDA call or kernel launch failed */
+  THERMO_ENOTCONV = -4,    /* max_iter reached; u holds the last iterate */
+  THERMO_EBREAKDOWN = -5,  /* CG breakdown: p^T A p <= 0 or NaN/Inf */
+  THERMO_ESINGULAR = -6,   /* non-positive pivot in the coarsest Cholesky */
+  THERMO_ESTATE = -7       /* call out of order (e.g. solve before setup) */
+} thermo_status;
+
+typedef enum {
+  THERMO_FP64 = 0,         /* everything FP64 (V-cycle included), standard PCG */
+  THERMO_MIXED = 1,        /* FP32 V-cycle inside FP64 flexible CG */
+  THERMO_MIXED_BF16S = 2   /* as MIXED, fine-grid smoother data stored as BF16 */
+} thermo_precision;
+
+typedef enum {
+  THERMO_PC_MMG = 0,       /* the multiscale multigrid V-cycle (Algorithm 1) */
+  THERMO_PC_NONE = 1,      /* plain CG (comparison mode) */
+  THERMO_PC_JACOBI = 2     /* point-Jacobi PCG (comparison mode) */
+} thermo_pc;
+
+typedef enum {
+  THERMO_GUESS_ZERO = 0,        /* u0 = 0 (Dirichlet values on Gamma_D) */
+  THERMO_GUESS_GIVEN = 1,       /* u0 = u on entry */
+  THERMO_GUESS_COARSE = 2,      /* u0 = P A_L^-1 P^T b: coarsest solution interpolated */
+  THERMO_GUESS_WARM_COARSE = 3  /* u0 = u + P A_L^-1 P^T (b - A u) */
+} thermo_guess;
+
+#define THERMO_MAX_LEVELS 8
+
+/* Hierarchy and solver options.  Level 1 cells are blocks of block^3 fine
+ * elements carrying nvec[0] local eigenvectors (Eq. (8)); level l >= 2 cells
+ * are groups of group[l-1]^3 level-(l-1) cells carrying nvec[l-1] vectors
+ * (Eq. (9)).  The last level is solved by dense FP64 Cholesky. */
+typedef struct {
+  int levels;                       /* number of coarse levels, 1..THERMO_MAX_LEVELS */
+  int block;                        /* b (fine elements per block edge) */
+  int group[THERMO_MAX_LEVELS];     /* group[l-1] = g_l for l >= 2 (group[0] unused) */
+  int nvec[THERMO_MAX_LEVELS];      /* nvec[l-1] = L_l, 1 <= L_l <= 32 */
+  int nu_fine;                      /* damped-Jacobi sweeps before and after (>= 1) */
+  int nu_coarse;                    /* l1-block-Jacobi sweeps on coarse levels (>= 1) */
+  double omega;                     /* fine Jacobi damping (default 2/3) */
+  thermo_precision prec;
+  thermo_pc pc;
+  int guess;                        /* a thermo_guess value */
+  int max_iter;                     /* default 10000 */
+  int flexible;                     /* -1 auto (flexible iff prec != FP64), 0, 1 */
+  int check_every;                  /* host convergence check every k iterations (>= 1) */
+} thermo_options;
+
+typedef struct {
+  int iters;                        /* A p products = preconditioner applications */
+  int restarts;                     /* residual replacements after a failed true-residual check */
+  double rel_res_recursive;         /* ||r_k|| / ||b|| of the recurrence at exit */
+  double rel_res_true;              /* ||b - A u|| / ||b|| recomputed in FP64 at exit */
+  double t_setup_ms;                /* last thermo_setup_precond wall time */
+  double t_solve_ms;                /* this solve's wall time */
+  int status;                       /* thermo_status of the solve */
+} thermo_solve_info;
+
+/* Fill *opt with the defaults for an Nx x Ny x Nz grid: b = 4, L_1 = 4, then
+ * groups of 2^3 cells down to a 4^3-cell coarsest level with L = 17 (the
+ * second level keeps 8 vectors when there are more than two coarse levels),
+ * nu_fine = 2, nu_coarse = 1, omega = 2/3, MIXED, MMG, coarse guess,
+ * max_iter = 10000, flexible auto, check_every = 1.  Returns EINVAL if the
+ * grid is not a multiple of 4 in each axis. */
+thermo_status thermo_default_options(const int grid[3], thermo_options *opt);
+
+/* Create a solver context.
+ *   grid[3]          host: Nx, Ny, Nz (each a multiple of opt->block and
+ *                    Nx/b etc. a multiple of the product of the group sizes)
+ *   h[3]             host: element edge lengths (> 0)
+ *   dirichlet_mask   device, uint8[(Nx+1)(Ny+1)(Nz+1)]: 1 = node on Gamma_D.
+ *                    Must be non-empty (else the operator is singular: EINVAL).
+ *   dirichlet_value  device, double[nodes] or NULL (= 0): T_D on Gamma_D
+ *   source           device, double[Nx*Ny*Nz]: element heat source q_e; the
+ *                    load is f_i = sum_{e contains i} q_e |e| / 8
+ *   cuda_stream      a cudaStream_t (NULL = legacy default stream)
+ *   opt              host, or NULL for thermo_default_options(grid)
+ *   out              host: receives the context
+ */
+thermo_status thermo_create(const int grid[3], const double h[3],
+                            const uint8_t *dirichlet_mask,
+                            const double *dirichlet_value,
+                            const double *source, void *cuda_stream,
+                            const thermo_options *opt, thermo_ctx **out);
+
+/* Set the design (Sec. 2.1 Eq. (1)): x device double[M] in [0,1] (not
+ * checked), p >= 1, 0 < kmin <= kmax.  kappa is evaluated once per element
+ * here and kept in FP64/FP32/BF16 copies.  Marks the preconditioner stale. */
+thermo_status thermo_set_density(thermo_ctx *ctx, const double *x, double p,
+                                 double kmin, double kmax);
+
+/* Build the MMG hierarchy for the current design (Sec. 3): local spectral
+ * problems (Eq. (8)) on every block, M-orthonormal bases, Galerkin operators,
+ * spectral problems on groups (Eq. (9)), l1-block-Jacobi inverses and the
+ * dense FP64 Cholesky of the coarsest operator.  ESINGULAR on a non-positive
+ * pivot.  Synchronises the stream.  With pc = NONE/JACOBI this only records
+ * that the context is ready. */
+thermo_status thermo_setup_precond(thermo_ctx *ctx);
+
+/* Solve A u = b to ||b - A u||_2 <= tol ||b||_2 (checked on the recursive
+ * residual, confirmed on the true FP64 residual at exit).
+ *   rhs   device double[nodes] (natural layout), or NULL for the assembled
+ *         load f (with Dirichlet lifting b_F = f_F - A_FD T_D, b_D = T_D)
+ *   u     device double[nodes]: initial guess if opt.guess is GIVEN or
+ *         WARM_COARSE; the solution on return (also on ENOTCONV)
+ *   info  host, may be NULL
+ * Synchronises the stream once per convergence check. */
+thermo_status thermo_solve(thermo_ctx *ctx, const double *rhs, double *u,
+                           double tol, thermo_solve_info *info);
+
+/* Adjoint sensitivity of the compliance c = f^T u for homogeneous Dirichlet
+ * data (adjoint = state, Sec. 2.3):
+ *   dc[e] = -p x_e^(p-1) (kmax - kmin) u_e^T K0 u_e
+ * u device double[nodes], dc device double[M]. */
+thermo_status thermo_sensitivity(thermo_ctx *ctx, const double *u, double *dc);
+
+/* c = f^T u (Sec. 2.3 Eq. (6) with q = 1: the mean temperature).
+ * u device double[nodes]; c host double*.  Synchronises the stream. */
+thermo_status thermo_compliance(thermo_ctx *ctx, const double *u, double *c);
+
+/* Last error message of this context (never NULL). */
+const char *thermo_last_error(const thermo_ctx *ctx);
+
+/* Release every device and host resource of the context (NULL is a no-op). */
+void thermo_destroy(thermo_ctx *ctx);
+
+/* ---- Inspection and building blocks (tests, benchmarks, the SIMP harness) */
+
+/* y = A u with the Dirichlet-eliminated operator (identity rows on Gamma_D,
+ * no coupling to Gamma_D columns), in the given arithmetic:
+ * THERMO_FP64 (FP64), THERMO_MIXED (FP32 data and math) or
+ * THERMO_MIXED_BF16S (BF16 data, FP32 math).  u, y: device double[nodes]. */
+thermo_status thermo_apply(thermo_ctx *ctx, int precision, const double *u, double *y);
+
+/* z = B r: one MMG V-cycle (Algorithm 1) in the context's precision.
+ * r, z: device double[nodes].  Requires setup_precond. */
+thermo_status thermo_vcycle(thermo_ctx *ctx, const double *r, double *z);
+
+/* The assembled load vector f (device double[nodes]). */
+thermo_status thermo_load_vector(thermo_ctx *ctx, double *f);
+
+/* Hierarchy description (host outputs, any may be NULL):
+ * nlevels (coarse levels), cells[l*3+k] cells per axis of level l+1,
+ * nvec[l], ndof[l] = cells * nvec. */
+thermo_status thermo_hierarchy(const thermo_ctx *ctx, int *nlevels, int *cells,
+                               int *nvec, long long *ndof);
+
+/* Copy level data out (device double outputs, FP64 masters):
+ *   what = 0: basis of level `level` — level 1: Phi as double[nodes][L_1]
+ *             (natural node order); level l >= 2: Psi as
+ *             double[cells_l][g^3 L_{l-1}][L_l] (rows in the group's local
+ *             cell order lx + g ly + g^2 lz, then vector index)
+ *   what = 1: Galerkin operator tiles double[cells][27][L][L], neighbour
+ *             n = (dx+1) + 3(dy+1) + 9(dz+1); row dofs of the cell, column
+ *             dofs of the neighbour
+ *   what = 2: local eigenvalues double[cells][L]
+ *   what = 3: (coarsest level only) dense inverse A_L^-1 double[n][n]
+ * `count` is the capacity of `out` in doubles; EINVAL if too small. */
+thermo_status thermo_export_level(thermo_ctx *ctx, int level, int what,
+                                  double *out, long long count);
+
+/* Density filter (textbook SIMP harness, not in the paper):
+ * out_e = sum_j w_ej in_j / sum_j w_ej with w_ej = max(0, rmin - |c_e - c_j|)
+ * in element units, truncated at the domain boundary; transpose = 1 applies
+ * the transpose (gradient chain rule).  in/out device double[M], in != out. */
+thermo_status thermo_filter(thermo_ctx *ctx, const double *in, double *out,
+                            double rmin, int transpose);
+
+/* Optimality-criteria update with bisection on the multiplier so that the
+ * filtered volume fraction hits volfrac: x (device double[M], in/out),
+ * dc, dv device double[M].  change (host, may be NULL) receives
+ * max |x_new - x_old|. */
+thermo_status thermo_oc_update(thermo_ctx *ctx, double *x, const double *dc,
+                               const double *dv, double volfrac, double move,
+                               double rmin, double *change);
+
+/* Number of kernel launches this library has issued in the process (host
+ * counter; for launch accounting in benchmarks). */
+long long thermo_launch_count(void);
+
+/* Benchmark one internal kernel: `reps` back-to-back launches on the
+ * context's own buffers, timed with CUDA events on the context stream.
+ *   which: 0 FP64 apply (+ fused p.Ap), 1 FP32 apply, 2 BF16 apply,
+ *          3 FP32 fine smoother sweep, 4 FP32 fused residual + restriction,
+ *          5 FP32 fused prolongation + sweep, 6 level-1 block-sparse apply,
+ *          7 FP64 CG update, 8 one mixed V-cycle, 9 one FP64 V-cycle,
+ *          10 FP64 fine smoother sweep
+ *   ms_per_launch (host): average duration; bytes_per_launch (host, may be
+ *   NULL): algorithmic DRAM bytes of one launch (0 for whole cycles).
+ * Kernels 4-6, 8, 9 need setup_precond; 2 needs a MIXED_BF16S context and 9
+ * an FP64 context.  Buffer contents are overwritten. */
+thermo_status thermo_bench_kernel(thermo_ctx *ctx, int which, int reps, double *ms_per_launch,
+                                  double *bytes_per_launch);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* THERMO_H */

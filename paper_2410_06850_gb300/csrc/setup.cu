@@ -1,0 +1,1022 @@
+// Preconditioner set-up (Sec. 3): local spectral problems, Galerkin coarse
+// operators, smoother inverses and the coarsest factorisation.
+//
+// * Eq. (8) on every level-1 block B (one CTA per block): the Neumann form of
+//   the couplings internal to B, Ã_ij = A_ij (i != j in B),
+//   Ã_ii = -sum_{j in B} A_ij, against the kappa-weighted lumped mass
+//   m_i = sum_{e ∋ i} kappa_e |e|/8.  C = M^-1/2 Ã M^-1/2 is diagonalised by a
+//   parallel cyclic Jacobi method in FP32 in shared memory; the L smallest
+//   eigenvectors are refined by an FP64 Rayleigh-Ritz step on the sparse Ã
+//   and M-orthonormalised by FP64 modified Gram-Schmidt.
+// * Eq. (9) on every group G of g^3 cells of the previous level (one CTA per
+//   group): Ã_G = (A_prev)_GG - blockdiag_c P_c^T diag(rho_G) P_c, i.e. the
+//   Galerkin block of G minus the projected couplings that leave G (rho_G is
+//   the fine row sum restricted to G); with M-orthonormal bases the mass is
+//   the identity, so this is a standard eigenproblem (same Jacobi + FP64
+//   Rayleigh-Ritz + Gram-Schmidt).
+// * Galerkin operators A_l = R A_{l-1} R^T as 27-neighbour tiles (FP64).
+// * l1-block-Jacobi inverses, dense FP64 Cholesky and explicit inverse of the
+//   coarsest operator.
+//
+// Eigenvector sign convention: the entry of largest magnitude (lowest index
+// on ties) is positive.  A cell with fewer admissible vectors than L keeps
+// zero vectors in the remaining slots, flagged inactive.
+#include <math.h>
+
+#include "common.cuh"
+#include "kernels.h"
+
+namespace thermo {
+
+// ---------------------------------------------------------------------------
+// CTA-wide helpers (any blockDim that is a multiple of 32)
+__device__ double cta_sum(double v, double* sh) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int w = threadIdx.x >> 5, l = threadIdx.x & 31, nw = blockDim.x >> 5;
+  __syncthreads();
+  if (l == 0) sh[w] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int i = 0; i < nw; ++i) s += sh[i];
+    sh[32] = s;
+  }
+  __syncthreads();
+  return sh[32];
+}
+
+// Parallel cyclic Jacobi (round-robin pairing) on a symmetric n2 x n2 matrix A
+// (row-major, shared memory), n2 even; accumulates V (A_in = V diag(A_out) V^T).
+// Rotation per pair (p, q): tau = (a_qq - a_pp)/(2 a_pq),
+// t = sign(tau)/(|tau| + sqrt(1 + tau^2)), c = 1/sqrt(1 + t^2), s = t c;
+// the 2x2 blocks of the pair grid are transformed independently.
+template <class T>
+__device__ int jacobi_eigen(T* A, T* V, int n2, T* cs, T* sn, int* pp, int* qq, double* sh, int max_sweeps,
+                            double tol) {
+  const int tid = threadIdx.x, nt = blockDim.x, m = n2 / 2;
+  for (int i = tid; i < n2 * n2; i += nt) V[i] = (i / n2 == i % n2) ? T(1) : T(0);
+  __syncthreads();
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int i = tid; i < n2 * n2; i += nt) {
+      const double v = (double)A[i];
+      if (i / n2 != i % n2)
+        off += v * v;
+      else if (fabs(v) < 1e30)  // padding / inactive sentinels do not count
+        tot += v * v;
+    }
+    off = cta_sum(off, sh);
+    tot = cta_sum(tot, sh);
+    if (off <= tol * tol * tot) break;
+    for (int s = 0; s < n2 - 1; ++s) {
+      for (int k = tid; k < m; k += nt) {
+        int p, q;
+        if (k == 0) {
+          p = n2 - 1;
+          q = s;
+        } else {
+          p = (s + k) % (n2 - 1);
+          q = (s - k + n2 - 1) % (n2 - 1);
+        }
+        const T apq = A[p * n2 + q], app = A[p * n2 + p], aqq = A[q * n2 + q];
+        T c = T(1), sv = T(0);
+        if (apq != T(0) && fabs((double)apq) > 1e-30 * sqrt(fabs((double)app * (double)aqq))) {
+          const T tau = (aqq - app) / (T(2) * apq);
+          const T t = (tau >= T(0) ? T(1) : T(-1)) / (fabs(tau) + sqrt(T(1) + tau * tau));
+          c = T(1) / sqrt(T(1) + t * t);
+          sv = t * c;
+        }
+        cs[k] = c;
+        sn[k] = sv;
+        pp[k] = p;
+        qq[k] = q;
+      }
+      __syncthreads();
+      for (int w = tid; w < m * m; w += nt) {
+        const int k = w / m, l = w - (w / m) * m;
+        const int p = pp[k], q = qq[k], r = pp[l], s2 = qq[l];
+        const T ck = cs[k], sk = sn[k], cl = cs[l], sl = sn[l];
+        const T a_pr = A[p * n2 + r], a_ps = A[p * n2 + s2], a_qr = A[q * n2 + r], a_qs = A[q * n2 + s2];
+        const T b_pr = ck * a_pr - sk * a_qr, b_ps = ck * a_ps - sk * a_qs;
+        const T b_qr = sk * a_pr + ck * a_qr, b_qs = sk * a_ps + ck * a_qs;
+        T c_pr = cl * b_pr - sl * b_ps, c_ps = sl * b_pr + cl * b_ps;
+        T c_qr = cl * b_qr - sl * b_qs, c_qs = sl * b_qr + cl * b_qs;
+        if (k == l) {
+          c_ps = T(0);
+          c_qr = T(0);
+        }
+        A[p * n2 + r] = c_pr;
+        A[p * n2 + s2] = c_ps;
+        A[q * n2 + r] = c_qr;
+        A[q * n2 + s2] = c_qs;
+      }
+      for (int w = tid; w < n2 * m; w += nt) {
+        const int i = w / m, l = w - (w / m) * m;
+        const int r = pp[l], s2 = qq[l];
+        const T cl = cs[l], sl = sn[l];
+        const T vr = V[i * n2 + r], vs = V[i * n2 + s2];
+        V[i * n2 + r] = cl * vr - sl * vs;
+        V[i * n2 + s2] = sl * vr + cl * vs;
+      }
+      __syncthreads();
+    }
+  }
+  return sweep;
+}
+
+// indices of the k smallest diagonal entries of A (ascending; ties -> lower index)
+template <class T>
+__device__ void select_smallest(const T* A, int n2, int k, int* sel) {
+  for (int i = threadIdx.x; i < n2; i += blockDim.x) {
+    const T li = A[i * n2 + i];
+    int rank = 0;
+    for (int j = 0; j < n2; ++j) {
+      const T lj = A[j * n2 + j];
+      rank += (lj < li || (lj == li && j < i)) ? 1 : 0;
+    }
+    if (rank < k) sel[rank] = i;
+  }
+  __syncthreads();
+}
+
+// Rayleigh-Ritz finish on an FP64 basis X[n][ld] (k columns, M-orthonormal):
+// H = X^T W (W = Ã X) is diagonalised (FP64 Jacobi), X <- X Y sorted by
+// eigenvalue, sign-fixed.  Scratch in shared memory.
+__device__ void rr_finish(double* X, const double* W, int n, int ld, int k, double* H, double* Y, double* cs,
+                          double* sn, int* pp, int* qq, double* sh, double* tmp, double* lam, int* sel) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int k2 = (k + 1) & ~1;
+  for (int w = tid; w < k2 * k2; w += nt) {
+    const int a = w / k2, b = w % k2;
+    double s = 0.0;
+    if (a < k && b < k) {
+      for (int i = 0; i < n; ++i) s += X[i * ld + a] * W[i * ld + b];
+    } else if (a == b) {
+      s = 1e300;  // padding column, never selected
+    }
+    H[w] = s;
+  }
+  __syncthreads();
+  // symmetrise
+  for (int w = tid; w < k2 * k2; w += nt) {
+    const int a = w / k2, b = w % k2;
+    if (a < b && a < k && b < k) {
+      const double v = 0.5 * (H[a * k2 + b] + H[b * k2 + a]);
+      H[a * k2 + b] = v;
+      H[b * k2 + a] = v;
+    }
+  }
+  __syncthreads();
+  jacobi_eigen<double>(H, Y, k2, cs, sn, pp, qq, sh, 30, 1e-15);
+  select_smallest<double>(H, k2, k, sel);
+  for (int w = tid; w < n * k; w += nt) {
+    const int i = w / k, a = w % k;
+    double s = 0.0;
+    for (int b = 0; b < k; ++b) s += X[i * ld + b] * Y[b * k2 + sel[a]];
+    tmp[i * ld + a] = s;
+  }
+  __syncthreads();
+  for (int w = tid; w < n * k; w += nt) {
+    const int i = w / k, a = w % k;
+    X[i * ld + a] = tmp[i * ld + a];
+  }
+  if (tid < k) lam[tid] = H[sel[tid] * k2 + sel[tid]];
+  __syncthreads();
+  // sign: largest |entry| (lowest index on ties) positive
+  if (tid < k) {
+    double best = -1.0;
+    int bi = 0;
+    for (int i = 0; i < n; ++i) {
+      const double v = fabs(X[i * ld + tid]);
+      if (v > best) {
+        best = v;
+        bi = i;
+      }
+    }
+    tmp[tid] = X[bi * ld + tid] < 0.0 ? -1.0 : 1.0;
+  }
+  __syncthreads();
+  for (int w = tid; w < n * k; w += nt) {
+    const int i = w / k, a = w % k;
+    X[i * ld + a] *= tmp[a];
+  }
+  __syncthreads();
+}
+
+// Modified Gram-Schmidt of the k columns of X[n][ld] in <a,b> = sum m_i a_i b_i
+// (m == nullptr: Euclidean).  Columns of zero norm are left zero.
+__device__ void mgs(double* X, const double* m, int n, int ld, int k, double* sh) {
+  for (int j = 0; j < k; ++j) {
+    for (int i = 0; i < j; ++i) {
+      double d = 0.0;
+      for (int r = threadIdx.x; r < n; r += blockDim.x) d += (m ? m[r] : 1.0) * X[r * ld + i] * X[r * ld + j];
+      d = cta_sum(d, sh);
+      for (int r = threadIdx.x; r < n; r += blockDim.x) X[r * ld + j] -= d * X[r * ld + i];
+      __syncthreads();
+    }
+    double nn = 0.0;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) nn += (m ? m[r] : 1.0) * X[r * ld + j] * X[r * ld + j];
+    nn = cta_sum(nn, sh);
+    const double inv = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
+    for (int r = threadIdx.x; r < n; r += blockDim.x) X[r * ld + j] *= inv;
+    __syncthreads();
+  }
+}
+
+// fine-grid coupling A_ij between node (x,y,z) and (x+ox, y+oy, z+oz), i != j
+__device__ __forceinline__ double coupling(const Geom& g, const double* k64, int x, int y, int z, int ox, int oy,
+                                           int oz) {
+  double s = 0.0;
+  const int exa = ox == 0 ? x - 1 : (ox < 0 ? x - 1 : x), exb = ox == 0 ? x : exa;
+  const int eya = oy == 0 ? y - 1 : (oy < 0 ? y - 1 : y), eyb = oy == 0 ? y : eya;
+  const int eza = oz == 0 ? z - 1 : (oz < 0 ? z - 1 : z), ezb = oz == 0 ? z : eza;
+  for (int ez = eza; ez <= ezb; ++ez)
+    for (int ey = eya; ey <= eyb; ++ey)
+      for (int ex = exa; ex <= exb; ++ex) s += k64[eidx(g, ex, ey, ez)];
+  const int pat = (ox != 0 ? 1 : 0) | (oy != 0 ? 2 : 0) | (oz != 0 ? 4 : 0);
+  return g.c[pat] * s;
+}
+__device__ __forceinline__ double kappa_sum8(const Geom& g, const double* k64, int x, int y, int z) {
+  double s = 0.0;
+  for (int dz = -1; dz <= 0; ++dz)
+    for (int dy = -1; dy <= 0; ++dy)
+      for (int dx = -1; dx <= 0; ++dx) s += k64[eidx(g, x + dx, y + dy, z + dz)];
+  return s;
+}
+
+// ---------------------------------------------------------------------------
+// Eq. (8): level-1 bases.  Blocks are launched per class (last in x/y/z or
+// not) so that the shared-memory footprint matches the block's node count.
+constexpr int EIG_NT = 256;
+
+struct L1Smem {
+  // offsets in bytes
+  size_t C, V, X, W, tmp, m, H, Y, cs, sn, cs64, sn64, pp, qq, sel, list, lmap, lam, sh, total;
+};
+__host__ __device__ inline L1Smem l1_smem(int n2, int L, int nmap) {
+  L1Smem s;
+  size_t o = 0;
+  auto al = [&](size_t bytes) {
+    size_t r = o;
+    o += (bytes + 15) & ~(size_t)15;
+    return r;
+  };
+  const int k2 = (L + 1) & ~1;
+  s.C = al((size_t)n2 * n2 * 4);
+  s.V = al((size_t)n2 * n2 * 4);
+  s.X = al((size_t)n2 * L * 8);
+  s.W = al((size_t)n2 * L * 8);
+  s.tmp = al((size_t)n2 * L * 8 + 8 * 64);
+  s.m = al((size_t)n2 * 8);
+  s.H = al((size_t)k2 * k2 * 8);
+  s.Y = al((size_t)k2 * k2 * 8);
+  s.cs = al((size_t)n2 / 2 * 4);
+  s.sn = al((size_t)n2 / 2 * 4);
+  s.cs64 = al((size_t)k2 * 8);
+  s.sn64 = al((size_t)k2 * 8);
+  s.pp = al((size_t)(n2 / 2 + k2) * 4);
+  s.qq = al((size_t)(n2 / 2 + k2) * 4);
+  s.sel = al((size_t)(n2 + k2) * 4);
+  s.list = al((size_t)n2 * 4);
+  s.lmap = al((size_t)nmap * 4);
+  s.lam = al((size_t)k2 * 8);
+  s.sh = al(40 * 8);
+  s.total = o;
+  return s;
+}
+
+__global__ void __launch_bounds__(EIG_NT) k_level1_eigen(Geom g, const uint32_t* __restrict__ bits,
+                                                         const double* __restrict__ k64, int L, int lx, int ly, int lz,
+                                                         int n2, double* __restrict__ phi, double* __restrict__ eig,
+                                                         uint8_t* __restrict__ act, int* status) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int b = g.b;
+  const int cxn = lx ? 1 : g.nbx - 1, cyn = ly ? 1 : g.nby - 1;
+  int bid = blockIdx.x;
+  const int ix = bid % cxn;
+  bid /= cxn;
+  const int iy = bid % cyn, iz = bid / cyn;
+  const int bx = lx ? g.nbx - 1 : ix, by = ly ? g.nby - 1 : iy, bz = lz ? g.nbz - 1 : iz;
+  const int wx = b + lx, wy = b + ly, wz = b + lz;  // nodes per axis of this block
+  const int X0 = bx * b, Y0 = by * b, Z0 = bz * b;
+  const int nmap = wx * wy * wz;
+  L1Smem S = l1_smem(n2, L, nmap);
+  float* C = (float*)(sm + S.C);
+  float* V = (float*)(sm + S.V);
+  double* X = (double*)(sm + S.X);
+  double* W = (double*)(sm + S.W);
+  double* tmp = (double*)(sm + S.tmp);
+  double* m = (double*)(sm + S.m);
+  double* H = (double*)(sm + S.H);
+  double* Y = (double*)(sm + S.Y);
+  float* cs = (float*)(sm + S.cs);
+  float* sn = (float*)(sm + S.sn);
+  double* cs64 = (double*)(sm + S.cs64);
+  double* sn64 = (double*)(sm + S.sn64);
+  int* pp = (int*)(sm + S.pp);
+  int* qq = (int*)(sm + S.qq);
+  int* sel = (int*)(sm + S.sel);
+  int* list = (int*)(sm + S.list);
+  int* lmap = (int*)(sm + S.lmap);
+  double* lam = (double*)(sm + S.lam);
+  double* sh = (double*)(sm + S.sh);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const long long cell = bx + (long long)g.nbx * (by + (long long)g.nby * bz);
+
+  // compact list of free nodes (natural order within the block), serial for determinism
+  if (tid == 0) {
+    int n = 0;
+    for (int k = 0; k < nmap; ++k) {
+      const int x = X0 + k % wx, y = Y0 + (k / wx) % wy, z = Z0 + k / (wx * wy);
+      if (!is_dir(g, bits, x, y, z)) {
+        lmap[k] = n;
+        list[n++] = k;
+      } else {
+        lmap[k] = -1;
+      }
+    }
+    sh[34] = (double)n;
+  }
+  __syncthreads();
+  const int n = (int)sh[34];
+  const int kk = n < L ? n : L;
+  // mass and the Neumann matrix scaled by M^-1/2
+  for (int i = tid; i < n; i += nt) {
+    const int k = list[i];
+    const int x = X0 + k % wx, y = Y0 + (k / wx) % wy, z = Z0 + k / (wx * wy);
+    m[i] = kappa_sum8(g, k64, x, y, z) * g.vol * 0.125;
+  }
+  for (int i = tid; i < n2 * n2; i += nt) C[i] = 0.f;
+  __syncthreads();
+  for (int i = tid; i < n; i += nt) {
+    const int k = list[i];
+    const int x = X0 + k % wx, y = Y0 + (k / wx) % wy, z = Z0 + k / (wx * wy);
+    double diag = 0.0;
+    for (int oz = -1; oz <= 1; ++oz)
+      for (int oy = -1; oy <= 1; ++oy)
+        for (int ox = -1; ox <= 1; ++ox) {
+          if (!ox && !oy && !oz) continue;
+          const int xx = x + ox - X0, yy = y + oy - Y0, zz = z + oz - Z0;
+          if (xx < 0 || yy < 0 || zz < 0 || xx >= wx || yy >= wy || zz >= wz) continue;
+          const int j = lmap[xx + wx * (yy + wy * zz)];
+          if (j < 0) continue;
+          const double a = coupling(g, k64, x, y, z, ox, oy, oz);
+          diag -= a;
+          C[i * n2 + j] = (float)(a / sqrt(m[i] * m[j]));
+        }
+    C[i * n2 + i] = (float)(diag / m[i]);
+  }
+  for (int i = n + tid; i < n2; i += nt) C[i * n2 + i] = 3.0e38f;  // padding: never selected
+  __syncthreads();
+  if (n > 0) jacobi_eigen<float>(C, V, n2, cs, sn, pp, qq, sh, 14, 3e-7);
+  select_smallest<float>(C, n2, kk, sel);
+  // FP64 basis phi = M^-1/2 v, M-orthonormalised
+  for (int w = tid; w < n * L; w += nt) {
+    const int i = w / L, a = w % L;
+    X[w] = a < kk ? (double)V[i * n2 + sel[a]] / sqrt(m[i]) : 0.0;
+  }
+  __syncthreads();
+  mgs(X, m, n, L, kk, sh);
+  // W = Ã X (difference form: (Ã x)_i = sum_{j in B} A_ij (x_j - x_i))
+  for (int i = tid; i < n; i += nt) {
+    const int k = list[i];
+    const int x = X0 + k % wx, y = Y0 + (k / wx) % wy, z = Z0 + k / (wx * wy);
+    double acc[32];
+    for (int a = 0; a < kk; ++a) acc[a] = 0.0;
+    for (int oz = -1; oz <= 1; ++oz)
+      for (int oy = -1; oy <= 1; ++oy)
+        for (int ox = -1; ox <= 1; ++ox) {
+          if (!ox && !oy && !oz) continue;
+          const int xx = x + ox - X0, yy = y + oy - Y0, zz = z + oz - Z0;
+          if (xx < 0 || yy < 0 || zz < 0 || xx >= wx || yy >= wy || zz >= wz) continue;
+          const int j = lmap[xx + wx * (yy + wy * zz)];
+          if (j < 0) continue;
+          const double aij = coupling(g, k64, x, y, z, ox, oy, oz);
+          for (int a = 0; a < kk; ++a) acc[a] += aij * (X[j * L + a] - X[i * L + a]);
+        }
+    for (int a = 0; a < kk; ++a) W[i * L + a] = acc[a];
+  }
+  __syncthreads();
+  if (kk > 0) rr_finish(X, W, n, L, kk, H, Y, cs64, sn64, pp + n2 / 2, qq + n2 / 2, sh, tmp, lam, sel + n2);
+  // outputs
+  for (int k = tid; k < nmap; k += nt) {
+    const int x = X0 + k % wx, y = Y0 + (k / wx) % wy, z = Z0 + k / (wx * wy);
+    const int i = lmap[k];
+    const long long nd = nidx(g, x, y, z);
+    for (int a = 0; a < L; ++a) phi[nd * L + a] = (i >= 0 && a < kk) ? X[i * L + a] : 0.0;
+  }
+  if (tid < L) {
+    eig[cell * L + tid] = tid < kk ? lam[tid] : 0.0;
+    act[cell * L + tid] = tid < kk ? 1 : 0;
+  }
+}
+
+cudaError_t level1_eigen(const Geom& g, const uint32_t* bits, const double* k64, int L1, double* phi64, double* eig,
+                         uint8_t* active, int* status, cudaStream_t st) {
+  for (int lz = 0; lz < 2; ++lz)
+    for (int ly = 0; ly < 2; ++ly)
+      for (int lx = 0; lx < 2; ++lx) {
+        const int cx = lx ? 1 : g.nbx - 1, cy = ly ? 1 : g.nby - 1, cz = lz ? 1 : g.nbz - 1;
+        const long long nb = (long long)cx * cy * cz;
+        if (nb <= 0) continue;
+        const int nmap = (g.b + lx) * (g.b + ly) * (g.b + lz);
+        const int n2 = (nmap + 1) & ~1;
+        const L1Smem S = l1_smem(n2, L1, nmap);
+        cudaError_t e = cudaFuncSetAttribute(k_level1_eigen, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)S.total);
+        if (e != cudaSuccess) return e;
+        note_launch(), k_level1_eigen<<<(unsigned)nb, EIG_NT, S.total, st>>>(g, bits, k64, L1, lx, ly, lz, n2, phi64, eig, active,
+                                                               status);
+        e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+      }
+  return cudaSuccess;
+}
+
+// ---------------------------------------------------------------------------
+// Row-sum corrections for the coarse-coarse problems (Eq. (9)):
+// D[t][B] = sum_{i in B} rho_i^(t) phi_i phi_i^T, with rho_i^(t) the sum of the
+// couplings of node i that leave its level-t cell or reach a Dirichlet node
+// (= sum_{j in cell_t(i), j free} A_ij, since the Neumann rows sum to zero).
+__global__ void k_level1_corr(Geom g, const uint32_t* __restrict__ bits, const double* __restrict__ k64, int L,
+                              const double* __restrict__ phi, int nt_lv, const int* __restrict__ gcum,
+                              double* __restrict__ D) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int b = g.b;
+  const long long cell = blockIdx.x;
+  const int bx = (int)(cell % g.nbx), by = (int)((cell / g.nbx) % g.nby), bz = (int)(cell / ((long long)g.nbx * g.nby));
+  const int wx = b + (bx == g.nbx - 1), wy = b + (by == g.nby - 1), wz = b + (bz == g.nbz - 1);
+  const int nmap = wx * wy * wz;
+  double* contrib = (double*)sm;  // [nmap][L*L]
+  for (int t = 0; t < nt_lv; ++t) {
+    const int G = gcum[t];
+    for (int k = threadIdx.x; k < nmap; k += blockDim.x) {
+      const int x = bx * b + k % wx, y = by * b + (k / wx) % wy, z = bz * b + k / (wx * wy);
+      double rho = 0.0;
+      if (!is_dir(g, bits, x, y, z)) {
+        const int cxi = bx / G, cyi = by / G, czi = bz / G;
+        for (int oz = -1; oz <= 1; ++oz)
+          for (int oy = -1; oy <= 1; ++oy)
+            for (int ox = -1; ox <= 1; ++ox) {
+              if (!ox && !oy && !oz) continue;
+              const int xx = x + ox, yy = y + oy, zz = z + oz;
+              if (xx < 0 || yy < 0 || zz < 0 || xx > g.Nx || yy > g.Ny || zz > g.Nz) continue;
+              const bool same = !is_dir(g, bits, xx, yy, zz) && blk_of(xx, b, g.nbx) / G == cxi &&
+                                blk_of(yy, b, g.nby) / G == cyi && blk_of(zz, b, g.nbz) / G == czi;
+              if (!same) rho -= coupling(g, k64, x, y, z, ox, oy, oz);
+            }
+      }
+      const long long nd = nidx(g, x, y, z);
+      for (int a = 0; a < L; ++a)
+        for (int c = 0; c < L; ++c) contrib[k * L * L + a * L + c] = rho * phi[nd * L + a] * phi[nd * L + c];
+    }
+    __syncthreads();
+    for (int o = threadIdx.x; o < L * L; o += blockDim.x) {
+      double s = 0.0;
+      for (int k = 0; k < nmap; ++k) s += contrib[k * L * L + o];
+      D[((long long)t * g.nbx * g.nby * g.nbz + cell) * L * L + o] = s;
+    }
+    __syncthreads();
+  }
+}
+cudaError_t level1_rowsum_corr(const Geom& g, const uint32_t* bits, const double* k64, int L1, const double* phi64,
+                               int nt, const int* gcum, double* D, cudaStream_t st) {
+  if (nt <= 0) return cudaSuccess;
+  const int nmap = (g.b + 1) * (g.b + 1) * (g.b + 1);
+  const size_t sm = (size_t)nmap * L1 * L1 * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(k_level1_corr, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  note_launch(), k_level1_corr<<<(unsigned)((long long)g.nbx * g.nby * g.nbz), 128, sm, st>>>(g, bits, k64, L1, phi64, nt, gcum, D);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Level-1 Galerkin tiles: for block B, Y = A Phi_B on the one-node ring
+// around B, then tile(B', B) = Phi_{B'}^T Y for the 27 neighbours B', stored
+// in B''s row (its neighbour index points back at B).
+__global__ void k_level1_rap(Geom g, const uint32_t* __restrict__ bits, const double* __restrict__ k64, int L,
+                             const double* __restrict__ phi, double* __restrict__ tiles) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int b = g.b;
+  const long long cell = blockIdx.x;
+  const int bx = (int)(cell % g.nbx), by = (int)((cell / g.nbx) % g.nby), bz = (int)(cell / ((long long)g.nbx * g.nby));
+  const int wx = b + (bx == g.nbx - 1), wy = b + (by == g.nby - 1), wz = b + (bz == g.nbz - 1);
+  const int X0 = bx * b, Y0 = by * b, Z0 = bz * b;
+  const int rx = wx + 2, ry = wy + 2, rz = wz + 2, nreg = rx * ry * rz;
+  double* Yv = (double*)sm;  // [nreg][L]
+  for (int k = threadIdx.x; k < nreg; k += blockDim.x) {
+    const int x = X0 - 1 + k % rx, y = Y0 - 1 + (k / rx) % ry, z = Z0 - 1 + k / (rx * ry);
+    double acc[32];
+    for (int a = 0; a < L; ++a) acc[a] = 0.0;
+    const bool inside = x >= 0 && y >= 0 && z >= 0 && x <= g.Nx && y <= g.Ny && z <= g.Nz;
+    if (inside && !is_dir(g, bits, x, y, z)) {
+      for (int oz = -1; oz <= 1; ++oz)
+        for (int oy = -1; oy <= 1; ++oy)
+          for (int ox = -1; ox <= 1; ++ox) {
+            const int xx = x + ox, yy = y + oy, zz = z + oz;
+            if (xx < X0 || yy < Y0 || zz < Z0 || xx >= X0 + wx || yy >= Y0 + wy || zz >= Z0 + wz) continue;
+            if (is_dir(g, bits, xx, yy, zz)) continue;
+            double aij;
+            if (!ox && !oy && !oz)
+              aij = g.c[0] * kappa_sum8(g, k64, x, y, z);
+            else
+              aij = coupling(g, k64, x, y, z, ox, oy, oz);
+            const long long nd = nidx(g, xx, yy, zz);
+            for (int a = 0; a < L; ++a) acc[a] += aij * phi[nd * L + a];
+          }
+    }
+    for (int a = 0; a < L; ++a) Yv[k * L + a] = acc[a];
+  }
+  __syncthreads();
+  // outputs: for each neighbour offset (dx,dy,dz) of B' relative to B
+  for (int o = threadIdx.x; o < 27 * L * L; o += blockDim.x) {
+    const int n = o / (L * L), a = (o / L) % L, kcol = o % L;
+    const int dx = n % 3 - 1, dy = (n / 3) % 3 - 1, dz = n / 9 - 1;
+    const int nbx = bx + dx, nby = by + dy, nbz = bz + dz;
+    if (nbx < 0 || nby < 0 || nbz < 0 || nbx >= g.nbx || nby >= g.nby || nbz >= g.nbz) continue;
+    // region positions belonging to B'
+    const int xa = dx < 0 ? 0 : (dx == 0 ? 1 : rx - 1), xb = dx < 0 ? 1 : (dx == 0 ? rx - 1 : rx);
+    const int ya = dy < 0 ? 0 : (dy == 0 ? 1 : ry - 1), yb = dy < 0 ? 1 : (dy == 0 ? ry - 1 : ry);
+    const int za = dz < 0 ? 0 : (dz == 0 ? 1 : rz - 1), zb = dz < 0 ? 1 : (dz == 0 ? rz - 1 : rz);
+    double s = 0.0;
+    for (int zz = za; zz < zb; ++zz)
+      for (int yy = ya; yy < yb; ++yy)
+        for (int xx = xa; xx < xb; ++xx) {
+          const int x = X0 - 1 + xx, y = Y0 - 1 + yy, z = Z0 - 1 + zz;
+          const long long nd = nidx(g, x, y, z);
+          s += phi[nd * L + a] * Yv[(xx + rx * (yy + ry * zz)) * L + kcol];
+        }
+    const long long nc = nbx + (long long)g.nbx * (nby + (long long)g.nby * nbz);
+    const int back = (1 - dx) + 3 * (1 - dy) + 9 * (1 - dz);
+    tiles[((nc * 27 + back) * L + a) * L + kcol] = s;
+  }
+}
+cudaError_t level1_rap(const Geom& g, const uint32_t* bits, const double* k64, int L1, const double* phi64,
+                       double* tiles, cudaStream_t st) {
+  const int r = g.b + 3;
+  const size_t sm = (size_t)r * r * r * L1 * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(k_level1_rap, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  note_launch(), k_level1_rap<<<(unsigned)((long long)g.nbx * g.nby * g.nbz), 128, sm, st>>>(g, bits, k64, L1, phi64, tiles);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------
+// Eq. (9): one CTA per group G of g^3 cells of the previous level.
+struct GSmem {
+  size_t C, V, X, W, tmp, H, Y, cs, sn, cs64, sn64, pp, qq, sel, act, lam, sh, total;
+};
+__host__ __device__ inline GSmem g_smem(int n2, int L) {
+  GSmem s;
+  size_t o = 0;
+  auto al = [&](size_t bytes) {
+    size_t r = o;
+    o += (bytes + 15) & ~(size_t)15;
+    return r;
+  };
+  const int k2 = (L + 1) & ~1;
+  s.C = al((size_t)n2 * n2 * 4);
+  s.V = al((size_t)n2 * n2 * 4);
+  s.X = al((size_t)n2 * L * 8);
+  s.W = al((size_t)n2 * L * 8);
+  s.tmp = al((size_t)n2 * L * 8 + 8 * 64);
+  s.H = al((size_t)k2 * k2 * 8);
+  s.Y = al((size_t)k2 * k2 * 8);
+  s.cs = al((size_t)n2 / 2 * 4);
+  s.sn = al((size_t)n2 / 2 * 4);
+  s.cs64 = al((size_t)k2 * 8);
+  s.sn64 = al((size_t)k2 * 8);
+  s.pp = al((size_t)(n2 / 2 + k2) * 4);
+  s.qq = al((size_t)(n2 / 2 + k2) * 4);
+  s.sel = al((size_t)(n2 + k2) * 4);
+  s.act = al((size_t)n2 * 4);
+  s.lam = al((size_t)k2 * 8);
+  s.sh = al(40 * 8);
+  s.total = o;
+  return s;
+}
+
+__device__ __forceinline__ long long cell_of_local(const CLevel& prev, const CLevel& cur, long long G, int lc) {
+  const int g = cur.g;
+  const int gx = (int)(G % cur.mx), gy = (int)((G / cur.mx) % cur.my), gz = (int)(G / ((long long)cur.mx * cur.my));
+  const int lx = lc % g, ly = (lc / g) % g, lz = lc / (g * g);
+  return (gx * g + lx) + (long long)prev.mx * ((gy * g + ly) + (long long)prev.my * (gz * g + lz));
+}
+__device__ __forceinline__ int nbr_index(int dx, int dy, int dz) { return (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1); }
+
+__global__ void __launch_bounds__(EIG_NT) k_group_eigen(CLevel prev, CLevel cur, const double* __restrict__ Tp,
+                                                        const double* __restrict__ Dc, const uint8_t* __restrict__ actp,
+                                                        int n2, double* __restrict__ Psi, double* __restrict__ eig,
+                                                        uint8_t* __restrict__ actc) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int g = cur.g, Lp = prev.L, L = cur.L, ng = g * g * g, n = ng * Lp;
+  GSmem S = g_smem(n2, L);
+  float* C = (float*)(sm + S.C);
+  float* V = (float*)(sm + S.V);
+  double* X = (double*)(sm + S.X);
+  double* W = (double*)(sm + S.W);
+  double* tmp = (double*)(sm + S.tmp);
+  double* H = (double*)(sm + S.H);
+  double* Y = (double*)(sm + S.Y);
+  float* cs = (float*)(sm + S.cs);
+  float* sn = (float*)(sm + S.sn);
+  double* cs64 = (double*)(sm + S.cs64);
+  double* sn64 = (double*)(sm + S.sn64);
+  int* pp = (int*)(sm + S.pp);
+  int* qq = (int*)(sm + S.qq);
+  int* sel = (int*)(sm + S.sel);
+  int* act = (int*)(sm + S.act);
+  double* lam = (double*)(sm + S.lam);
+  double* sh = (double*)(sm + S.sh);
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const long long G = blockIdx.x;
+  // active dofs (compact order = local dof order)
+  for (int d = tid; d < n; d += nt) {
+    const long long c = cell_of_local(prev, cur, G, d / Lp);
+    act[d] = actp[c * Lp + d % Lp];
+  }
+  for (int i = tid; i < n2 * n2; i += nt) C[i] = 0.f;
+  __syncthreads();
+  if (tid == 0) {
+    int na = 0;
+    for (int d = 0; d < n; ++d) na += act[d] ? 1 : 0;
+    sh[34] = na;
+  }
+  __syncthreads();
+  const int na = (int)sh[34];
+  const int kk = na < L ? na : L;
+  // Ã_G = (A_prev)_GG - blockdiag D_c  (inactive dofs: huge diagonal)
+  for (int w = tid; w < n * n; w += nt) {
+    const int di = w / n, dj = w % n;
+    const int lci = di / Lp, i = di % Lp, lcj = dj / Lp, j = dj % Lp;
+    const int dx = lcj % g - lci % g, dy = (lcj / g) % g - (lci / g) % g, dz = lcj / (g * g) - lci / (g * g);
+    double v = 0.0;
+    if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1) {
+      const long long c = cell_of_local(prev, cur, G, lci);
+      v = Tp[((c * 27 + nbr_index(dx, dy, dz)) * Lp + i) * Lp + j];
+      if (lci == lcj) v -= Dc[(c * Lp + i) * Lp + j];
+    }
+    if (!act[di] || !act[dj]) v = (di == dj) ? 3.0e38 : 0.0;
+    C[di * n2 + dj] = (float)v;
+  }
+  for (int i = n + tid; i < n2; i += nt) C[i * n2 + i] = 3.0e38f;
+  __syncthreads();
+  // symmetrise (the FP64 tiles are symmetric up to rounding)
+  for (int w = tid; w < n * n; w += nt) {
+    const int di = w / n, dj = w % n;
+    if (di < dj) {
+      const float v = 0.5f * (C[di * n2 + dj] + C[dj * n2 + di]);
+      C[di * n2 + dj] = v;
+      C[dj * n2 + di] = v;
+    }
+  }
+  __syncthreads();
+  jacobi_eigen<float>(C, V, n2, cs, sn, pp, qq, sh, 14, 3e-7);
+  select_smallest<float>(C, n2, kk, sel);
+  for (int w = tid; w < n * L; w += nt) {
+    const int i = w / L, a = w % L;
+    X[w] = (a < kk && act[i]) ? (double)V[i * n2 + sel[a]] : 0.0;
+  }
+  __syncthreads();
+  mgs(X, nullptr, n, L, kk, sh);
+  // W = Ã_G X in FP64 from the tiles
+  for (int w = tid; w < n * kk; w += nt) {
+    const int di = w / kk, a = w % kk;
+    const int lci = di / Lp, i = di % Lp;
+    const long long c = cell_of_local(prev, cur, G, lci);
+    double s = 0.0;
+    if (act[di]) {
+      for (int lcj = 0; lcj < ng; ++lcj) {
+        const int dx = lcj % g - lci % g, dy = (lcj / g) % g - (lci / g) % g, dz = lcj / (g * g) - lci / (g * g);
+        if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1) continue;
+        const double* T = Tp + ((c * 27 + nbr_index(dx, dy, dz)) * Lp + i) * Lp;
+        for (int j = 0; j < Lp; ++j) {
+          double t = T[j];
+          if (lci == lcj) t -= Dc[(c * Lp + i) * Lp + j];
+          if (act[lcj * Lp + j]) s += t * X[(lcj * Lp + j) * L + a];
+        }
+      }
+    }
+    W[di * L + a] = s;
+  }
+  __syncthreads();
+  if (kk > 0) rr_finish(X, W, n, L, kk, H, Y, cs64, sn64, pp + n2 / 2, qq + n2 / 2, sh, tmp, lam, sel + n2);
+  for (int w = tid; w < n * L; w += nt) {
+    const int i = w / L, a = w % L;
+    Psi[G * (long long)n * L + w] = a < kk ? X[i * L + a] : 0.0;
+  }
+  if (tid < L) {
+    eig[G * L + tid] = tid < kk ? lam[tid] : 0.0;
+    actc[G * L + tid] = tid < kk ? 1 : 0;
+  }
+}
+cudaError_t group_eigen(const CLevel& prev, const CLevel& cur, const double* tiles_prev, const double* Dcorr,
+                        const uint8_t* act_prev, double* Psi, double* eig, uint8_t* act_cur, int* status,
+                        cudaStream_t st) {
+  const int n = cur.g * cur.g * cur.g * prev.L;
+  const int n2 = (n + 1) & ~1;
+  const GSmem S = g_smem(n2, cur.L);
+  if (S.total > 227 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_group_eigen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.total);
+  if (e != cudaSuccess) return e;
+  note_launch(), k_group_eigen<<<(unsigned)cur.ncell, EIG_NT, S.total, st>>>(prev, cur, tiles_prev, Dcorr, act_prev, n2, Psi, eig,
+                                                               act_cur);
+  return cudaGetLastError();
+}
+
+// D_G^(t) = Psi_G^T blockdiag_{c in G}(D_c^(t)) Psi_G for every later level t
+__global__ void k_group_corr(CLevel prev, CLevel cur, const double* __restrict__ Psi, const double* __restrict__ Dp,
+                             double* __restrict__ Dcur, int nt_lv) {
+  const int g = cur.g, Lp = prev.L, L = cur.L, ng = g * g * g, n = ng * Lp;
+  const long long G = blockIdx.x;
+  const double* ps = Psi + G * (long long)n * L;
+  for (int o = threadIdx.x; o < nt_lv * L * L; o += blockDim.x) {
+    const int t = o / (L * L), a = (o / L) % L, bb = o % L;
+    double s = 0.0;
+    for (int lc = 0; lc < ng; ++lc) {
+      const long long c = cell_of_local(prev, cur, G, lc);
+      const double* D = Dp + ((long long)t * prev.ncell + c) * Lp * Lp;
+      for (int i = 0; i < Lp; ++i) {
+        double u = 0.0;
+        for (int j = 0; j < Lp; ++j) u += D[i * Lp + j] * ps[(lc * Lp + j) * L + bb];
+        s += ps[(lc * Lp + i) * L + a] * u;
+      }
+    }
+    Dcur[((long long)t * cur.ncell + G) * L * L + a * L + bb] = s;
+  }
+}
+cudaError_t group_project_corr(const CLevel& prev, const CLevel& cur, const double* Psi, const double* Dprev,
+                               double* Dcur, int nt, cudaStream_t st) {
+  if (nt <= 0) return cudaSuccess;
+  note_launch(), k_group_corr<<<(unsigned)cur.ncell, 128, 0, st>>>(prev, cur, Psi, Dprev + prev.ncell * prev.L * prev.L, Dcur, nt);
+  return cudaGetLastError();
+}
+
+// A_l tiles: tile(G, G') = sum_{c in G, c' in G' adjacent} Psi_G[c]^T T(c,c') Psi_G'[c']
+__global__ void k_group_rap(CLevel prev, CLevel cur, const double* __restrict__ Psi, const double* __restrict__ Tp,
+                            double* __restrict__ T) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int g = cur.g, Lp = prev.L, L = cur.L, ng = g * g * g, n = ng * Lp;
+  double* out = (double*)sm;       // [27][L][L]
+  double* Wt = out + 27 * L * L;   // [Lp][L]
+  const long long G = blockIdx.x;
+  const int gx = (int)(G % cur.mx), gy = (int)((G / cur.mx) % cur.my), gz = (int)(G / ((long long)cur.mx * cur.my));
+  for (int i = threadIdx.x; i < 27 * L * L; i += blockDim.x) out[i] = 0.0;
+  __syncthreads();
+  const double* psG = Psi + G * (long long)n * L;
+  for (int lc = 0; lc < ng; ++lc) {
+    const int lx = lc % g, ly = (lc / g) % g, lz = lc / (g * g);
+    const int cx = gx * g + lx, cy = gy * g + ly, cz = gz * g + lz;
+    const long long c = cx + (long long)prev.mx * (cy + (long long)prev.my * cz);
+    for (int nn = 0; nn < 27; ++nn) {
+      const int dx = nn % 3 - 1, dy = (nn / 3) % 3 - 1, dz = nn / 9 - 1;
+      const int ncx = cx + dx, ncy = cy + dy, ncz = cz + dz;
+      if (ncx < 0 || ncy < 0 || ncz < 0 || ncx >= prev.mx || ncy >= prev.my || ncz >= prev.mz) continue;
+      const int Gx = ncx / g, Gy = ncy / g, Gz = ncz / g;
+      const long long G2 = Gx + (long long)cur.mx * (Gy + (long long)cur.my * Gz);
+      const int lc2 = (ncx % g) + g * ((ncy % g) + g * (ncz % g));
+      const int gn = nbr_index(Gx - gx, Gy - gy, Gz - gz);
+      const double* Tc = Tp + (c * 27 + nn) * Lp * Lp;
+      const double* ps2 = Psi + G2 * (long long)n * L + (long long)lc2 * Lp * L;
+      for (int w = threadIdx.x; w < Lp * L; w += blockDim.x) {
+        const int i = w / L, bb = w % L;
+        double s = 0.0;
+        for (int j = 0; j < Lp; ++j) s += Tc[i * Lp + j] * ps2[j * L + bb];
+        Wt[w] = s;
+      }
+      __syncthreads();
+      for (int w = threadIdx.x; w < L * L; w += blockDim.x) {
+        const int a = w / L, bb = w % L;
+        double s = 0.0;
+        for (int i = 0; i < Lp; ++i) s += psG[(lc * Lp + i) * L + a] * Wt[i * L + bb];
+        out[gn * L * L + w] += s;
+      }
+      __syncthreads();
+    }
+  }
+  for (int i = threadIdx.x; i < 27 * L * L; i += blockDim.x) T[G * 27 * L * L + i] = out[i];
+}
+cudaError_t group_rap(const CLevel& prev, const CLevel& cur, const double* Psi, const double* tiles_prev, double* tiles,
+                      cudaStream_t st) {
+  const size_t sm = (27 * (size_t)cur.L * cur.L + (size_t)prev.L * cur.L) * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(k_group_rap, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  note_launch(), k_group_rap<<<(unsigned)cur.ncell, 256, sm, st>>>(prev, cur, Psi, tiles_prev, tiles);
+  return cudaGetLastError();
+}
+
+// inactive dofs (zero basis vectors) get an identity row in the centre tile
+__global__ void k_fix_inactive(CLevel lv, const uint8_t* __restrict__ act, double* __restrict__ T) {
+  const long long nd = lv.ncell * lv.L;
+  for (long long d = blockIdx.x * (long long)blockDim.x + threadIdx.x; d < nd; d += (long long)gridDim.x * blockDim.x) {
+    if (act[d]) continue;
+    const long long c = d / lv.L;
+    const int i = (int)(d % lv.L);
+    T[((c * 27 + 13) * lv.L + i) * lv.L + i] = 1.0;
+  }
+}
+cudaError_t fix_inactive(const CLevel& lv, const uint8_t* act, double* tiles, cudaStream_t st) {
+  const long long nd = lv.ncell * lv.L;
+  note_launch(), k_fix_inactive<<<(unsigned)((nd + 255) / 256), 256, 0, st>>>(lv, act, tiles);
+  return cudaGetLastError();
+}
+
+// l1-block-Jacobi: inverse of (A_cc + diag(sum_{off-cell} |a_ij|)), FP64 Gauss-Jordan
+__global__ void k_l1inv(CLevel lv, const double* __restrict__ T, double* __restrict__ Di64, float* __restrict__ Di32) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  const int L = lv.L;
+  double* M = (double*)sm + threadIdx.x * 2 * L * L;  // [L][2L] augmented
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= lv.ncell) return;
+  for (int i = 0; i < L; ++i) {
+    double off = 0.0;
+    for (int n = 0; n < 27; ++n) {
+      if (n == 13) continue;
+      const double* row = T + ((c * 27 + n) * L + i) * L;
+      for (int j = 0; j < L; ++j) off += fabs(row[j]);
+    }
+    const double* row = T + ((c * 27 + 13) * L + i) * L;
+    for (int j = 0; j < L; ++j) {
+      M[i * 2 * L + j] = row[j] + (i == j ? off : 0.0);
+      M[i * 2 * L + L + j] = i == j ? 1.0 : 0.0;
+    }
+  }
+  for (int k = 0; k < L; ++k) {
+    int piv = k;
+    for (int i = k + 1; i < L; ++i)
+      if (fabs(M[i * 2 * L + k]) > fabs(M[piv * 2 * L + k])) piv = i;
+    if (piv != k)
+      for (int j = 0; j < 2 * L; ++j) {
+        const double t = M[k * 2 * L + j];
+        M[k * 2 * L + j] = M[piv * 2 * L + j];
+        M[piv * 2 * L + j] = t;
+      }
+    const double d = M[k * 2 * L + k];
+    const double inv = d != 0.0 ? 1.0 / d : 0.0;
+    for (int j = 0; j < 2 * L; ++j) M[k * 2 * L + j] *= inv;
+    for (int i = 0; i < L; ++i) {
+      if (i == k) continue;
+      const double f = M[i * 2 * L + k];
+      if (f != 0.0)
+        for (int j = 0; j < 2 * L; ++j) M[i * 2 * L + j] -= f * M[k * 2 * L + j];
+    }
+  }
+  for (int i = 0; i < L; ++i)
+    for (int j = 0; j < L; ++j) {
+      const double v = M[i * 2 * L + L + j];
+      Di64[(c * L + i) * L + j] = v;
+      Di32[(c * L + i) * L + j] = (float)v;
+    }
+}
+cudaError_t l1_inverse(const CLevel& lv, const double* tiles, double* Dinv64, float* Dinv32, cudaStream_t st) {
+  int nt = 64;
+  size_t per = 2 * (size_t)lv.L * lv.L * sizeof(double);
+  while (nt > 1 && per * nt > 96 * 1024) nt >>= 1;
+  const size_t sm = per * nt;
+  cudaError_t e = cudaFuncSetAttribute(k_l1inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  note_launch(), k_l1inv<<<(unsigned)((lv.ncell + nt - 1) / nt), nt, sm, st>>>(lv, tiles, Dinv64, Dinv32);
+  return cudaGetLastError();
+}
+
+// dense coarsest operator A[(c,i)][(c',j)]
+__global__ void k_dense(CLevel lv, const double* __restrict__ T, double* __restrict__ A) {
+  const long long N = lv.ncell * lv.L;
+  for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < N * N; w += (long long)gridDim.x * blockDim.x) {
+    const long long r = w / N, col = w % N;
+    const long long c = r / lv.L, c2 = col / lv.L;
+    const int i = (int)(r % lv.L), j = (int)(col % lv.L);
+    const int cx = (int)(c % lv.mx), cy = (int)((c / lv.mx) % lv.my), cz = (int)(c / ((long long)lv.mx * lv.my));
+    const int dx = (int)(c2 % lv.mx) - cx, dy = (int)((c2 / lv.mx) % lv.my) - cy,
+              dz = (int)(c2 / ((long long)lv.mx * lv.my)) - cz;
+    double v = 0.0;
+    if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1)
+      v = T[((c * 27 + nbr_index(dx, dy, dz)) * lv.L + i) * lv.L + j];
+    A[w] = v;
+  }
+}
+cudaError_t dense_assemble(const CLevel& lv, const double* tiles, double* A, cudaStream_t st) {
+  const long long N = lv.ncell * lv.L;
+  long long nb = (N * N + 255) / 256;
+  if (nb > 152 * 64) nb = 152 * 64;
+  note_launch(), k_dense<<<(unsigned)nb, 256, 0, st>>>(lv, tiles, A);
+  return cudaGetLastError();
+}
+
+// Right-looking Cholesky (lower), one column per step; then A^-1 column by
+// column with forward/back substitution.  Symmetrised input.
+__global__ void k_symm(int n, double* A) {
+  for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < (long long)n * n;
+       w += (long long)gridDim.x * blockDim.x) {
+    const int i = (int)(w / n), j = (int)(w % n);
+    if (i > j) {
+      const double v = 0.5 * (A[(long long)i * n + j] + A[(long long)j * n + i]);
+      A[(long long)i * n + j] = v;
+      A[(long long)j * n + i] = v;
+    }
+  }
+}
+__global__ void k_chol_col(int n, int k, double* A, int* status) {
+  __shared__ double dk;
+  if (threadIdx.x == 0) {
+    const double d = A[(long long)k * n + k];
+    if (!(d > 0.0) || !isfinite(d)) {
+      atomicExch(status, k + 1);
+      dk = 1.0;
+    } else {
+      dk = sqrt(d);
+    }
+  }
+  __syncthreads();
+  const double d = dk;
+  for (int i = k + threadIdx.x + blockIdx.x * blockDim.x; i < n; i += blockDim.x * gridDim.x) {
+    if (i == k)
+      A[(long long)k * n + k] = d;
+    else
+      A[(long long)i * n + k] /= d;
+  }
+}
+__global__ void k_chol_update(int n, int k, double* A) {
+  // A[i][j] -= L[i][k] L[j][k] for k < j <= i
+  const long long m = n - k - 1;
+  for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < m * m; w += (long long)gridDim.x * blockDim.x) {
+    const int i = k + 1 + (int)(w / m), j = k + 1 + (int)(w % m);
+    if (j > i) continue;
+    A[(long long)i * n + j] -= A[(long long)i * n + k] * A[(long long)j * n + k];
+  }
+}
+// X[:, col] = A^-1 e_col using the lower factor Lf (row-major, lower part)
+__global__ void k_chol_inv(int n, const double* __restrict__ Lf, double* __restrict__ X) {
+  extern __shared__ __align__(16) unsigned char sm[];
+  double* y = (double*)sm;
+  const int col = blockIdx.x;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = (i == col) ? 1.0 : 0.0;
+  __syncthreads();
+  for (int i = 0; i < n; ++i) {  // forward: L y = e
+    const double yi = y[i] / Lf[(long long)i * n + i];
+    __syncthreads();
+    if (threadIdx.x == 0) y[i] = yi;
+    for (int k = i + 1 + threadIdx.x; k < n; k += blockDim.x) y[k] -= Lf[(long long)k * n + i] * yi;
+    __syncthreads();
+  }
+  for (int i = n - 1; i >= 0; --i) {  // backward: L^T x = y
+    const double xi = y[i] / Lf[(long long)i * n + i];
+    __syncthreads();
+    if (threadIdx.x == 0) y[i] = xi;
+    for (int k = threadIdx.x; k < i; k += blockDim.x) y[k] -= Lf[(long long)i * n + k] * xi;
+    __syncthreads();
+  }
+  for (int i = threadIdx.x; i < n; i += blockDim.x) X[(long long)i * n + col] = y[i];
+}
+cudaError_t cholesky_inverse(int n, double* A, double* work, int* status, cudaStream_t st) {
+  long long nb = ((long long)n * n + 255) / 256;
+  if (nb > 152 * 32) nb = 152 * 32;
+  note_launch(), k_symm<<<(unsigned)nb, 256, 0, st>>>(n, A);
+  for (int k = 0; k < n; ++k) {
+    note_launch(), k_chol_col<<<1, 256, 0, st>>>(n, k, A, status);
+    const long long m = (long long)(n - k - 1) * (n - k - 1);
+    if (m > 0) {
+      long long b2 = (m + 255) / 256;
+      if (b2 > 152 * 16) b2 = 152 * 16;
+      note_launch(), k_chol_update<<<(unsigned)b2, 256, 0, st>>>(n, k, A);
+    }
+  }
+  const size_t sm = (size_t)n * sizeof(double);
+  cudaError_t e = cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  if (e != cudaSuccess) return e;
+  note_launch(), k_chol_inv<<<n, 256, sm, st>>>(n, A, work);
+  return cudaGetLastError();
+}
+
+__global__ void k_cvt(const double* __restrict__ a, float* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = (float)a[i];
+}
+cudaError_t cvt_f64_f32(const double* a, float* b, long long n, cudaStream_t st) {
+  long long nb = (n + 255) / 256;
+  if (nb > 152 * 32) nb = 152 * 32;
+  if (nb < 1) nb = 1;
+  note_launch(), k_cvt<<<(unsigned)nb, 256, 0, st>>>(a, b, n);
+  return cudaGetLastError();
+}
+
+__global__ void k_phi_nat(Geom g, const double* __restrict__ phi, int L, double* __restrict__ out) {
+  const long long n = (long long)g.nx * g.ny * g.nz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % g.nx);
+    const long long t = i / g.nx;
+    const int y = (int)(t % g.ny), z = (int)(t / g.ny);
+    const long long nd = nidx(g, x, y, z);
+    for (int a = 0; a < L; ++a) out[i * L + a] = phi[nd * L + a];
+  }
+}
+cudaError_t phi_natural(const Geom& g, const double* phi_pad, int L1, double* out, cudaStream_t st) {
+  const long long n = (long long)g.nx * g.ny * g.nz;
+  long long nb = (n + 255) / 256;
+  if (nb > 152 * 32) nb = 152 * 32;
+  note_launch(), k_phi_nat<<<(unsigned)nb, 256, 0, st>>>(g, phi_pad, L1, out);
+  return cudaGetLastError();
+}
+
+}  // namespace thermo

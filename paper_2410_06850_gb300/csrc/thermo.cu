@@ -1,0 +1,988 @@
+// Host orchestration and the C ABI of libthermo (see include/thermo.h).
+//
+// The context owns every device buffer in the padded layout of common.cuh.
+// Solve = FP64 (flexible) preconditioned CG (Sec. 4) around the multigrid
+// cycle of Algorithm 1 (Sec. 3), generalised to the context's number of
+// levels; all per-iteration work runs in this library's kernels, with one
+// host readback of the device scalars per convergence check.
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/thermo.h"
+#include "common.cuh"
+#include "kernels.h"
+
+using namespace thermo;
+
+namespace thermo {
+static long long g_launches = 0;
+void note_launch() { ++g_launches; }
+long long launch_count() { return g_launches; }
+}  // namespace thermo
+
+namespace {
+
+struct Lev {
+  CLevel cl;
+  double* T64 = nullptr;   // Galerkin tiles [ncell][27][L][L]
+  float* T32 = nullptr;
+  double* Di64 = nullptr;  // l1 block inverses [ncell][L][L]
+  float* Di32 = nullptr;
+  double* Psi64 = nullptr; // (l >= 2) [ncell][g^3 Lprev][L]
+  float* Psi32 = nullptr;
+  uint8_t* act = nullptr;
+  double* eig = nullptr;
+  double* Dc = nullptr;    // row-sum corrections for later levels [nt][ncell][L][L]
+  int ntc = 0;
+  // cycle vectors (FP64 form and FP32 form)
+  double *r64 = nullptr, *e64 = nullptr, *t64 = nullptr, *s64 = nullptr;
+  float *r32 = nullptr, *e32 = nullptr, *t32 = nullptr, *s32 = nullptr;
+};
+
+}  // namespace
+
+struct thermo_ctx {
+  std::string err;
+  cudaStream_t st = nullptr;
+  thermo_options opt;
+  Geom g;
+  int L1 = 4;
+  long long nnode = 0, nelem = 0;
+  std::vector<void*> allocs;
+  // fine data
+  uint32_t* bits = nullptr;
+  double* k64 = nullptr;
+  float* k32 = nullptr;
+  bf16* k16 = nullptr;
+  double* xd = nullptr;     // design copy (natural)
+  double *f = nullptr, *blift = nullptr, *TD = nullptr, *zero64 = nullptr;
+  double *u = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *bv = nullptr, *tmp = nullptr, *z64 = nullptr;
+  double *ea64 = nullptr, *eb64 = nullptr;
+  float *r32 = nullptr, *z32 = nullptr, *ea32 = nullptr, *eb32 = nullptr, *tmp32 = nullptr;
+  bf16 *r16 = nullptr, *ea16 = nullptr, *eb16 = nullptr;
+  double* phi64 = nullptr;
+  float* phi32 = nullptr;
+  // levels 1..nlev (index 0 unused)
+  int nlev = 0;
+  Lev lev[THERMO_MAX_LEVELS + 1];
+  double* Ainv = nullptr;
+  double* cholA = nullptr;
+  int ncoarse = 0;
+  int* gcum_dev = nullptr;
+  // scalars and reductions
+  CgScalars* sc = nullptr;
+  CgScalars* sc_h = nullptr;  // pinned
+  Reducer red;
+  int* status_dev = nullptr;
+  int* status_h = nullptr;     // pinned
+  double* dscal = nullptr;     // device scratch scalars [16]
+  double* dscal_h = nullptr;   // pinned
+  bool have_density = false, have_precond = false;
+  double sp = 3, skmin = 1e-3, skmax = 1;
+  double t_setup_ms = 0.0;
+  int ndir = 0;
+  double* colsum = nullptr;    // filter column sums (OC)
+  double* xnew = nullptr;
+  double rmin_cs = -1.0;
+};
+
+static thermo_status fail(thermo_ctx* c, thermo_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  return s;
+}
+#define CK(call)                                                                              \
+  do {                                                                                        \
+    cudaError_t e_ = (call);                                                                  \
+    if (e_ != cudaSuccess)                                                                    \
+      return fail(ctx, THERMO_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                  __FILE__, __LINE__);                                                        \
+  } while (0)
+
+template <class T>
+static cudaError_t dalloc(thermo_ctx* ctx, T** p, size_t n) {
+  void* v = nullptr;
+  cudaError_t e = cudaMalloc(&v, n * sizeof(T) + 64);
+  if (e != cudaSuccess) return e;
+  ctx->allocs.push_back(v);
+  e = cudaMemsetAsync(v, 0, n * sizeof(T) + 64, ctx->st);
+  *p = (T*)v;
+  return e;
+}
+
+static double now_ms() {
+  return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
+}
+
+// ---------------------------------------------------------------------------
+extern "C" thermo_status thermo_default_options(const int grid[3], thermo_options* opt) {
+  if (!grid || !opt) return THERMO_EINVAL;
+  memset(opt, 0, sizeof(*opt));
+  for (int k = 0; k < 3; ++k)
+    if (grid[k] <= 0 || grid[k] % 4) return THERMO_EINVAL;
+  int m = grid[0] / 4;
+  for (int k = 1; k < 3; ++k) m = grid[k] / 4 < m ? grid[k] / 4 : m;
+  int lv = 1;
+  std::vector<int> groups;
+  while (m > 4 && m % 2 == 0 && lv < THERMO_MAX_LEVELS) {
+    m /= 2;
+    ++lv;
+  }
+  opt->levels = lv;
+  opt->block = 4;
+  opt->nvec[0] = 4;
+  for (int l = 1; l < lv; ++l) {
+    opt->group[l] = 2;
+    opt->nvec[l] = (l == 1 && lv > 2) ? 8 : 17;
+  }
+  opt->nu_fine = 2;
+  opt->nu_coarse = 1;
+  opt->omega = 2.0 / 3.0;
+  opt->prec = THERMO_MIXED;
+  opt->pc = THERMO_PC_MMG;
+  opt->guess = THERMO_GUESS_COARSE;
+  opt->max_iter = 10000;
+  opt->flexible = -1;
+  opt->check_every = 1;
+  return THERMO_OK;
+}
+
+static int pick_tile(int N, int b, int maxt) {
+  for (int t = maxt - maxt % b; t >= b; t -= b)
+    if (N % t == 0) return t;
+  return 0;
+}
+
+extern "C" thermo_status thermo_create(const int grid[3], const double h[3], const uint8_t* mask, const double* dval,
+                                       const double* source, void* stream, const thermo_options* opt_in,
+                                       thermo_ctx** out) {
+  if (!out) return THERMO_EINVAL;
+  *out = nullptr;
+  if (!grid || !h || !mask || !source) return THERMO_EINVAL;
+  thermo_options opt;
+  if (opt_in)
+    opt = *opt_in;
+  else if (thermo_default_options(grid, &opt) != THERMO_OK)
+    return THERMO_EINVAL;
+  thermo_ctx* ctx = new (std::nothrow) thermo_ctx();
+  if (!ctx) return THERMO_ENOMEM;
+  *out = ctx;
+  ctx->st = (cudaStream_t)stream;
+  ctx->opt = opt;
+  for (int k = 0; k < 3; ++k) {
+    if (grid[k] <= 0 || !(h[k] > 0.0)) return fail(ctx, THERMO_EINVAL, "grid and h must be positive");
+  }
+  const int b = opt.block;
+  if (b < 2 || b > 8) return fail(ctx, THERMO_EINVAL, "block must be in [2, 8]");
+  if (opt.levels < 1 || opt.levels > THERMO_MAX_LEVELS) return fail(ctx, THERMO_EINVAL, "levels out of range");
+  if (grid[0] % b || grid[1] % b || grid[2] % b) return fail(ctx, THERMO_EINVAL, "grid must be a multiple of block");
+  if (opt.nu_fine < 1 || opt.nu_coarse < 1) return fail(ctx, THERMO_EINVAL, "smoothing sweeps must be >= 1");
+  if (opt.nvec[0] < 1 || opt.nvec[0] > 8 || opt.nvec[0] == 7)
+    return fail(ctx, THERMO_EINVAL, "nvec[0] must be in {1..6, 8}");
+  Geom& g = ctx->g;
+  memset(&g, 0, sizeof(g));
+  g.Nx = grid[0];
+  g.Ny = grid[1];
+  g.Nz = grid[2];
+  g.nx = g.Nx + 1;
+  g.ny = g.Ny + 1;
+  g.nz = g.Nz + 1;
+  g.P = ((g.Nx + 3 + 31) / 32) * 32;
+  g.RYn = g.Ny + 3;
+  g.RYe = g.Ny + 2;
+  g.base = 32;
+  g.nsize = g.base + (long long)(g.nz + 2) * g.RYn * g.P + 64;
+  g.esize = g.base + (long long)(g.Nz + 2) * g.RYe * g.P + 64;
+  g.mwr = g.P / 32;
+  g.msize = (long long)(g.nz + 2) * g.RYn * g.mwr + 8;
+  {
+    // K0[a][b] = c[a ^ b] from the Kronecker form (k (x) m (x) m etc.)
+    const double hx = h[0], hy = h[1], hz = h[2];
+    const double ax = hy * hz / hx, ay = hx * hz / hy, az = hx * hy / hz;
+    for (int pat = 0; pat < 8; ++pat) {
+      const int px = pat & 1, py = (pat >> 1) & 1, pz = (pat >> 2) & 1;
+      auto k1 = [](int d) { return d ? -1.0 : 1.0; };
+      auto m1 = [](int d) { return d ? 1.0 / 6.0 : 1.0 / 3.0; };
+      g.c[pat] = ax * k1(px) * m1(py) * m1(pz) + ay * m1(px) * k1(py) * m1(pz) + az * m1(px) * m1(py) * k1(pz);
+    }
+    g.cube = (fabs(g.c[1]) <= 1e-14 * fabs(g.c[0]) && fabs(g.c[2]) <= 1e-14 * fabs(g.c[0]) &&
+              fabs(g.c[4]) <= 1e-14 * fabs(g.c[0]) && fabs(g.c[3] - g.c[7]) <= 1e-14 * fabs(g.c[0]) &&
+              fabs(g.c[5] - g.c[7]) <= 1e-14 * fabs(g.c[0]) && fabs(g.c[6] - g.c[7]) <= 1e-14 * fabs(g.c[0]))
+                 ? 1
+                 : 0;
+    if (g.cube) {
+      g.c[1] = g.c[2] = g.c[4] = 0.0;
+      g.c[3] = g.c[5] = g.c[6] = g.c[7];
+    }
+    g.vol = hx * hy * hz;
+  }
+  g.b = b;
+  g.nbx = g.Nx / b;
+  g.nby = g.Ny / b;
+  g.nbz = g.Nz / b;
+  g.TX = pick_tile(g.Nx, b, 32);
+  g.TY = pick_tile(g.Ny, b, 8);
+  g.ZC = 0;
+  for (int zc : {32, 16, 8, 4, 2}) {
+    if (zc % b == 0 && g.Nz % zc == 0 && (g.Nz >= 4 * zc || zc == b)) {
+      g.ZC = zc;
+      break;
+    }
+  }
+  if (!g.ZC) g.ZC = pick_tile(g.Nz, b, g.Nz);
+  if (!g.TX || !g.TY || !g.ZC) return fail(ctx, THERMO_EINVAL, "unsupported grid / block combination");
+  ctx->L1 = opt.nvec[0];
+  ctx->nnode = (long long)g.nx * g.ny * g.nz;
+  ctx->nelem = (long long)g.Nx * g.Ny * g.Nz;
+  // hierarchy shape
+  ctx->nlev = opt.levels;
+  {
+    int mx = g.nbx, my = g.nby, mz = g.nbz;
+    for (int l = 1; l <= ctx->nlev; ++l) {
+      CLevel& cl = ctx->lev[l].cl;
+      if (l >= 2) {
+        const int gg = opt.group[l - 1];
+        if (gg < 1 || mx % gg || my % gg || mz % gg)
+          return fail(ctx, THERMO_EINVAL, "level %d: cells not divisible by group %d", l, gg);
+        mx /= gg;
+        my /= gg;
+        mz /= gg;
+        cl.g = gg;
+      } else {
+        cl.g = 1;
+      }
+      cl.mx = mx;
+      cl.my = my;
+      cl.mz = mz;
+      cl.L = opt.nvec[l - 1];
+      cl.ncell = (long long)mx * my * mz;
+      if (cl.L < 1 || cl.L > 32) return fail(ctx, THERMO_EINVAL, "nvec out of range at level %d", l);
+      if (l >= 2) {
+        const int n = cl.g * cl.g * cl.g * ctx->lev[l - 1].cl.L;
+        if (n > 180) return fail(ctx, THERMO_EINVAL, "level %d local eigenproblem too large (%d > 180)", l, n);
+      }
+    }
+    const CLevel& top = ctx->lev[ctx->nlev].cl;
+    ctx->ncoarse = (int)(top.ncell * top.L);
+    if (ctx->ncoarse > 20000) return fail(ctx, THERMO_EINVAL, "coarsest level too large (%d)", ctx->ncoarse);
+  }
+  // allocations
+  const long long ns = g.nsize, es = g.esize;
+  CK(dalloc(ctx, &ctx->bits, g.msize));
+  CK(dalloc(ctx, &ctx->k64, es));
+  CK(dalloc(ctx, &ctx->k32, es));
+  CK(dalloc(ctx, &ctx->k16, es));
+  CK(dalloc(ctx, &ctx->xd, ctx->nelem));
+  for (double** pp : {&ctx->f, &ctx->blift, &ctx->TD, &ctx->zero64, &ctx->u, &ctx->r, &ctx->p, &ctx->q, &ctx->bv,
+                      &ctx->tmp})
+    CK(dalloc(ctx, pp, ns));
+  if (opt.prec == THERMO_FP64 || opt.pc != THERMO_PC_MMG) {
+    CK(dalloc(ctx, &ctx->z64, ns));
+  }
+  CK(dalloc(ctx, &ctx->ea64, ns));
+  CK(dalloc(ctx, &ctx->eb64, ns));
+  for (float** pp : {&ctx->r32, &ctx->z32, &ctx->ea32, &ctx->eb32, &ctx->tmp32}) CK(dalloc(ctx, pp, ns));
+  if (opt.prec == THERMO_MIXED_BF16S) {
+    for (bf16** pp : {&ctx->r16, &ctx->ea16, &ctx->eb16}) CK(dalloc(ctx, pp, ns));
+  }
+  CK(dalloc(ctx, &ctx->phi64, ns * ctx->L1));
+  CK(dalloc(ctx, &ctx->phi32, ns * ctx->L1));
+  for (int l = 1; l <= ctx->nlev; ++l) {
+    Lev& lv = ctx->lev[l];
+    const CLevel& cl = lv.cl;
+    const long long nd = cl.ncell * cl.L;
+    const long long nt = cl.ncell * 27 * cl.L * cl.L;
+    CK(dalloc(ctx, &lv.T64, nt));
+    if (l < ctx->nlev) CK(dalloc(ctx, &lv.T32, nt));
+    CK(dalloc(ctx, &lv.Di64, cl.ncell * cl.L * cl.L));
+    CK(dalloc(ctx, &lv.Di32, cl.ncell * cl.L * cl.L));
+    if (l >= 2) {
+      const long long np = cl.ncell * (long long)cl.g * cl.g * cl.g * ctx->lev[l - 1].cl.L * cl.L;
+      CK(dalloc(ctx, &lv.Psi64, np));
+      CK(dalloc(ctx, &lv.Psi32, np));
+    }
+    CK(dalloc(ctx, &lv.act, nd));
+    CK(dalloc(ctx, &lv.eig, nd));
+    lv.ntc = ctx->nlev - l;
+    if (lv.ntc > 0) CK(dalloc(ctx, &lv.Dc, (long long)lv.ntc * cl.ncell * cl.L * cl.L));
+    for (double** pp : {&lv.r64, &lv.e64, &lv.t64, &lv.s64}) CK(dalloc(ctx, pp, nd));
+    for (float** pp : {&lv.r32, &lv.e32, &lv.t32, &lv.s32}) CK(dalloc(ctx, pp, nd));
+  }
+  CK(dalloc(ctx, &ctx->Ainv, (long long)ctx->ncoarse * ctx->ncoarse));
+  CK(dalloc(ctx, &ctx->cholA, (long long)ctx->ncoarse * ctx->ncoarse));
+  {
+    std::vector<int> gc(THERMO_MAX_LEVELS, 1);
+    int acc = 1;
+    for (int l = 2; l <= ctx->nlev; ++l) {
+      acc *= ctx->lev[l].cl.g;
+      gc[l - 2] = acc;
+    }
+    CK(dalloc(ctx, &ctx->gcum_dev, THERMO_MAX_LEVELS));
+    CK(cudaMemcpyAsync(ctx->gcum_dev, gc.data(), THERMO_MAX_LEVELS * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
+  }
+  CK(dalloc(ctx, &ctx->sc, 1));
+  CK(dalloc(ctx, &ctx->dscal, 16));
+  CK(dalloc(ctx, &ctx->status_dev, 4));
+  {
+    const unsigned nf = fine_num_ctas(g);
+    const long long np = (long long)(nf > 8192 ? nf : 8192) * 2;
+    CK(dalloc(ctx, &ctx->red.partial, np));
+    CK(dalloc(ctx, &ctx->red.counter, 4));
+    ctx->red.nblocks = (int)np;
+  }
+  CK(cudaMallocHost((void**)&ctx->sc_h, sizeof(CgScalars)));
+  CK(cudaMallocHost((void**)&ctx->status_h, 4 * sizeof(int)));
+  CK(cudaMallocHost((void**)&ctx->dscal_h, 16 * sizeof(double)));
+  // boundary data and load
+  CK(mask_to_bits(g, mask, ctx->bits, ctx->st));
+  CK(count_mask(g, mask, ctx->nnode, ctx->status_dev + 3, ctx->st));
+  CK(cudaMemcpyAsync(ctx->status_h, ctx->status_dev, 4 * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  ctx->ndir = ctx->status_h[3];
+  if (ctx->ndir == 0) return fail(ctx, THERMO_EINVAL, "empty Dirichlet set: the operator is singular");
+  if (dval) CK(pack_nodes(g, dval, ctx->TD, ctx->st));
+  CK(load_vector(g, source, ctx->f, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return THERMO_OK;
+}
+
+extern "C" void thermo_destroy(thermo_ctx* ctx) {
+  if (!ctx) return;
+  if (ctx->st) cudaStreamSynchronize(ctx->st);
+  for (void* v : ctx->allocs) cudaFree(v);
+  if (ctx->sc_h) cudaFreeHost(ctx->sc_h);
+  if (ctx->status_h) cudaFreeHost(ctx->status_h);
+  if (ctx->dscal_h) cudaFreeHost(ctx->dscal_h);
+  delete ctx;
+}
+
+extern "C" const char* thermo_last_error(const thermo_ctx* ctx) {
+  if (!ctx) return "null context";
+  return ctx->err.c_str();
+}
+
+extern "C" thermo_status thermo_set_density(thermo_ctx* ctx, const double* x, double p, double kmin, double kmax) {
+  if (!ctx) return THERMO_EINVAL;
+  if (!x) return fail(ctx, THERMO_EINVAL, "x is NULL");
+  if (!(p >= 1.0) || !(kmin > 0.0) || !(kmax >= kmin) || !std::isfinite(kmax))
+    return fail(ctx, THERMO_EINVAL, "need p >= 1 and 0 < kmin <= kmax");
+  CK(cudaMemcpyAsync(ctx->xd, x, ctx->nelem * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+  CK(simp_kappa(ctx->g, ctx->xd, p, kmin, kmax, ctx->k64, ctx->k32, ctx->k16, ctx->st));
+  // lifted right-hand side b = f - A_FD T_D (b_D = T_D)
+  CK(dirichlet_rhs(ctx->g, ctx->bits, ctx->k64, ctx->f, ctx->TD, ctx->blift, ctx->st));
+  ctx->sp = p;
+  ctx->skmin = kmin;
+  ctx->skmax = kmax;
+  ctx->have_density = true;
+  ctx->have_precond = false;
+  return THERMO_OK;
+}
+
+// ---------------------------------------------------------------------------
+// preconditioner set-up (Sec. 3)
+extern "C" thermo_status thermo_setup_precond(thermo_ctx* ctx) {
+  if (!ctx) return THERMO_EINVAL;
+  if (!ctx->have_density) return fail(ctx, THERMO_ESTATE, "setup_precond before set_density");
+  cudaStream_t st = ctx->st;
+  const double t0 = now_ms();
+  if (ctx->opt.pc != THERMO_PC_MMG) {
+    ctx->have_precond = true;
+    ctx->t_setup_ms = 0.0;
+    return THERMO_OK;
+  }
+  const Geom& g = ctx->g;
+  const int L1 = ctx->L1;
+  CK(cudaMemsetAsync(ctx->status_dev, 0, 4 * sizeof(int), st));
+  Lev& l1 = ctx->lev[1];
+  CK(level1_eigen(g, ctx->bits, ctx->k64, L1, ctx->phi64, l1.eig, l1.act, ctx->status_dev, st));
+  CK(level1_rowsum_corr(g, ctx->bits, ctx->k64, L1, ctx->phi64, l1.ntc, ctx->gcum_dev, l1.Dc, st));
+  CK(level1_rap(g, ctx->bits, ctx->k64, L1, ctx->phi64, l1.T64, st));
+  CK(fix_inactive(l1.cl, l1.act, l1.T64, st));
+  for (int l = 2; l <= ctx->nlev; ++l) {
+    Lev& pv = ctx->lev[l - 1];
+    Lev& cu = ctx->lev[l];
+    CK(group_eigen(pv.cl, cu.cl, pv.T64, pv.Dc, pv.act, cu.Psi64, cu.eig, cu.act, ctx->status_dev, st));
+    if (cu.ntc > 0) CK(group_project_corr(pv.cl, cu.cl, cu.Psi64, pv.Dc, cu.Dc, cu.ntc, st));
+    CK(group_rap(pv.cl, cu.cl, cu.Psi64, pv.T64, cu.T64, st));
+    CK(fix_inactive(cu.cl, cu.act, cu.T64, st));
+    const long long np = cu.cl.ncell * (long long)cu.cl.g * cu.cl.g * cu.cl.g * pv.cl.L * cu.cl.L;
+    CK(cvt_f64_f32(cu.Psi64, cu.Psi32, np, st));
+  }
+  for (int l = 1; l < ctx->nlev; ++l) {
+    Lev& lv = ctx->lev[l];
+    CK(l1_inverse(lv.cl, lv.T64, lv.Di64, lv.Di32, st));
+    CK(cvt_f64_f32(lv.T64, lv.T32, lv.cl.ncell * 27 * lv.cl.L * lv.cl.L, st));
+  }
+  CK(cvt_f64_f32(ctx->phi64, ctx->phi32, g.nsize * L1, st));
+  CK(dense_assemble(ctx->lev[ctx->nlev].cl, ctx->lev[ctx->nlev].T64, ctx->cholA, st));
+  CK(cholesky_inverse(ctx->ncoarse, ctx->cholA, ctx->Ainv, ctx->status_dev, st));
+  CK(cudaMemcpyAsync(ctx->status_h, ctx->status_dev, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  ctx->t_setup_ms = now_ms() - t0;
+  if (ctx->status_h[0] != 0)
+    return fail(ctx, THERMO_ESINGULAR, "coarsest Cholesky: non-positive pivot at %d", ctx->status_h[0] - 1);
+  ctx->have_precond = true;
+  return THERMO_OK;
+}
+
+// ---------------------------------------------------------------------------
+// coarse part of the cycle on levels l..nlev, input lev[l].r, output lev[l].e
+template <class T>
+static T* lvr(Lev& l);
+template <>
+double* lvr<double>(Lev& l) { return l.r64; }
+template <>
+float* lvr<float>(Lev& l) { return l.r32; }
+template <class T>
+static T* lve(Lev& l);
+template <>
+double* lve<double>(Lev& l) { return l.e64; }
+template <>
+float* lve<float>(Lev& l) { return l.e32; }
+template <class T>
+static T* lvt(Lev& l);
+template <>
+double* lvt<double>(Lev& l) { return l.t64; }
+template <>
+float* lvt<float>(Lev& l) { return l.t32; }
+template <class T>
+static T* lvs(Lev& l);
+template <>
+double* lvs<double>(Lev& l) { return l.s64; }
+template <>
+float* lvs<float>(Lev& l) { return l.s32; }
+template <class T>
+static const T* lvT(Lev& l);
+template <>
+const double* lvT<double>(Lev& l) { return l.T64; }
+template <>
+const float* lvT<float>(Lev& l) { return l.T32; }
+template <class T>
+static const T* lvD(Lev& l);
+template <>
+const double* lvD<double>(Lev& l) { return l.Di64; }
+template <>
+const float* lvD<float>(Lev& l) { return l.Di32; }
+template <class T>
+static const T* lvP(Lev& l);
+template <>
+const double* lvP<double>(Lev& l) { return l.Psi64; }
+template <>
+const float* lvP<float>(Lev& l) { return l.Psi32; }
+
+template <class T>
+static cudaError_t coarse_cycle(thermo_ctx* ctx, int l) {
+  cudaStream_t st = ctx->st;
+  Lev& lv = ctx->lev[l];
+  cudaError_t e;
+  if (l == ctx->nlev) return dense_gemv<T>(ctx->ncoarse, ctx->Ainv, lvr<T>(lv), lve<T>(lv), st);
+  const int nu = ctx->opt.nu_coarse;
+  T* E = lve<T>(lv);
+  T* Tt = lvt<T>(lv);
+  if ((e = coarse_smooth0<T>(lv.cl, lvD<T>(lv), lvr<T>(lv), E, st)) != cudaSuccess) return e;
+  for (int s = 1; s < nu; ++s) {
+    if ((e = coarse_smooth<T>(lv.cl, lvT<T>(lv), lvD<T>(lv), lvr<T>(lv), E, Tt, st)) != cudaSuccess) return e;
+    std::swap(E, Tt);
+  }
+  Lev& nx = ctx->lev[l + 1];
+  if ((e = coarse_residual<T>(lv.cl, lvT<T>(lv), lvr<T>(lv), E, lvs<T>(lv), st)) != cudaSuccess) return e;
+  if ((e = coarse_restrict<T>(lv.cl, nx.cl, lvP<T>(nx), lvs<T>(lv), lvr<T>(nx), st)) != cudaSuccess) return e;
+  if ((e = coarse_cycle<T>(ctx, l + 1)) != cudaSuccess) return e;
+  if ((e = coarse_prolong<T>(lv.cl, nx.cl, lvP<T>(nx), lve<T>(nx), E, st)) != cudaSuccess) return e;
+  for (int s = 0; s < nu; ++s) {
+    if ((e = coarse_smooth<T>(lv.cl, lvT<T>(lv), lvD<T>(lv), lvr<T>(lv), E, Tt, st)) != cudaSuccess) return e;
+    std::swap(E, Tt);
+  }
+  if (E != lve<T>(lv)) {
+    e = cudaMemcpyAsync(lve<T>(lv), E, lv.cl.ncell * lv.cl.L * sizeof(T), cudaMemcpyDeviceToDevice, st);
+  }
+  return e;
+}
+
+// One V-cycle z = B r on the fine grid; S storage, C = compute, output To.
+template <class S, class To>
+static cudaError_t vcycle_fine(thermo_ctx* ctx, const S* kap, const S* r, S* ea, S* eb, To* z) {
+  typedef typename Cv<S>::C C;
+  const Geom& g = ctx->g;
+  cudaStream_t st = ctx->st;
+  const int nu = ctx->opt.nu_fine, L1 = ctx->L1;
+  const C om = (C)ctx->opt.omega;
+  const C* phi;
+  if (sizeof(C) == 8)
+    phi = (const C*)ctx->phi64;
+  else
+    phi = (const C*)ctx->phi32;
+  Lev& l1 = ctx->lev[1];
+  C* rc = (sizeof(C) == 8) ? (C*)l1.r64 : (C*)l1.r32;
+  C* ec = (sizeof(C) == 8) ? (C*)l1.e64 : (C*)l1.e32;
+  cudaError_t e;
+  S* E = ea;
+  S* F = eb;
+  if ((e = fine_smooth<S, S>(g, ctx->bits, kap, r, nullptr, E, om, st)) != cudaSuccess) return e;
+  for (int s = 1; s < nu; ++s) {
+    if ((e = fine_smooth<S, S>(g, ctx->bits, kap, r, E, F, om, st)) != cudaSuccess) return e;
+    std::swap(E, F);
+  }
+  if ((e = fine_restrict<S>(g, ctx->bits, kap, r, E, phi, rc, L1, st)) != cudaSuccess) return e;
+  if (sizeof(C) == 8)
+    e = coarse_cycle<double>(ctx, 1);
+  else
+    e = coarse_cycle<float>(ctx, 1);
+  if (e != cudaSuccess) return e;
+  if (nu == 1) return fine_prolong_smooth<S, To>(g, ctx->bits, kap, r, E, phi, ec, z, om, L1, st);
+  if ((e = fine_prolong_smooth<S, S>(g, ctx->bits, kap, r, E, phi, ec, F, om, L1, st)) != cudaSuccess) return e;
+  std::swap(E, F);
+  for (int s = 1; s < nu - 1; ++s) {
+    if ((e = fine_smooth<S, S>(g, ctx->bits, kap, r, E, F, om, st)) != cudaSuccess) return e;
+    std::swap(E, F);
+  }
+  return fine_smooth<S, To>(g, ctx->bits, kap, r, E, z, om, st);
+}
+
+// z = B r where r is the FP64 residual already converted to the cycle's
+// storage (mixed: ctx->r32 / r16); output: z64 (FP64 form) or z32.
+static cudaError_t apply_precond(thermo_ctx* ctx) {
+  const thermo_options& o = ctx->opt;
+  const Geom& g = ctx->g;
+  if (o.pc == THERMO_PC_NONE) return cudaMemcpyAsync(ctx->z64, ctx->r, g.nsize * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st);
+  if (o.pc == THERMO_PC_JACOBI) return fine_smooth<double, double>(g, ctx->bits, ctx->k64, ctx->r, nullptr, ctx->z64, 1.0, ctx->st);
+  if (o.prec == THERMO_FP64) return vcycle_fine<double, double>(ctx, ctx->k64, ctx->r, ctx->ea64, ctx->eb64, ctx->z64);
+  if (o.prec == THERMO_MIXED) return vcycle_fine<float, float>(ctx, ctx->k32, ctx->r32, ctx->ea32, ctx->eb32, ctx->z32);
+  return vcycle_fine<bf16, float>(ctx, ctx->k16, ctx->r16, ctx->ea16, ctx->eb16, ctx->z32);
+}
+static int zkind(const thermo_ctx* ctx) {
+  return (ctx->opt.pc != THERMO_PC_MMG || ctx->opt.prec == THERMO_FP64) ? 0 : 1;
+}
+static const void* zptr(const thermo_ctx* ctx) { return zkind(ctx) == 0 ? (const void*)ctx->z64 : (const void*)ctx->z32; }
+static int rkind(const thermo_ctx* ctx) {
+  if (ctx->opt.pc != THERMO_PC_MMG || ctx->opt.prec == THERMO_FP64) return -1;
+  return ctx->opt.prec == THERMO_MIXED ? 1 : 2;
+}
+static void* rptr(thermo_ctx* ctx) {
+  const int k = rkind(ctx);
+  return k == 1 ? (void*)ctx->r32 : (k == 2 ? (void*)ctx->r16 : nullptr);
+}
+
+// y = P A_L^-1 P^T v added to u (composite restriction / prolongation, FP64)
+static thermo_status coarse_correction(thermo_ctx* ctx, const double* v, double* u) {
+  const Geom& g = ctx->g;
+  cudaStream_t st = ctx->st;
+  Lev& l1 = ctx->lev[1];
+  CK(fine_restrict<double>(g, ctx->bits, ctx->k64, v, ctx->zero64, ctx->phi64, l1.r64, ctx->L1, st));
+  for (int l = 1; l < ctx->nlev; ++l) {
+    Lev& a = ctx->lev[l];
+    Lev& b = ctx->lev[l + 1];
+    CK(coarse_restrict<double>(a.cl, b.cl, b.Psi64, a.r64, b.r64, st));
+  }
+  Lev& top = ctx->lev[ctx->nlev];
+  CK(dense_gemv<double>(ctx->ncoarse, ctx->Ainv, top.r64, top.e64, st));
+  for (int l = ctx->nlev - 1; l >= 1; --l) {
+    Lev& a = ctx->lev[l];
+    Lev& b = ctx->lev[l + 1];
+    CK(cudaMemsetAsync(a.e64, 0, a.cl.ncell * a.cl.L * sizeof(double), st));
+    CK(coarse_prolong<double>(a.cl, b.cl, b.Psi64, b.e64, a.e64, st));
+  }
+  CK(fine_prolong_add(g, ctx->phi64, ctx->L1, l1.e64, u, st));
+  return THERMO_OK;
+}
+
+static thermo_status read_scalars(thermo_ctx* ctx) {
+  CK(cudaMemcpyAsync(ctx->sc_h, ctx->sc, sizeof(CgScalars), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return THERMO_OK;
+}
+
+// true residual r = b - A u into ctx->r, ||r||^2 in sc->rr
+static thermo_status true_residual(thermo_ctx* ctx, const double* b) {
+  CK(fine_apply_f64(ctx->g, ctx->bits, ctx->k64, ctx->u, ctx->q, nullptr, nullptr, nullptr, ctx->st));
+  CK(vec_residual(ctx->g, b, ctx->q, ctx->r, ctx->red, &ctx->sc->rr, ctx->st));
+  return THERMO_OK;
+}
+
+extern "C" thermo_status thermo_solve(thermo_ctx* ctx, const double* rhs, double* u, double tol,
+                                      thermo_solve_info* info) {
+  if (!ctx) return THERMO_EINVAL;
+  if (!u) return fail(ctx, THERMO_EINVAL, "u is NULL");
+  if (!(tol > 0.0)) return fail(ctx, THERMO_EINVAL, "tol must be > 0");
+  if (!ctx->have_density) return fail(ctx, THERMO_ESTATE, "solve before set_density");
+  if (!ctx->have_precond) return fail(ctx, THERMO_ESTATE, "solve before setup_precond");
+  const thermo_options& o = ctx->opt;
+  const Geom& g = ctx->g;
+  cudaStream_t st = ctx->st;
+  thermo_solve_info inf;
+  memset(&inf, 0, sizeof inf);
+  inf.t_setup_ms = ctx->t_setup_ms;
+  CK(cudaStreamSynchronize(st));
+  const double t0 = now_ms();
+  const double* b = ctx->blift;
+  if (rhs) {
+    CK(pack_nodes(g, rhs, ctx->bv, st));
+    b = ctx->bv;
+  }
+  const int flexible = o.flexible < 0 ? (o.prec != THERMO_FP64 && o.pc == THERMO_PC_MMG) : o.flexible;
+  const bool mmg = o.pc == THERMO_PC_MMG;
+  // initial guess
+  if (o.guess == THERMO_GUESS_GIVEN || o.guess == THERMO_GUESS_WARM_COARSE) {
+    CK(pack_nodes(g, u, ctx->u, st));
+  } else {
+    CK(cudaMemcpyAsync(ctx->u, ctx->TD, g.nsize * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  }
+  if (mmg && (o.guess == THERMO_GUESS_COARSE || o.guess == THERMO_GUESS_WARM_COARSE)) {
+    thermo_status s = true_residual(ctx, b);
+    if (s != THERMO_OK) return s;
+    s = coarse_correction(ctx, ctx->r, ctx->u);
+    if (s != THERMO_OK) return s;
+  }
+  CK(vec_dot(g, b, b, 0, ctx->red, &ctx->sc->bb, st));
+  {
+    thermo_status s = true_residual(ctx, b);
+    if (s != THERMO_OK) return s;
+  }
+  CK(cudaMemsetAsync(&ctx->sc->flag, 0, sizeof(int), st));
+  thermo_status s = read_scalars(ctx);
+  if (s != THERMO_OK) return s;
+  const double bnorm = sqrt(ctx->sc_h->bb);
+  double rn = sqrt(ctx->sc_h->rr);
+  if (!std::isfinite(bnorm)) return fail(ctx, THERMO_EINVAL, "right-hand side is not finite");
+  if (!std::isfinite(rn)) {
+    inf.status = THERMO_EBREAKDOWN;
+    if (info) *info = inf;
+    return fail(ctx, THERMO_EBREAKDOWN, "initial residual is not finite (check the density)");
+  }
+  int it = 0, restarts = 0;
+  thermo_status result = THERMO_OK;
+  auto start_cycle = [&](void) -> thermo_status {
+    // r (FP64) -> cycle storage, z = B r, rz = r.z, p = z
+    if (rkind(ctx) > 0) CK(vec_copy_cvt(g, ctx->r, rptr(ctx), rkind(ctx), st));
+    CK(apply_precond(ctx));
+    CK(vec_dot(g, ctx->r, zptr(ctx), zkind(ctx), ctx->red, &ctx->sc->rz, st));
+    CK(cg_pupdate(g, zptr(ctx), zkind(ctx), ctx->p, ctx->sc, 1, st));
+    return THERMO_OK;
+  };
+  if (bnorm == 0.0) {
+    CK(cudaMemsetAsync(ctx->u, 0, g.nsize * sizeof(double), st));
+    rn = 0.0;
+  } else if (rn > tol * bnorm) {
+    s = start_cycle();
+    if (s != THERMO_OK) return s;
+    const int check = o.check_every < 1 ? 1 : o.check_every;
+    while (true) {
+      CK(fine_apply_f64(g, ctx->bits, ctx->k64, ctx->p, ctx->q, ctx->red.partial, ctx->red.counter, &ctx->sc->pq, st));
+      CK(cg_update(g, ctx->u, ctx->r, ctx->p, ctx->q, flexible ? zptr(ctx) : nullptr, zkind(ctx), rptr(ctx),
+                   rkind(ctx), ctx->sc, ctx->red, st));
+      ++it;
+      if (it % check == 0 || it >= o.max_iter) {
+        s = read_scalars(ctx);
+        if (s != THERMO_OK) return s;
+        if (ctx->sc_h->flag) {
+          result = fail(ctx, THERMO_EBREAKDOWN, "CG breakdown at iteration %d", it);
+          break;
+        }
+        rn = sqrt(ctx->sc_h->rr);
+        if (rn <= tol * bnorm) {
+          s = true_residual(ctx, b);
+          if (s != THERMO_OK) return s;
+          s = read_scalars(ctx);
+          if (s != THERMO_OK) return s;
+          const double rt = sqrt(ctx->sc_h->rr);
+          if (rt <= tol * bnorm || restarts >= 5) {
+            if (rt > tol * bnorm) result = fail(ctx, THERMO_ENOTCONV, "true residual stagnates above tol");
+            break;
+          }
+          ++restarts;
+          s = start_cycle();
+          if (s != THERMO_OK) return s;
+          continue;
+        }
+        if (it >= o.max_iter) {
+          result = fail(ctx, THERMO_ENOTCONV, "no convergence in %d iterations", it);
+          break;
+        }
+      }
+      CK(apply_precond(ctx));
+      CK(cg_beta_dot(g, ctx->r, zptr(ctx), zkind(ctx), flexible, ctx->sc, ctx->red, st));
+      CK(cg_pupdate(g, zptr(ctx), zkind(ctx), ctx->p, ctx->sc, 0, st));
+    }
+  }
+  // final true residual (FP64)
+  {
+    thermo_status s2 = true_residual(ctx, b);
+    if (s2 != THERMO_OK) return s2;
+    s2 = read_scalars(ctx);
+    if (s2 != THERMO_OK) return s2;
+  }
+  inf.rel_res_recursive = bnorm > 0 ? rn / bnorm : 0.0;
+  inf.rel_res_true = bnorm > 0 ? sqrt(ctx->sc_h->rr) / bnorm : 0.0;
+  CK(unpack_nodes(g, ctx->u, u, st));
+  CK(cudaStreamSynchronize(st));
+  inf.iters = it;
+  inf.restarts = restarts;
+  inf.t_solve_ms = now_ms() - t0;
+  inf.status = result;
+  if (info) *info = inf;
+  return result;
+}
+
+extern "C" thermo_status thermo_sensitivity(thermo_ctx* ctx, const double* u, double* dc) {
+  if (!ctx) return THERMO_EINVAL;
+  if (!u || !dc) return fail(ctx, THERMO_EINVAL, "NULL argument");
+  if (!ctx->have_density) return fail(ctx, THERMO_ESTATE, "sensitivity before set_density");
+  CK(pack_nodes(ctx->g, u, ctx->tmp, ctx->st));
+  CK(sensitivity(ctx->g, ctx->tmp, ctx->xd, ctx->sp, ctx->skmin, ctx->skmax, dc, ctx->st));
+  return THERMO_OK;
+}
+
+extern "C" thermo_status thermo_compliance(thermo_ctx* ctx, const double* u, double* c) {
+  if (!ctx) return THERMO_EINVAL;
+  if (!u || !c) return fail(ctx, THERMO_EINVAL, "NULL argument");
+  CK(pack_nodes(ctx->g, u, ctx->tmp, ctx->st));
+  CK(vec_dot(ctx->g, ctx->f, ctx->tmp, 0, ctx->red, ctx->dscal, ctx->st));
+  CK(cudaMemcpyAsync(ctx->dscal_h, ctx->dscal, sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  *c = ctx->dscal_h[0];
+  return THERMO_OK;
+}
+
+extern "C" thermo_status thermo_apply(thermo_ctx* ctx, int precision, const double* u, double* y) {
+  if (!ctx) return THERMO_EINVAL;
+  if (!u || !y) return fail(ctx, THERMO_EINVAL, "NULL argument");
+  if (!ctx->have_density) return fail(ctx, THERMO_ESTATE, "apply before set_density");
+  const Geom& g = ctx->g;
+  cudaStream_t st = ctx->st;
+  CK(pack_nodes(g, u, ctx->tmp, st));
+  if (precision == THERMO_FP64) {
+    CK(fine_apply_f64(g, ctx->bits, ctx->k64, ctx->tmp, ctx->q, nullptr, nullptr, nullptr, st));
+  } else if (precision == THERMO_MIXED) {
+    CK(vec_copy_cvt(g, ctx->tmp, ctx->ea32, 1, st));
+    CK(fine_apply_lp<float>(g, ctx->bits, ctx->k32, ctx->ea32, ctx->eb32, st));
+    CK(vec_to_f64(g, ctx->eb32, 1, ctx->q, st));
+  } else if (precision == THERMO_MIXED_BF16S) {
+    bf16 *a16 = ctx->ea16, *b16 = ctx->eb16;
+    if (!a16) return fail(ctx, THERMO_EINVAL, "BF16 buffers exist only for a MIXED_BF16S context");
+    CK(vec_copy_cvt(g, ctx->tmp, a16, 2, st));
+    CK(fine_apply_lp<bf16>(g, ctx->bits, ctx->k16, a16, b16, st));
+    CK(vec_to_f64(g, b16, 2, ctx->q, st));
+  } else {
+    return fail(ctx, THERMO_EINVAL, "unknown precision %d", precision);
+  }
+  CK(unpack_nodes(g, ctx->q, y, st));
+  return THERMO_OK;
+}
+
+extern "C" thermo_status thermo_vcycle(thermo_ctx* ctx, const double* r, double* z) {
+  if (!ctx) return THERMO_EINVAL;
+  if (!r || !z) return fail(ctx, THERMO_EINVAL, "NULL argument");
+  if (!ctx->have_precond || ctx->opt.pc != THERMO_PC_MMG) return fail(ctx, THERMO_ESTATE, "no MMG preconditioner");
+  const Geom& g = ctx->g;
+  cudaStream_t st = ctx->st;
+  CK(pack_nodes(g, r, ctx->r, st));
+  if (rkind(ctx) > 0) CK(vec_copy_cvt(g, ctx->r, rptr(ctx), rkind(ctx), st));
+  CK(apply_precond(ctx));
+  if (zkind(ctx) == 1) {
+    CK(vec_to_f64(g, ctx->z32, 1, ctx->tmp, st));
+    CK(unpack_nodes(g, ctx->tmp, z, st));
+  } else {
+    CK(unpack_nodes(g, ctx->z64, z, st));
+  }
+  return THERMO_OK;
+}
+
+extern "C" thermo_status thermo_load_vector(thermo_ctx* ctx, double* f) {
+  if (!ctx || !f) return THERMO_EINVAL;
+  CK(unpack_nodes(ctx->g, ctx->f, f, ctx->st));
+  return THERMO_OK;
+}
+
+extern "C" thermo_status thermo_hierarchy(const thermo_ctx* ctx, int* nlevels, int* cells, int* nvec,
+                                          long long* ndof) {
+  if (!ctx) return THERMO_EINVAL;
+  if (nlevels) *nlevels = ctx->nlev;
+  for (int l = 1; l <= ctx->nlev; ++l) {
+    const CLevel& c = ctx->lev[l].cl;
+    if (cells) {
+      cells[(l - 1) * 3 + 0] = c.mx;
+      cells[(l - 1) * 3 + 1] = c.my;
+      cells[(l - 1) * 3 + 2] = c.mz;
+    }
+    if (nvec) nvec[l - 1] = c.L;
+    if (ndof) ndof[l - 1] = c.ncell * c.L;
+  }
+  return THERMO_OK;
+}
+
+extern "C" thermo_status thermo_export_level(thermo_ctx* ctx, int level, int what, double* out, long long count) {
+  if (!ctx) return THERMO_EINVAL;
+  if (!out || level < 1 || level > ctx->nlev) return fail(ctx, THERMO_EINVAL, "bad level / output");
+  if (!ctx->have_precond || ctx->opt.pc != THERMO_PC_MMG) return fail(ctx, THERMO_ESTATE, "no hierarchy yet");
+  Lev& lv = ctx->lev[level];
+  const CLevel& c = lv.cl;
+  cudaStream_t st = ctx->st;
+  long long need = 0;
+  const double* src = nullptr;
+  if (what == 0) {
+    if (level == 1) {
+      need = ctx->nnode * ctx->L1;
+      if (count < need) return fail(ctx, THERMO_EINVAL, "output too small (%lld < %lld)", count, need);
+      CK(phi_natural(ctx->g, ctx->phi64, ctx->L1, out, st));
+      return THERMO_OK;
+    }
+    need = c.ncell * (long long)c.g * c.g * c.g * ctx->lev[level - 1].cl.L * c.L;
+    src = lv.Psi64;
+  } else if (what == 1) {
+    need = c.ncell * 27 * c.L * c.L;
+    src = lv.T64;
+  } else if (what == 2) {
+    need = c.ncell * c.L;
+    src = lv.eig;
+  } else if (what == 3) {
+    if (level != ctx->nlev) return fail(ctx, THERMO_EINVAL, "inverse exists on the coarsest level only");
+    need = (long long)ctx->ncoarse * ctx->ncoarse;
+    src = ctx->Ainv;
+  } else {
+    return fail(ctx, THERMO_EINVAL, "unknown item %d", what);
+  }
+  if (count < need) return fail(ctx, THERMO_EINVAL, "output too small (%lld < %lld)", count, need);
+  CK(cudaMemcpyAsync(out, src, need * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  return THERMO_OK;
+}
+
+extern "C" thermo_status thermo_filter(thermo_ctx* ctx, const double* in, double* out, double rmin, int transpose) {
+  if (!ctx) return THERMO_EINVAL;
+  if (!in || !out || in == out || !(rmin > 0.0)) return fail(ctx, THERMO_EINVAL, "bad filter arguments");
+  CK(density_filter(ctx->g.Nx, ctx->g.Ny, ctx->g.Nz, in, out, rmin, transpose, ctx->st));
+  return THERMO_OK;
+}
+
+extern "C" thermo_status thermo_oc_update(thermo_ctx* ctx, double* x, const double* dc, const double* dv,
+                                          double volfrac, double move, double rmin, double* change) {
+  if (!ctx) return THERMO_EINVAL;
+  if (!x || !dc || !dv || !(volfrac > 0.0) || !(move > 0.0)) return fail(ctx, THERMO_EINVAL, "bad OC arguments");
+  const long long M = ctx->nelem;
+  cudaStream_t st = ctx->st;
+  if (!ctx->colsum) {
+    CK(dalloc(ctx, &ctx->colsum, M));
+    CK(dalloc(ctx, &ctx->xnew, M));
+  }
+  if (ctx->rmin_cs != rmin) {
+    // column sums of the filter, colsum = H^T 1: the filtered volume is colsum . x / M
+    CK(fill_const(ctx->xnew, M, 1.0, st));
+    CK(density_filter(ctx->g.Nx, ctx->g.Ny, ctx->g.Nz, ctx->xnew, ctx->colsum, rmin, 1, st));
+    ctx->rmin_cs = rmin;
+  }
+  double l1 = 0.0, l2 = 1e9, vol = 0.0;
+  while ((l2 - l1) / (l1 + l2) > 1e-3) {
+    const double lmid = 0.5 * (l1 + l2);
+    CK(oc_candidate(M, x, dc, dv, ctx->colsum, lmid, move, ctx->xnew, ctx->red, ctx->dscal, st));
+    CK(cudaMemcpyAsync(ctx->dscal_h, ctx->dscal, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    vol = ctx->dscal_h[0];
+    if (vol > volfrac)
+      l1 = lmid;
+    else
+      l2 = lmid;
+  }
+  if (change) {
+    CK(max_abs_diff(M, x, ctx->xnew, ctx->red, ctx->dscal + 1, st));
+    CK(cudaMemcpyAsync(ctx->dscal_h + 1, ctx->dscal + 1, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    *change = ctx->dscal_h[1];
+  }
+  CK(cudaMemcpyAsync(x, ctx->xnew, M * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  return THERMO_OK;
+}
+
+extern "C" long long thermo_launch_count(void) { return thermo::launch_count(); }
+
+// Time `reps` back-to-back launches of one internal kernel on the context's
+// buffers with CUDA events on the context stream (see thermo.h).
+extern "C" thermo_status thermo_bench_kernel(thermo_ctx* ctx, int which, int reps, double* ms_per_launch,
+                                             double* bytes_per_launch) {
+  if (!ctx || reps < 1 || !ms_per_launch) return THERMO_EINVAL;
+  if (!ctx->have_density) return fail(ctx, THERMO_ESTATE, "bench before set_density");
+  const bool needs_pc = which == 4 || which == 5 || which == 6 || which == 8 || which == 9;
+  if (needs_pc && (!ctx->have_precond || ctx->opt.pc != THERMO_PC_MMG))
+    return fail(ctx, THERMO_ESTATE, "kernel %d needs the MMG hierarchy", which);
+  const Geom& g = ctx->g;
+  cudaStream_t st = ctx->st;
+  const double n = (double)ctx->nnode, M = (double)ctx->nelem;
+  Lev& l1 = ctx->lev[1];
+  const double L1 = ctx->L1;
+  double bytes = 0.0;
+  auto run = [&]() -> cudaError_t {
+    switch (which) {
+      case 0:
+        bytes = n * 16 + M * 8;
+        return fine_apply_f64(g, ctx->bits, ctx->k64, ctx->p, ctx->q, ctx->red.partial, ctx->red.counter,
+                              &ctx->sc->pq, st);
+      case 1:
+        bytes = n * 8 + M * 4;
+        return fine_apply_lp<float>(g, ctx->bits, ctx->k32, ctx->ea32, ctx->eb32, st);
+      case 2:
+        if (!ctx->ea16) return cudaErrorInvalidValue;
+        bytes = n * 4 + M * 2;
+        return fine_apply_lp<bf16>(g, ctx->bits, ctx->k16, ctx->ea16, ctx->eb16, st);
+      case 3:
+        bytes = n * 12 + M * 4;
+        return fine_smooth<float, float>(g, ctx->bits, ctx->k32, ctx->r32, ctx->ea32, ctx->eb32, 0.6f, st);
+      case 4:
+        bytes = n * (8 + 4 * L1) + M * 4;
+        return fine_restrict<float>(g, ctx->bits, ctx->k32, ctx->r32, ctx->ea32, ctx->phi32, l1.r32, ctx->L1, st);
+      case 5:
+        bytes = n * (12 + 4 * L1) + M * 4;
+        return fine_prolong_smooth<float, float>(g, ctx->bits, ctx->k32, ctx->r32, ctx->ea32, ctx->phi32, l1.e32,
+                                                 ctx->eb32, 0.6f, ctx->L1, st);
+      case 6:
+        bytes = (double)l1.cl.ncell * (27.0 * l1.cl.L * l1.cl.L + 2.0 * l1.cl.L) * 4.0;
+        return coarse_apply<float>(l1.cl, l1.T32, l1.e32, l1.s32, st);
+      case 7:
+        bytes = n * (8 * 4 + 4 + 8 * 2 + 4);
+        return cg_update(g, ctx->tmp, ctx->bv, ctx->p, ctx->q, ctx->z32, 1, ctx->r32, 1, ctx->sc, ctx->red, st);
+      case 8: {
+        bytes = 0.0;
+        const thermo_precision keep = ctx->opt.prec;
+        ctx->opt.prec = THERMO_MIXED;
+        cudaError_t e = apply_precond(ctx);
+        ctx->opt.prec = keep;
+        return e;
+      }
+      case 9: {
+        bytes = 0.0;
+        if (!ctx->z64) return cudaErrorInvalidValue;
+        const thermo_precision keep = ctx->opt.prec;
+        ctx->opt.prec = THERMO_FP64;
+        cudaError_t e = apply_precond(ctx);
+        ctx->opt.prec = keep;
+        return e;
+      }
+      case 10:
+        bytes = n * 24 + M * 8;
+        return fine_smooth<double, double>(g, ctx->bits, ctx->k64, ctx->r, ctx->ea64, ctx->eb64, 0.6, st);
+      default:
+        return cudaErrorInvalidValue;
+    }
+  };
+  CK(run());  // warm-up (also sets kernel attributes)
+  cudaEvent_t e0, e1;
+  CK(cudaEventCreate(&e0));
+  CK(cudaEventCreate(&e1));
+  CK(cudaEventRecord(e0, st));
+  for (int i = 0; i < reps; ++i) CK(run());
+  CK(cudaEventRecord(e1, st));
+  CK(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  CK(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *ms_per_launch = ms / reps;
+  if (bytes_per_launch) *bytes_per_launch = bytes;
+  return THERMO_OK;
+}

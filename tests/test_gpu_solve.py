@@ -1,0 +1,166 @@
+"""Whole-method parity: V-cycle (Algorithm 1) and preconditioned CG solves
+through the C ABI vs the FP64 oracle (direct solve and the oracle's own MMG).
+
+* FP64 form: solution within 1e-8 relative of the oracle's exact solution
+  (solved to 1e-12), iteration count within +-2 of the oracle's MMG-PCG at
+  1e-8 (bases agree to FP32-eigen accuracy, so the counts may differ by one
+  or two at most).
+* Mixed forms (FP32 V-cycle, BF16-storage smoother) inside FP64 flexible CG:
+  the same 1e-8 solution accuracy once solved to 1e-12, error vs the oracle
+  reported.
+* Comparison modes (plain CG, Jacobi-PCG) reach the same solution.
+"""
+import numpy as np
+import pytest
+import scipy.sparse.linalg as spla
+import torch
+
+from helpers import gpu_solver, oracle_problem, relerr, small_problem
+from oracle import fem, krylov, mmg
+
+pytestmark = pytest.mark.gpu
+
+
+def _exact(P):
+    return spla.spsolve(P["A"].tocsc(), P["b"])
+
+
+@pytest.fixture(scope="module")
+def smooth32():
+    pr = small_problem(32, kind="smooth")
+    P = oracle_problem(pr)
+    return pr, P, _exact(P)
+
+
+def test_vcycle_fp64_matches_oracle(smooth32):
+    pr, P, _ = smooth32
+    s = gpu_solver(pr, prec=0)
+    s.setup_precond()
+    H = mmg.MMG(P)
+    n = P["A"].shape[0]
+    rng = np.random.default_rng(3)
+    r = rng.standard_normal(n)
+    r[P["mask"]] = 0.0
+    z = s.vcycle(torch.as_tensor(r)).cpu().numpy()
+    zo = H(r)
+    assert relerr(z, zo) < 1e-4, relerr(z, zo)
+    # symmetric and positive (FP64 V-cycle)
+    y = rng.standard_normal(n)
+    y[P["mask"]] = 0.0
+    zy = s.vcycle(torch.as_tensor(y)).cpu().numpy()
+    assert abs(z @ y - r @ zy) <= 1e-10 * np.linalg.norm(z) * np.linalg.norm(y)
+    assert r @ z > 0
+    s.close()
+
+
+@pytest.mark.parametrize("prec", [0, 1, 2])
+def test_solve_matches_exact_solution(smooth32, prec):
+    pr, P, ud = smooth32
+    s = gpu_solver(pr, prec=prec)
+    s.setup_precond()
+    u, info = s.solve(tol=1e-12)
+    u = u.cpu().numpy()
+    assert info["rel_res_true"] <= 1e-12
+    assert relerr(u, ud) < 1e-8, relerr(u, ud)
+    s.close()
+
+
+def test_fp64_iteration_count_matches_oracle(smooth32):
+    pr, P, ud = smooth32
+    H = mmg.MMG(P)
+    _, io = krylov.pcg(P["A"], P["b"], precond=H, u0=H.coarse_guess(P["b"]), tol=1e-8)
+    s = gpu_solver(pr, prec=0)
+    s.setup_precond()
+    u, info = s.solve(tol=1e-8)
+    assert abs(info["iters"] - io["iters"]) <= 2, (info["iters"], io["iters"])
+    assert info["rel_res_true"] <= 1e-8
+    s.close()
+
+
+@pytest.mark.parametrize("kind,N,kmin", [("chan", 32, 1e-6), ("thresh", 32, 1e-3), ("chan", 64, 1e-9)])
+def test_high_contrast_solves(kind, N, kmin):
+    pr = small_problem(N, kind=kind, seed=3, kmin=kmin)
+    P = oracle_problem(pr)
+    ud = _exact(P) if N <= 32 else None
+    res = {}
+    for prec in (0, 1, 2):
+        s = gpu_solver(pr, prec=prec)
+        s.setup_precond()
+        u, info = s.solve(tol=1e-10)
+        res[prec] = (u.cpu().numpy(), info)
+        assert info["rel_res_true"] <= 1e-10, (prec, info)
+        s.close()
+    if ud is not None:
+        for prec in (0, 1, 2):
+            assert relerr(res[prec][0], ud) < 1e-6, (prec, relerr(res[prec][0], ud))
+    else:
+        # true FP64 residual of each solution, recomputed by the oracle
+        for prec in (0, 1, 2):
+            r = P["b"] - P["A"] @ res[prec][0]
+            assert np.linalg.norm(r) <= 1.5e-10 * np.linalg.norm(P["b"])
+
+
+@pytest.mark.parametrize("pc", [1, 2])
+def test_comparison_modes(smooth32, pc):
+    pr, P, ud = smooth32
+    s = gpu_solver(pr, prec=0, pc=pc, guess=0, max_iter=20000)
+    s.setup_precond()
+    u, info = s.solve(tol=1e-11)
+    assert relerr(u.cpu().numpy(), ud) < 1e-7
+    _, io = krylov.pcg(P["A"], P["b"], precond=None if pc == 1 else krylov.jacobi_precond(P["A"]), tol=1e-11,
+                       maxit=20000)
+    assert abs(info["iters"] - io["iters"]) <= max(3, 0.02 * io["iters"]), (info["iters"], io["iters"])
+    s.close()
+
+
+def test_guess_modes_and_given_rhs(smooth32):
+    pr, P, ud = smooth32
+    s = gpu_solver(pr, prec=1, guess=2)
+    s.setup_precond()
+    u, info = s.solve(tol=1e-10)
+    s2 = gpu_solver(pr, prec=1, guess=3)
+    s2.setup_precond()
+    u0 = torch.as_tensor(0.9 * ud)
+    u2, info2 = s2.solve(u=u0.cuda(), tol=1e-10)
+    assert relerr(u2.cpu().numpy(), ud) < 1e-7
+    assert info2["iters"] <= info["iters"]
+    rhs = torch.as_tensor(P["b"])
+    u3, _ = s.solve(rhs=rhs, tol=1e-10)
+    assert relerr(u3.cpu().numpy(), ud) < 1e-7
+    s.close()
+    s2.close()
+
+
+def test_compliance_and_sensitivity_match_oracle(smooth32):
+    pr, P, ud = smooth32
+    s = gpu_solver(pr, prec=1)
+    s.setup_precond()
+    u, info = s.solve(tol=1e-12)
+    c = s.compliance(u)
+    co = fem.compliance(P["f"], ud)
+    assert abs(c - co) <= 1e-10 * abs(co)
+    dc = s.sensitivity(u).cpu().numpy()
+    dco = fem.sensitivity(pr["grid"], pr["h"], pr["x"], pr["p"], pr["kmin"], pr["kmax"], ud)
+    assert relerr(dc, dco) < 1e-8
+    s.close()
+
+
+def test_nonzero_dirichlet_values_layered_exact():
+    import workloads as W
+    N = 16
+    grid = (N, N, N)
+    x = np.zeros((N, N, N))
+    x[: N // 2] = 1.0
+    vals = np.zeros((N + 1, N + 1, N + 1))
+    vals[-1] = 1.0
+    pr = dict(grid=grid, h=(1 / N,) * 3, mask=W.full_face_mask(grid, "z01"), source=np.zeros(N ** 3),
+              x=x.ravel(), p=1.0, kmin=1e-6, kmax=1.0, values=vals.ravel())
+    s = gpu_solver(pr, prec=1)
+    s.setup_precond()
+    u, info = s.solve(tol=1e-12)
+    t = 1e-6 / (1 + 1e-6)
+    z = np.arange(N + 1) / N
+    prof = np.where(z <= 0.5, t * z / 0.5, t + (1 - t) * (z - 0.5) / 0.5)
+    exact = (prof[:, None, None] * np.ones((1, N + 1, N + 1))).ravel()
+    np.testing.assert_allclose(u.cpu().numpy(), exact, atol=1e-10)
+    s.close()
