@@ -165,6 +165,11 @@ def main():
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ref-iters", type=int, default=60, help="GPU iteration count used to scale the reference")
+    ap.add_argument("--profile-kernel", type=int, default=None,
+                    help="only build the workload and launch thermo_bench_kernel(K) three times (for ncu)")
+    ap.add_argument("--profile-solve", action="store_true",
+                    help="only set up and run one mixed solve inside an NVTX range 'solve' (for ncu)")
+    ap.add_argument("--prec", type=int, default=1, help="precision of the profiling modes")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -221,6 +226,24 @@ def main():
         t = torch.tensor([v], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
+
+    if args.profile_kernel is not None or args.profile_solve:
+        s = make(args.prec)
+        s.set_density(x_d, pr["p"], pr["kmin"], pr["kmax"])
+        s.setup_precond()
+        if args.profile_kernel is not None:
+            ms, by = s.bench_kernel(args.profile_kernel, 3)
+            print(json.dumps({"kernel": args.profile_kernel, "ms": ms, "bytes": by}))
+        else:
+            s.solve(tol=args.tol)
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_push("solve")
+            u, info = s.solve(tol=args.tol)
+            torch.cuda.synchronize()
+            torch.cuda.nvtx.range_pop()
+            print(json.dumps({"iters": info["iters"], "solve_ms": info["t_solve_ms"]}))
+        s.close()
+        return 0
 
     # ---- mixed form (headline)
     s = make(thermo.MIXED)

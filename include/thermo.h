@@ -100,8 +100,8 @@ typedef struct {
 typedef struct {
   int iters;                        /* A p products = preconditioner applications */
   int restarts;                     /* residual replacements after a failed true-residual check */
-  double rel_res_recursive;         /* ||r_k|| / ||b|| of the recurrence at exit */
-  double rel_res_true;              /* ||b - A u|| / ||b|| recomputed in FP64 at exit */
+  double rel_res_recursive;         /* ||r_k|| / ||b_F|| of the recurrence at exit */
+  double rel_res_true;              /* ||b - A u|| / ||b_F|| recomputed in FP64 at exit */
   double t_setup_ms;                /* last thermo_setup_precond wall time */
   double t_solve_ms;                /* this solve's wall time */
   int status;                       /* thermo_status of the solve */
@@ -148,8 +148,10 @@ thermo_status thermo_set_density(thermo_ctx *ctx, const double *x, double p,
  * that the context is ready. */
 thermo_status thermo_setup_precond(thermo_ctx *ctx);
 
-/* Solve A u = b to ||b - A u||_2 <= tol ||b||_2 (checked on the recursive
- * residual, confirmed on the true FP64 residual at exit).
+/* Solve A u = b to ||b - A u||_2 <= tol ||b_F||_2, where b_F is b on the free
+ * (non-Dirichlet) nodes; the Dirichlet rows are identities satisfied exactly
+ * by every iterate.  Checked on the recursive residual, confirmed on the true
+ * FP64 residual at exit.
  *   rhs   device double[nodes] (natural layout), or NULL for the assembled
  *         load f (with Dirichlet lifting b_F = f_F - A_FD T_D, b_D = T_D)
  *   u     device double[nodes]: initial guess if opt.guess is GIVEN or

@@ -2,7 +2,9 @@
 
 The paper solves both linear systems with PETSc CG wrapped around the MMG
 preconditioner (Sec. 4, experimental setup).  The stopping rule used here is
-the unpreconditioned 2-norm relative to ||b||:  ||b - A u_k|| <= tol ||b||,
+the unpreconditioned 2-norm relative to the free part of the right-hand side:
+||b - A u_k|| <= tol ||b_F|| (Dirichlet rows are identities and carry no
+residual once u holds the boundary values),
 checked on the recursive residual and confirmed on the true residual at exit
 (on failure of the confirmation the residual is replaced by the true one and
 the iteration restarts from the current iterate).
@@ -21,13 +23,16 @@ import numpy as np
 
 
 def pcg(A, b, precond=None, u0=None, tol=1e-8, maxit=10000, flexible=False,
-        max_restarts=5):
+        max_restarts=5, free=None):
     """Returns (u, info) with info = dict(iters, converged, relres_recursive,
-    relres_true, history)."""
+    relres_true, history).  ``free``: boolean mask of the unknowns that are
+    not Dirichlet rows; the relative residual is measured against ||b_F||
+    (the identity rows hold exactly for every iterate that starts with the
+    Dirichlet values)."""
     n = b.shape[0]
     u = np.zeros(n) if u0 is None else np.array(u0, dtype=np.float64, copy=True)
     M = (lambda r: r.copy()) if precond is None else precond
-    bnorm = float(np.linalg.norm(b))
+    bnorm = float(np.linalg.norm(b if free is None else b[free]))
     if bnorm == 0.0:
         return np.zeros(n), dict(iters=0, converged=True, relres_recursive=0.0,
                                  relres_true=0.0, history=[0.0])

@@ -48,6 +48,8 @@ cudaError_t vec_residual(const Geom& g, const double* b, const double* Ax, doubl
                          double* rr, cudaStream_t st);
 cudaError_t vec_dot(const Geom& g, const double* a, const void* b, int b_is_float, const Reducer& red, double* out,
                     cudaStream_t st);
+cudaError_t vec_dot_free(const Geom& g, const uint32_t* bits, const double* a, const double* b, const Reducer& red,
+                         double* out, cudaStream_t st);
 cudaError_t vec_copy_cvt(const Geom& g, const double* src, void* dst, int dst_kind, cudaStream_t st);  // 0 f64,1 f32,2 bf16
 cudaError_t cg_update(const Geom& g, double* u, double* r, const double* p, const double* q, const void* z_old,
                       int z_kind, void* r_lp, int r_lp_kind, CgScalars* sc, const Reducer& red, cudaStream_t st);

@@ -642,7 +642,7 @@ extern "C" thermo_status thermo_solve(thermo_ctx* ctx, const double* rhs, double
     s = coarse_correction(ctx, ctx->r, ctx->u);
     if (s != THERMO_OK) return s;
   }
-  CK(vec_dot(g, b, b, 0, ctx->red, &ctx->sc->bb, st));
+  CK(vec_dot_free(g, ctx->bits, b, b, ctx->red, &ctx->sc->bb, st));
   {
     thermo_status s = true_residual(ctx, b);
     if (s != THERMO_OK) return s;

@@ -308,6 +308,29 @@ cudaError_t vec_copy_cvt(const Geom& g, const double* src, void* dst, int kind, 
   return cudaGetLastError();
 }
 
+// a.b over free (non-Dirichlet) interior nodes only
+__global__ void __launch_bounds__(VNT) k_dot_free(Geom g, Rows R, const uint32_t* __restrict__ bits,
+                                                  const double* __restrict__ a, const double* __restrict__ b,
+                                                  Reducer red, double* out) {
+  double v[1] = {0.0}, res[1];
+  for (long long it = blockIdx.x * (long long)VNT + threadIdx.x; it < R.items; it += (long long)gridDim.x * VNT) {
+    const long long row = it / R.ppr, pr = it - row * R.ppr;
+    const int z = (int)(row / g.ny), y = (int)(row - (row / g.ny) * g.ny);
+    const long long i = item_index(g, it, R.ppr);
+    double2 x = ld2<double>(a + i), w = ld2<double>(b + i);
+    const int x0 = (int)(2 * pr);
+    if (!is_dir(g, bits, x0, y, z)) v[0] += x.x * w.x;
+    if (!is_dir(g, bits, x0 + 1, y, z)) v[0] += x.y * w.y;
+  }
+  if (reduce_k<1>(v, red, res) && threadIdx.x == 0) *out = res[0];
+}
+cudaError_t vec_dot_free(const Geom& g, const uint32_t* bits, const double* a, const double* b, const Reducer& red,
+                         double* out, cudaStream_t st) {
+  Rows R = rows_of(g);
+  note_launch(), k_dot_free<<<vec_blocks(R.items), VNT, 0, st>>>(g, R, bits, a, b, red, out);
+  return cudaGetLastError();
+}
+
 // alpha = rz / pq;  u += alpha p;  r -= alpha q;  rr = r.r;  rzo = r.z_old;  r_lp = (low) r
 template <class Tz, class Tr>
 __global__ void __launch_bounds__(VNT) k_cg_update(Geom g, Rows R, double* __restrict__ u, double* __restrict__ r,

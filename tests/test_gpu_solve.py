@@ -157,10 +157,13 @@ def test_nonzero_dirichlet_values_layered_exact():
               x=x.ravel(), p=1.0, kmin=1e-6, kmax=1.0, values=vals.ravel())
     s = gpu_solver(pr, prec=1)
     s.setup_precond()
-    u, info = s.solve(tol=1e-12)
+    u, info = s.solve(tol=1e-11)
     t = 1e-6 / (1 + 1e-6)
     z = np.arange(N + 1) / N
     prof = np.where(z <= 0.5, t * z / 0.5, t + (1 - t) * (z - 0.5) / 0.5)
     exact = (prof[:, None, None] * np.ones((1, N + 1, N + 1))).ravel()
-    np.testing.assert_allclose(u.cpu().numpy(), exact, atol=1e-10)
+    uu = u.cpu().numpy()
+    np.testing.assert_allclose(uu, exact, atol=1e-9)
+    lower = exact < 2 * t  # the conductive half carries values of order t = 1e-6
+    np.testing.assert_allclose(uu[lower], exact[lower], rtol=1e-4, atol=1e-13)
     s.close()
