@@ -170,6 +170,7 @@ def main():
     ap.add_argument("--profile-solve", action="store_true",
                     help="only set up and run one mixed solve inside an NVTX range 'solve' (for ncu)")
     ap.add_argument("--prec", type=int, default=1, help="precision of the profiling modes")
+    ap.add_argument("--kernels-only", action="store_true", help="only time the kernels and one solve per form")
     args = ap.parse_args()
 
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -226,6 +227,29 @@ def main():
         t = torch.tensor([v], dtype=torch.float64, device="cuda")
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         return float(t.item())
+
+    if args.kernels_only:
+        res = {}
+        for prec in (thermo.MIXED, thermo.MIXED_BF16S, thermo.FP64):
+            sv = make(prec)
+            sv.set_density(x_d, pr["p"], pr["kmin"], pr["kmax"])
+            t0 = time.perf_counter()
+            sv.setup_precond()
+            torch.cuda.synchronize()
+            ts = time.perf_counter() - t0
+            u, info = sv.solve(tol=args.tol)
+            ks = {}
+            for k in range(11):
+                try:
+                    ms, by = sv.bench_kernel(k, 10)
+                    ks[k] = (round(ms, 4), round(by / (ms * 1e-3) / 1e9, 1) if by else None)
+                except Exception:
+                    pass
+            res[prec] = {"setup_s": ts, "iters": info["iters"], "solve_s": info["t_solve_ms"] / 1e3,
+                         "rel": info["rel_res_true"], "kernels_ms_GBps": ks}
+            sv.close()
+        print(json.dumps(res))
+        return 0
 
     if args.profile_kernel is not None or args.profile_solve:
         s = make(args.prec)

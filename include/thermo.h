@@ -186,7 +186,8 @@ void thermo_destroy(thermo_ctx *ctx);
 thermo_status thermo_apply(thermo_ctx *ctx, int precision, const double *u, double *y);
 
 /* z = B r: one MMG V-cycle (Algorithm 1) in the context's precision.
- * r, z: device double[nodes].  Requires setup_precond. */
+ * r, z: device double[nodes]; entries of r on Gamma_D are ignored (treated as
+ * zero) and z vanishes there.  Requires setup_precond. */
 thermo_status thermo_vcycle(thermo_ctx *ctx, const double *r, double *z);
 
 /* The assembled load vector f (device double[nodes]). */

@@ -83,16 +83,50 @@ __device__ __forceinline__ C stencil(const C (&vm)[3][3], const C (&v0)[3][3], c
   return y;
 }
 
-template <class S, class To, int OP, bool CUBE, int L1, bool DOT>
+// cp.async helpers (asynchronous global -> shared copies, completion by group)
+__device__ __forceinline__ void cp_async_n(void* smem, const void* gmem, int bytes) {
+  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+  if (bytes == 4)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
+  else if (bytes == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
+  else
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+// Stage layout (per plane): the node tile spans x in [x0 - SX, x0 - SX + VW),
+// y in [y0 - 1, y0 + TY + 2); the element tile spans x in [x0 - SX, x0 - SX + KW),
+// y in [y0 - 1, y0 + TY + 1).  SX = 2 for 2-byte storage (4-byte copy units
+// must start on an even index), else 1.  Copies move U = 4 bytes (or one
+// element if wider) per cp.async.
+template <class S>
+struct Stage {
+  static constexpr int SX = sizeof(S) == 2 ? 2 : 1;
+  static constexpr int EPU = sizeof(S) == 2 ? 2 : 1;  // elements per copy unit
+};
+
+template <class S, class To, int OP, bool CUBE, int L1, bool DOT, bool MASKIN, int NS>
 __global__ void __launch_bounds__(FINE_NT) fine_tile(FineArgs<S, To> a) {
   typedef typename Cv<S>::C C;
+  constexpr int SX = Stage<S>::SX, EPU = Stage<S>::EPU;
+  constexpr int LP = L1 > 0 ? L1 : 1;
   const Geom& g = a.g;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int TX = g.TX, TY = g.TY;
-  const int VW = TX + 3, VH = TY + 3, KW = TX + 2, KH = TY + 2;
-  C* vbuf = reinterpret_cast<C*>(smem_raw);
-  C* kbuf = vbuf + 2 * VW * VH;
-  C* red = kbuf + 2 * KW * KH;  // RESTRICT scratch [(TX+1)(TY+1)][L1]
+  const int VW = ((TX + 2 + SX) + EPU - 1) / EPU * EPU, VH = TY + 3;
+  const int KW = ((TX + 1 + SX) + EPU - 1) / EPU * EPU, KH = TY + 2;
+  const int VS = VW * VH, KS = KW * KH;  // elements per stage
+  S* vbuf = reinterpret_cast<S*>(smem_raw);                       // [NS][VS]
+  S* kbuf = vbuf + NS * VS;                                       // [NS][KS]
+  size_t off = ((size_t)NS * (VS + KS) * sizeof(S) + 15) & ~(size_t)15;
+  C* phis = reinterpret_cast<C*>(smem_raw + off);                 // [NS][VS][L1] (PSMOOTH)
+  if (OP == F_PSMOOTH) off += (size_t)NS * VS * LP * sizeof(C);
+  C* red = reinterpret_cast<C*>(smem_raw + off);                  // RESTRICT scratch
   __shared__ double dsh[32];
   __shared__ C cc[8];
   const int tid = threadIdx.x;
@@ -105,7 +139,65 @@ __global__ void __launch_bounds__(FINE_NT) fine_tile(FineArgs<S, To> a) {
   const int x = x0 + tx, y = y0 + ty;
   const bool mapped = ty <= TY;
   const bool active = mapped && (tx < TX || lastx) && (ty < TY || lasty);
-  const int rtx = mapped ? tx : 0, rty = mapped ? ty : 0;  // safe smem read coords
+  const int rtx = mapped ? tx : 0, rty = mapped ? ty : 0;
+
+  // per-thread copy slots (computed once): smem index and offset within a plane
+  const int nvu = VS / EPU, nku = KS / EPU;
+  const int vslots = (nvu + FINE_NT - 1) / FINE_NT, kslots = (nku + FINE_NT - 1) / FINE_NT;
+  int vso[3], vgo[3], kso[3], kgo[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int u = tid + k * FINE_NT;
+    vso[k] = -1;
+    kso[k] = -1;
+    if (k < vslots && u < nvu) {
+      const int e = u * EPU, lx = e % VW, ly = e / VW;
+      vso[k] = e;
+      vgo[k] = (int)(ly * g.P + lx);
+    }
+    if (k < kslots && u < nku) {
+      const int e = u * EPU, lx = e % KW, ly = e / KW;
+      kso[k] = e;
+      kgo[k] = (int)(ly * g.P + lx);
+    }
+  }
+  const long long vbase0 = nidx(g, x0 - SX, y0 - 1, 0) - (long long)g.RYn * g.P;  // plane -1 offset base
+  const long long kbase0 = eidx(g, x0 - SX, y0 - 1, 0) - (long long)g.RYe * g.P;
+  const long long vpl = (long long)g.RYn * g.P, kpl = (long long)g.RYe * g.P;
+  // node plane zz lives in stage (zz - zs + 1) % NS, element plane kk in (kk - zs + 1) % NS
+  auto issue = [&](int zz, int kk) {
+    if (OP != F_DIAG && zz <= ze + 1) {
+      S* dst = vbuf + ((zz - zs + 1) % NS) * VS;
+      const S* src = a.v + vbase0 + (long long)(zz + 1) * vpl;
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        if (vso[k] >= 0) cp_async_n(dst + vso[k], src + vgo[k], EPU * (int)sizeof(S));
+      if (OP == F_PSMOOTH) {
+        C* pd = phis + ((zz - zs + 1) % NS) * VS * LP;
+        const C* ps = a.phi + (vbase0 + (long long)(zz + 1) * vpl) * LP;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+          if (vso[k] >= 0)
+            for (int q = 0; q < EPU; ++q) {
+              const int e = vso[k] + q;
+              const long long go = (long long)vgo[k] + q;
+              if (LP * sizeof(C) % 16 == 0) {
+                for (int j = 0; j < LP; j += 16 / (int)sizeof(C)) cp_async_n(pd + e * LP + j, ps + go * LP + j, 16);
+              } else {
+                for (int j = 0; j < LP; ++j) cp_async_n(pd + e * LP + j, ps + go * LP + j, (int)sizeof(C));
+              }
+            }
+      }
+    }
+    if (kk >= zs - 1 && kk <= ze) {
+      S* dst = kbuf + ((kk - zs + 1) % NS) * KS;
+      const S* src = a.kap + kbase0 + (long long)(kk + 1) * kpl;
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        if (kso[k] >= 0) cp_async_n(dst + kso[k], src + kgo[k], EPU * (int)sizeof(S));
+    }
+    cp_commit();
+  };
 
   C vm[3][3], v0[3][3], vp[3][3], km[2][2], kp[2][2];
 #pragma unroll
@@ -116,54 +208,58 @@ __global__ void __launch_bounds__(FINE_NT) fine_tile(FineArgs<S, To> a) {
   for (int i = 0; i < 2; ++i)
 #pragma unroll
     for (int j = 0; j < 2; ++j) km[i][j] = kp[i][j] = C(0);
-
-  C acc[L1 > 0 ? L1 : 1];
+  C acc[LP];
 #pragma unroll
-  for (int j = 0; j < (L1 > 0 ? L1 : 1); ++j) acc[j] = C(0);
+  for (int j = 0; j < LP; ++j) acc[j] = C(0);
   double dacc = 0.0;
 
+  // prologue: node planes zs-1 .. zs+NS-3, element planes zs-2 .. zs+NS-4
+  for (int j = 0; j < NS - 1; ++j) issue(zs - 1 + j, zs - 2 + j);
+
   for (int t = zs - 2; t <= ze; ++t) {
-    const int buf = t & 1;
-    C* vb = vbuf + buf * VW * VH;
-    C* kb = kbuf + buf * KW * KH;
-    if (OP != F_DIAG) {
-      const int zz = t + 1;
-      for (int i = tid; i < VW * VH; i += FINE_NT) {
-        const int lx = i % VW, ly = i / VW;
-        const int xx = x0 - 1 + lx, yy = y0 - 1 + ly;
-        const long long n = nidx(g, xx, yy, zz);
-        C val = Cv<S>::ld(a.v + n);
-        if (OP == F_PSMOOTH && L1 > 0) {
-          if (xx >= 0 && yy >= 0 && zz >= 0 && xx <= g.Nx && yy <= g.Ny && zz <= g.Nz) {
-            const long long cell =
-                blk_of(xx, g.b, g.nbx) + (long long)g.nbx * (blk_of(yy, g.b, g.nby) + (long long)g.nby * blk_of(zz, g.b, g.nbz));
-#pragma unroll
-            for (int j = 0; j < (L1 > 0 ? L1 : 1); ++j) val += a.phi[n * L1 + j] * a.ec[cell * L1 + j];
-          }
-        }
-        if (is_dir(g, a.mask, xx, yy, zz)) val = C(0);
-        vb[i] = val;
-      }
-    }
-    if (t >= zs - 1) {
-      for (int i = tid; i < KW * KH; i += FINE_NT) {
-        const int lx = i % KW, ly = i / KW;
-        kb[i] = Cv<S>::ld(a.kap + eidx(g, x0 - 1 + lx, y0 - 1 + ly, t));
-      }
-    }
+    cp_wait<NS - 2>();
     __syncthreads();
+    const int vst = (t + 1 - zs + 1) % NS, kst = (t - zs + 1 + NS) % NS;
+    S* vb = vbuf + vst * VS;
+    if ((OP == F_PSMOOTH && L1 > 0) || MASKIN) {
+      // in-place fix-up of the landed node plane: prolongation and/or masking
+      const int zz = t + 1;
+#pragma unroll
+      for (int k = 0; k < 3; ++k)
+        if (vso[k] >= 0)
+          for (int q = 0; q < EPU; ++q) {
+            const int e = vso[k] + q;
+            const int lx = e % VW, ly = e / VW;
+            const int xx = x0 - SX + lx, yy = y0 - 1 + ly;
+            C val = Cv<S>::ld(vb + e);
+            if (OP == F_PSMOOTH && L1 > 0 && xx >= 0 && yy >= 0 && zz >= 0 && xx <= g.Nx && yy <= g.Ny &&
+                zz <= g.Nz) {
+              const long long cell = blk_of(xx, g.b, g.nbx) +
+                                     (long long)g.nbx * (blk_of(yy, g.b, g.nby) + (long long)g.nby * blk_of(zz, g.b, g.nbz));
+              const C* ph = phis + (vst * VS + e) * LP;
+#pragma unroll
+              for (int j = 0; j < LP; ++j) val += ph[j] * a.ec[cell * LP + j];
+            }
+            if (MASKIN && is_dir(g, a.mask, xx, yy, zz)) val = C(0);
+            Cv<S>::st(vb + e, val);
+          }
+      __syncthreads();
+    }
     if (OP != F_DIAG) {
 #pragma unroll
       for (int oy = 0; oy < 3; ++oy)
 #pragma unroll
-        for (int ox = 0; ox < 3; ++ox) vp[oy][ox] = vb[(rty + oy) * VW + rtx + ox];
+        for (int ox = 0; ox < 3; ++ox) vp[oy][ox] = Cv<S>::ld(vb + (rty + oy) * VW + rtx + ox + SX - 1);
     }
     if (t >= zs - 1) {
+      const S* kb = kbuf + kst * KS;
 #pragma unroll
       for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
-        for (int dx = 0; dx < 2; ++dx) kp[dy][dx] = kb[(rty + dy) * KW + rtx + dx];
+        for (int dx = 0; dx < 2; ++dx) kp[dy][dx] = Cv<S>::ld(kb + (rty + dy) * KW + rtx + dx + SX - 1);
     }
+    // prefetch: node plane t+NS into the stage of node plane t, element plane t+NS-1
+    issue(t + NS, t + NS - 1);
     if (t >= zs && active) {
       C K8;
       const C Av = stencil<C, CUBE>(vm, v0, vp, km, kp, cc, K8);
@@ -188,7 +284,7 @@ __global__ void __launch_bounds__(FINE_NT) fine_tile(FineArgs<S, To> a) {
         const C rr = Cv<S>::ld(a.r + n);
         const C s = dir ? C(0) : rr - Av;
 #pragma unroll
-        for (int j = 0; j < (L1 > 0 ? L1 : 1); ++j) acc[j] += s * a.phi[n * L1 + j];
+        for (int j = 0; j < LP; ++j) acc[j] += s * a.phi[n * LP + j];
       }
     }
     if (OP == F_RESTRICT && L1 > 0 && t >= zs) {
@@ -211,7 +307,6 @@ __global__ void __launch_bounds__(FINE_NT) fine_tile(FineArgs<S, To> a) {
           const long long cell = (x0 / g.b + lbx) + (long long)g.nbx * ((y0 / g.b + lby) + (long long)g.nby * bz);
           a.rc[cell * L1 + j] = s;
         }
-        __syncthreads();
 #pragma unroll
         for (int j = 0; j < L1; ++j) acc[j] = C(0);
       }
@@ -228,6 +323,7 @@ __global__ void __launch_bounds__(FINE_NT) fine_tile(FineArgs<S, To> a) {
 #pragma unroll
       for (int j = 0; j < 2; ++j) km[i][j] = kp[i][j];
   }
+  cp_wait<0>();
 
   if (DOT) {
     const double s = block_sum<FINE_NT>(dacc, dsh);
@@ -259,26 +355,28 @@ __global__ void __launch_bounds__(FINE_NT) fine_tile(FineArgs<S, To> a) {
 
 static dim3 fine_grid(const Geom& g) { return dim3(g.Nx / g.TX, g.Ny / g.TY, g.Nz / g.ZC); }
 
+constexpr int FINE_NS = 6;  // planes in the cp.async ring (NS - 1 in flight)
+
 template <class S>
-static size_t fine_smem(const Geom& g, int L1) {
+static size_t fine_smem(const Geom& g, int op, int L1) {
   typedef typename Cv<S>::C C;
-  size_t n = 2 * (size_t)(g.TX + 3) * (g.TY + 3) + 2 * (size_t)(g.TX + 2) * (g.TY + 2) +
-             (size_t)(g.TX + 1) * (g.TY + 1) * (L1 > 0 ? L1 : 0);
-  return n * sizeof(C);
+  const int SX = Stage<S>::SX, EPU = Stage<S>::EPU;
+  const int VW = ((g.TX + 2 + SX) + EPU - 1) / EPU * EPU, VH = g.TY + 3;
+  const int KW = ((g.TX + 1 + SX) + EPU - 1) / EPU * EPU, KH = g.TY + 2;
+  const int LP = L1 > 0 ? L1 : 1;
+  size_t n = ((size_t)FINE_NS * (VW * VH + KW * KH) * sizeof(S) + 15) & ~(size_t)15;
+  if (op == F_PSMOOTH) n += (size_t)FINE_NS * VW * VH * LP * sizeof(C);
+  if (op == F_RESTRICT) n += (size_t)(g.TX + 1) * (g.TY + 1) * LP * sizeof(C);
+  return n;
 }
 
-template <class S, class To, int OP, int L1, bool DOT>
+template <class S, class To, int OP, int L1, bool DOT, bool MASKIN = false>
 static cudaError_t launch_fine(const FineArgs<S, To>& a, int L1rt, cudaStream_t st) {
-  const size_t sm = fine_smem<S>(a.g, OP == F_RESTRICT ? L1rt : 0);
-  if (a.g.cube) {
-    auto k = fine_tile<S, To, OP, true, L1, DOT>;
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    note_launch(), k<<<fine_grid(a.g), FINE_NT, sm, st>>>(a);
-  } else {
-    auto k = fine_tile<S, To, OP, false, L1, DOT>;
-    if (sm > 48 * 1024) cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    note_launch(), k<<<fine_grid(a.g), FINE_NT, sm, st>>>(a);
-  }
+  const size_t sm = fine_smem<S>(a.g, OP, L1rt);
+  auto k = a.g.cube ? fine_tile<S, To, OP, true, L1, DOT, MASKIN, FINE_NS>
+                    : fine_tile<S, To, OP, false, L1, DOT, MASKIN, FINE_NS>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  note_launch(), k<<<fine_grid(a.g), FINE_NT, sm, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -297,12 +395,15 @@ static FineArgs<S, To> fargs(const Geom& g, const uint32_t* mask, const S* kap) 
   return a;
 }
 
-// y = A u (FP64), optionally dot = u . y (deterministic)
+// y = A u (FP64), optionally dot = u . y (deterministic).  mask_input: treat
+// the input as arbitrary on Gamma_D (zero it on load); otherwise the caller
+// guarantees u = 0 there (Krylov directions).
 cudaError_t fine_apply_f64(const Geom& g, const uint32_t* mask, const double* kap, const double* u, double* y,
-                           double* partial, unsigned* counter, double* dot, cudaStream_t st) {
+                           double* partial, unsigned* counter, double* dot, cudaStream_t st, bool mask_input) {
   auto a = fargs<double, double>(g, mask, kap);
   a.v = u;
   a.out = y;
+  if (mask_input) return launch_fine<double, double, F_APPLY, 0, false, true>(a, 0, st);
   if (dot) {
     a.partial = partial;
     a.counter = counter;
@@ -313,14 +414,18 @@ cudaError_t fine_apply_f64(const Geom& g, const uint32_t* mask, const double* ka
 }
 
 template <class S>
-cudaError_t fine_apply_lp(const Geom& g, const uint32_t* mask, const S* kap, const S* u, S* y, cudaStream_t st) {
+cudaError_t fine_apply_lp(const Geom& g, const uint32_t* mask, const S* kap, const S* u, S* y, cudaStream_t st,
+                          bool mask_input) {
   auto a = fargs<S, S>(g, mask, kap);
   a.v = u;
   a.out = y;
+  if (mask_input) return launch_fine<S, S, F_APPLY, 0, false, true>(a, 0, st);
   return launch_fine<S, S, F_APPLY, 0, false>(a, 0, st);
 }
-template cudaError_t fine_apply_lp<float>(const Geom&, const uint32_t*, const float*, const float*, float*, cudaStream_t);
-template cudaError_t fine_apply_lp<bf16>(const Geom&, const uint32_t*, const bf16*, const bf16*, bf16*, cudaStream_t);
+template cudaError_t fine_apply_lp<float>(const Geom&, const uint32_t*, const float*, const float*, float*, cudaStream_t,
+                                          bool);
+template cudaError_t fine_apply_lp<bf16>(const Geom&, const uint32_t*, const bf16*, const bf16*, bf16*, cudaStream_t,
+                                         bool);
 
 #define L1_DISPATCH(L1rt, CALL)                                  \
   switch (L1rt) {                                                \

@@ -7,9 +7,10 @@ namespace thermo {
 // ---- fine.cu
 unsigned fine_num_ctas(const Geom& g);
 cudaError_t fine_apply_f64(const Geom& g, const uint32_t* mask, const double* kap, const double* u, double* y,
-                           double* partial, unsigned* counter, double* dot, cudaStream_t st);
+                           double* partial, unsigned* counter, double* dot, cudaStream_t st, bool mask_input = false);
 template <class S>
-cudaError_t fine_apply_lp(const Geom& g, const uint32_t* mask, const S* kap, const S* u, S* y, cudaStream_t st);
+cudaError_t fine_apply_lp(const Geom& g, const uint32_t* mask, const S* kap, const S* u, S* y, cudaStream_t st,
+                          bool mask_input = false);
 template <class S, class To>
 cudaError_t fine_smooth(const Geom& g, const uint32_t* mask, const S* kap, const S* r, const S* e, To* out,
                         typename Cv<S>::C omega, cudaStream_t st);
@@ -59,6 +60,7 @@ cudaError_t cg_pupdate(const Geom& g, const void* z, int z_kind, double* p, cons
                        cudaStream_t st);
 cudaError_t vec_to_f64(const Geom& g, const void* src, int kind, double* dst, cudaStream_t st);
 cudaError_t fine_prolong_add(const Geom& g, const double* phi, int L1, const double* ec, double* u, cudaStream_t st);
+cudaError_t vec_mask_dir(const Geom& g, const uint32_t* bits, double* v, cudaStream_t st);
 cudaError_t fill_const(double* a, long long n, double v, cudaStream_t st);
 cudaError_t vec_axpy_pad(const Geom& g, double a, const double* x, double* y, cudaStream_t st);
 cudaError_t sensitivity(const Geom& g, const double* upad, const double* x, double p, double kmin, double kmax,

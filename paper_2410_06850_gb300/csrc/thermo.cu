@@ -603,7 +603,7 @@ static thermo_status read_scalars(thermo_ctx* ctx) {
 
 // true residual r = b - A u into ctx->r, ||r||^2 in sc->rr
 static thermo_status true_residual(thermo_ctx* ctx, const double* b) {
-  CK(fine_apply_f64(ctx->g, ctx->bits, ctx->k64, ctx->u, ctx->q, nullptr, nullptr, nullptr, ctx->st));
+  CK(fine_apply_f64(ctx->g, ctx->bits, ctx->k64, ctx->u, ctx->q, nullptr, nullptr, nullptr, ctx->st, true));
   CK(vec_residual(ctx->g, b, ctx->q, ctx->r, ctx->red, &ctx->sc->rr, ctx->st));
   return THERMO_OK;
 }
@@ -760,16 +760,16 @@ extern "C" thermo_status thermo_apply(thermo_ctx* ctx, int precision, const doub
   cudaStream_t st = ctx->st;
   CK(pack_nodes(g, u, ctx->tmp, st));
   if (precision == THERMO_FP64) {
-    CK(fine_apply_f64(g, ctx->bits, ctx->k64, ctx->tmp, ctx->q, nullptr, nullptr, nullptr, st));
+    CK(fine_apply_f64(g, ctx->bits, ctx->k64, ctx->tmp, ctx->q, nullptr, nullptr, nullptr, st, true));
   } else if (precision == THERMO_MIXED) {
     CK(vec_copy_cvt(g, ctx->tmp, ctx->ea32, 1, st));
-    CK(fine_apply_lp<float>(g, ctx->bits, ctx->k32, ctx->ea32, ctx->eb32, st));
+    CK(fine_apply_lp<float>(g, ctx->bits, ctx->k32, ctx->ea32, ctx->eb32, st, true));
     CK(vec_to_f64(g, ctx->eb32, 1, ctx->q, st));
   } else if (precision == THERMO_MIXED_BF16S) {
     bf16 *a16 = ctx->ea16, *b16 = ctx->eb16;
     if (!a16) return fail(ctx, THERMO_EINVAL, "BF16 buffers exist only for a MIXED_BF16S context");
     CK(vec_copy_cvt(g, ctx->tmp, a16, 2, st));
-    CK(fine_apply_lp<bf16>(g, ctx->bits, ctx->k16, a16, b16, st));
+    CK(fine_apply_lp<bf16>(g, ctx->bits, ctx->k16, a16, b16, st, true));
     CK(vec_to_f64(g, b16, 2, ctx->q, st));
   } else {
     return fail(ctx, THERMO_EINVAL, "unknown precision %d", precision);
@@ -785,6 +785,7 @@ extern "C" thermo_status thermo_vcycle(thermo_ctx* ctx, const double* r, double*
   const Geom& g = ctx->g;
   cudaStream_t st = ctx->st;
   CK(pack_nodes(g, r, ctx->r, st));
+  CK(vec_mask_dir(g, ctx->bits, ctx->r, st));  // the cycle assumes r = 0 on Gamma_D
   if (rkind(ctx) > 0) CK(vec_copy_cvt(g, ctx->r, rptr(ctx), rkind(ctx), st));
   CK(apply_precond(ctx));
   if (zkind(ctx) == 1) {

@@ -640,6 +640,21 @@ cudaError_t fine_prolong_add(const Geom& g, const double* phi, int L1, const dou
   return cudaGetLastError();
 }
 
+// v = 0 on Dirichlet nodes (padded FP64)
+__global__ void k_mask_dir(Geom g, const uint32_t* __restrict__ bits, double* __restrict__ v) {
+  const long long n = (long long)g.nx * g.ny * g.nz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % g.nx);
+    const long long t = i / g.nx;
+    const int y = (int)(t % g.ny), z = (int)(t / g.ny);
+    if (is_dir(g, bits, x, y, z)) v[nidx(g, x, y, z)] = 0.0;
+  }
+}
+cudaError_t vec_mask_dir(const Geom& g, const uint32_t* bits, double* v, cudaStream_t st) {
+  note_launch(), k_mask_dir<<<grid1((long long)g.nx * g.ny * g.nz), 256, 0, st>>>(g, bits, v);
+  return cudaGetLastError();
+}
+
 __global__ void k_fill(double* __restrict__ a, long long n, double v) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     a[i] = v;
