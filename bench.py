@@ -254,7 +254,8 @@ def main():
     if args.profile_kernel is not None or args.profile_solve:
         s = make(args.prec)
         s.set_density(x_d, pr["p"], pr["kmin"], pr["kmax"])
-        s.setup_precond()
+        if args.profile_kernel is None or args.profile_kernel in (4, 5, 6, 8, 9):
+            s.setup_precond()
         if args.profile_kernel is not None:
             ms, by = s.bench_kernel(args.profile_kernel, 3)
             print(json.dumps({"kernel": args.profile_kernel, "ms": ms, "bytes": by}))

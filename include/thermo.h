@@ -95,6 +95,11 @@ typedef struct {
   int max_iter;                     /* default 10000 */
   int flexible;                     /* -1 auto (flexible iff prec != FP64), 0, 1 */
   int check_every;                  /* host convergence check every k iterations (>= 1) */
+  int smoother;                     /* fine smoother: 0 damped Jacobi (nu_fine sweeps, omega),
+                                       1 Chebyshev-accelerated Jacobi (default) */
+  int cheb_degree;                  /* Chebyshev: operator applications per smoothing (>= 1) */
+  double cheb_ratio;                /* Chebyshev interval [lmax/ratio, 1.1 lmax] of D^-1 A */
+  int power_iters;                  /* power iterations estimating lmax(D^-1 A) in set-up */
 } thermo_options;
 
 typedef struct {
@@ -110,8 +115,10 @@ typedef struct {
 /* Fill *opt with the defaults for an Nx x Ny x Nz grid: b = 4, L_1 = 4, then
  * groups of 2^3 cells down to a 4^3-cell coarsest level with L = 17 (the
  * second level keeps 8 vectors when there are more than two coarse levels),
- * nu_fine = 2, nu_coarse = 1, omega = 2/3, MIXED, MMG, coarse guess,
- * max_iter = 10000, flexible auto, check_every = 1.  Returns EINVAL if the
+ * Chebyshev fine smoother of degree 4 on [lmax/30, 1.1 lmax] (15 power
+ * iterations), nu_fine = 2 / omega = 2/3 for the Jacobi alternative,
+ * nu_coarse = 1, MIXED, MMG, coarse guess, max_iter = 10000, flexible auto,
+ * check_every = 1.  Returns EINVAL if the
  * grid is not a multiple of 4 in each axis. */
 thermo_status thermo_default_options(const int grid[3], thermo_options *opt);
 

@@ -22,9 +22,12 @@ Follows Sec. 3 of the paper step by step:
 * Galerkin coarse operators A_c = R_c A R_c^T, A_cc = R_cc A_c R_cc^T (Sec. 3).
 * Smoothed V-cycle, Algorithm 1 (generalised to any number of levels, with
   the coarsest "correction" read as a solve with A_cc, i.e. A_cc^{-1} r_cc).
-  Fine smoother: nu damped-Jacobi sweeps; coarse smoother: l1-block-Jacobi
-  over each cell's L x L block (the paper's block-Jacobi, Sec. 4); both are
-  symmetric, so S^{-T} = S^{-1}.  Coarsest: dense Cholesky (the paper uses a
+  Fine smoother: nu damped-Jacobi sweeps, or (default) Chebyshev-accelerated
+  Jacobi of degree m on [lmax/30, 1.1 lmax] of D^-1 A -- the paper smooths
+  with block-Jacobi inside PETSc's Krylov smoothers (Sec. 4), whose
+  multigrid default is Chebyshev; coarse smoother: l1-block-Jacobi over each
+  cell's L x L block.  Both are polynomials in / inverses of symmetric
+  operators applied identically before and after, so S^{-T} = S^{-1}.  Coarsest: dense Cholesky (the paper uses a
   sparse LU; A_cc is SPD so the solves agree).
 
 Parity pins (tests/test_oracle_mmg.py): two-level exactness with a complete
@@ -47,9 +50,13 @@ class MMGOptions:
     block: int = 4                      # b: block edge in fine elements
     nvec: tuple = (4, 17)               # L_1, L_2, ... (one per coarse level)
     group: tuple = (2,)                 # g_2, g_3, ... (one per level >= 2)
-    nu_fine: int = 2
+    nu_fine: int = 2                    # damped-Jacobi sweeps (smoother = "jacobi")
     nu_coarse: int = 1
     omega: float = 2.0 / 3.0
+    smoother: str = "jacobi"            # fine smoother: "jacobi" or "chebyshev"
+    cheb_degree: int = 4                # Chebyshev: matrix-vector products per smoothing
+    cheb_ratio: float = 30.0            # interval [lmax / ratio, 1.1 lmax] of D^-1 A
+    power_iters: int = 15               # power iterations for lmax(D^-1 A)
 
     def __post_init__(self):
         self.nvec = tuple(int(v) for v in self.nvec)
@@ -58,7 +65,7 @@ class MMGOptions:
             raise ValueError("need one group size per level >= 2")
 
 
-def default_options(N: int) -> MMGOptions:
+def default_options(N: int, smoother: str = "chebyshev") -> MMGOptions:
     """Hierarchy used for an N^3 grid: b = 4, L_1 = 4, then groups of 2^3
     cells down to a 4^3-cell coarsest level with L = 17 (1,088 unknowns);
     the second level keeps L = 8 when the hierarchy has more than three grids
@@ -70,11 +77,11 @@ def default_options(N: int) -> MMGOptions:
         m //= 2
         levels.append(m)
     if not levels:
-        return MMGOptions(block=4, nvec=(4,), group=())
+        return MMGOptions(block=4, nvec=(4,), group=(), smoother=smoother)
     nvec = [4]
     for i, _ in enumerate(levels):
         nvec.append(8 if (i == 0 and len(levels) > 1) else 17)
-    return MMGOptions(block=4, nvec=tuple(nvec), group=(2,) * len(levels))
+    return MMGOptions(block=4, nvec=tuple(nvec), group=(2,) * len(levels), smoother=smoother)
 
 
 @dataclass
@@ -86,6 +93,43 @@ class Level:
     active: np.ndarray = None         # per-dof flag (False: zero basis vector)
     smoother: list = field(default_factory=list)  # per-cell inverse of the l1 block
     eigvals: list = field(default_factory=list)
+
+
+def power_start(n):
+    """Deterministic start vector of the power iteration: 1 + (i mod 7)/7."""
+    return 1.0 + (np.arange(n) % 7) / 7.0
+
+
+def lmax_estimate(A, D, free, iters):
+    """Power iteration for the largest eigenvalue of D^-1 A on the free nodes:
+    v <- D^-1 A v / ||D^-1 A v||, estimate ||D^-1 A v|| for the last unit v."""
+    v = power_start(A.shape[0]) * free
+    v /= np.linalg.norm(v)
+    lam = 0.0
+    for _ in range(iters):
+        w = (A @ v) / D * free
+        lam = np.linalg.norm(w)
+        v = w / lam
+    return lam
+
+
+def chebyshev_coefficients(lmax, ratio, degree):
+    """Chebyshev smoother on [lmax/ratio, 1.1 lmax] for D^-1 A, as the
+    three-term recurrence  e_{k+1} = e_k + a_k (e_k - e_{k-1}) + b_k D^-1 (r - A e_k)
+    (a_0 = 0).  Its error propagation is the scaled Chebyshev polynomial
+    T_m((hi + lo - 2 lam)/(hi - lo)) / T_m((hi + lo)/(hi - lo)), m = degree.
+    Returns lists (a, b) of length degree."""
+    lo, hi = lmax / ratio, 1.1 * lmax
+    theta, delta = 0.5 * (hi + lo), 0.5 * (hi - lo)
+    sigma = theta / delta
+    rho = 1.0 / sigma
+    a, b = [0.0], [1.0 / theta]
+    for _ in range(1, degree):
+        rho_new = 1.0 / (2.0 * sigma - rho)
+        a.append(rho_new * rho)
+        b.append(2.0 * rho_new / delta)
+        rho = rho_new
+    return a, b
 
 
 def node_blocks(grid, b, mask):
@@ -254,6 +298,10 @@ class MMG:
         self.D0 = A.diagonal().copy()
         o = self.opts
         P1, act, eig, fine_cell, shape = level1_basis(prob, o)
+        if o.smoother == "chebyshev":
+            free = (~prob["mask"]).astype(float)
+            self.lmax = lmax_estimate(A, self.D0, free, o.power_iters)
+            self.cheb = chebyshev_coefficients(self.lmax, o.cheb_ratio, o.cheb_degree)
         self.levels = [Level(shape=shape, L=o.nvec[0], P=P1, active=act, eigvals=eig)]
         self.levels[0].A = _galerkin(A, P1, act)
         Pcomp = P1
@@ -291,22 +339,46 @@ class MMG:
     def _A(self, l):
         return self.A0 if l == 0 else self.levels[l - 1].A
 
+    def _chebyshev(self, r, e):
+        """Chebyshev smoothing on the fine grid from the iterate e."""
+        a, b = self.cheb
+        prev = e
+        for k in range(len(a)):
+            new = e + b[k] * (r - self.A0 @ e) / self.D0
+            if k > 0:
+                new = new + a[k] * (e - prev)
+            prev, e = e, new
+        return e
+
+    def _presmooth(self, l, r):
+        e = np.zeros_like(r)
+        if l == 0 and self.opts.smoother == "chebyshev":
+            return self._chebyshev(r, e)
+        nu = self.opts.nu_fine if l == 0 else self.opts.nu_coarse
+        for _ in range(nu):
+            e = self._smooth(l, r, e)
+        return e
+
+    def _postsmooth(self, l, r, e):
+        if l == 0 and self.opts.smoother == "chebyshev":
+            return self._chebyshev(r, e)
+        nu = self.opts.nu_fine if l == 0 else self.opts.nu_coarse
+        for _ in range(nu):
+            e = self._smooth(l, r, e)
+        return e
+
     def vcycle(self, r, l=0):
         """Algorithm 1 on grids l, l+1, ..., coarsest (recursive)."""
         nlev = len(self.levels)
         if l == nlev:
             return self.coarse_solve(r)
-        nu = self.opts.nu_fine if l == 0 else self.opts.nu_coarse
         A = self._A(l)
-        e = np.zeros_like(r)
-        for _ in range(nu):                       # pre-smoothing (from e = 0)
-            e = self._smooth(l, r, e)
+        e = self._presmooth(l, r)                 # pre-smoothing (from e = 0)
         P = self.levels[l].P
         rc = P.T @ (r - A @ e)                    # restriction of the residual
         ec = self.vcycle(rc, l + 1)
         e = e + P @ ec                            # prolongation
-        for _ in range(nu):                       # post-smoothing (S^{-T} = S^{-1})
-            e = self._smooth(l, r, e)
+        e = self._postsmooth(l, r, e)             # post-smoothing (S^{-T} = S^{-1})
         return e
 
     __call__ = vcycle

@@ -39,7 +39,10 @@ struct FineArgs {
   const C* phi;     // level-1 basis [nsize][L1]
   const C* ec;      // level-1 correction [cells][L1]
   C* rc;            // level-1 restricted residual [cells][L1]
-  C omega;
+  const S* w;       // SMOOTH: previous iterate of the three-term recurrence (may be null)
+  S* out2;          // PSMOOTH: also store the prolonged iterate (may be null)
+  C cA;             // coefficient of (v - w)
+  C omega;          // coefficient of D^-1 (r - A v)
   double* partial;  // dot partials, one per CTA
   unsigned* counter;
   double* dot;
@@ -271,10 +274,13 @@ __global__ void __launch_bounds__(FINE_NT) fine_tile(FineArgs<S, To> a) {
         Cv<To>::st(a.out + n, yv);
         if (DOT) dacc += (double)v0[1][1] * (double)yv;
       } else if (OP == F_SMOOTH || OP == F_PSMOOTH) {
+        // e' = v + cA (v - w) + omega D^-1 (r - A v)  (Jacobi: cA = 0)
         const C rr = Cv<S>::ld(a.r + n);
         C e = v0[1][1] + a.omega * (rr - Av) / (cc[0] * K8);
+        if (OP == F_SMOOTH && a.w) e += a.cA * (v0[1][1] - Cv<S>::ld(a.w + n));
         if (dir) e = C(0);
         Cv<To>::st(a.out + n, e);
+        if (OP == F_PSMOOTH && a.out2) Cv<S>::st(a.out2 + n, dir ? C(0) : v0[1][1]);
       } else if (OP == F_DIAG) {
         const C rr = Cv<S>::ld(a.r + n);
         C e = a.omega * rr / (cc[0] * K8);
@@ -440,14 +446,17 @@ template cudaError_t fine_apply_lp<bf16>(const Geom&, const uint32_t*, const bf1
   }
 
 // Fine part of the cycle, storage S (double / float / bf16), compute C.
+// One sweep e' = e + cA (e - w) + cB D^-1 (r - A e); e == nullptr: e' = cB D^-1 r.
 template <class S, class To>
-cudaError_t fine_smooth(const Geom& g, const uint32_t* mask, const S* kap, const S* r, const S* e, To* out,
-                        typename Cv<S>::C omega, cudaStream_t st) {
+cudaError_t fine_smooth(const Geom& g, const uint32_t* mask, const S* kap, const S* r, const S* e, const S* w,
+                        To* out, typename Cv<S>::C cA, typename Cv<S>::C cB, cudaStream_t st) {
   auto a = fargs<S, To>(g, mask, kap);
   a.r = r;
   a.v = e;
+  a.w = w;
   a.out = out;
-  a.omega = omega;
+  a.cA = cA;
+  a.omega = cB;
   if (e == nullptr) return launch_fine<S, To, F_DIAG, 0, false>(a, 0, st);
   return launch_fine<S, To, F_SMOOTH, 0, false>(a, 0, st);
 }
@@ -464,26 +473,28 @@ cudaError_t fine_restrict(const Geom& g, const uint32_t* mask, const S* kap, con
   return cudaSuccess;
 }
 
+// v = e + Phi ec (prolongation), out = v + cB D^-1 (r - A v); out2 (optional) = v
 template <class S, class To>
 cudaError_t fine_prolong_smooth(const Geom& g, const uint32_t* mask, const S* kap, const S* r, const S* e,
-                                const typename Cv<S>::C* phi, const typename Cv<S>::C* ec, To* out,
-                                typename Cv<S>::C omega, int L1, cudaStream_t st) {
+                                const typename Cv<S>::C* phi, const typename Cv<S>::C* ec, To* out, S* out2,
+                                typename Cv<S>::C cB, int L1, cudaStream_t st) {
   auto a = fargs<S, To>(g, mask, kap);
   a.r = r;
   a.v = e;
   a.phi = phi;
   a.ec = ec;
   a.out = out;
-  a.omega = omega;
+  a.out2 = out2;
+  a.omega = cB;
   L1_DISPATCH(L1, return (launch_fine<S, To, F_PSMOOTH, LL, false>(a, LL, st)));
   return cudaSuccess;
 }
 
-#define INST_FINE(S, To)                                                                                       \
-  template cudaError_t fine_smooth<S, To>(const Geom&, const uint32_t*, const S*, const S*, const S*, To*,   \
-                                          Cv<S>::C, cudaStream_t);                                           \
-  template cudaError_t fine_prolong_smooth<S, To>(const Geom&, const uint32_t*, const S*, const S*, const S*, \
-                                                  const Cv<S>::C*, const Cv<S>::C*, To*, Cv<S>::C, int,      \
+#define INST_FINE(S, To)                                                                                        \
+  template cudaError_t fine_smooth<S, To>(const Geom&, const uint32_t*, const S*, const S*, const S*, const S*, \
+                                          To*, Cv<S>::C, Cv<S>::C, cudaStream_t);                              \
+  template cudaError_t fine_prolong_smooth<S, To>(const Geom&, const uint32_t*, const S*, const S*, const S*,  \
+                                                  const Cv<S>::C*, const Cv<S>::C*, To*, S*, Cv<S>::C, int,    \
                                                   cudaStream_t);
 INST_FINE(double, double)
 INST_FINE(float, float)

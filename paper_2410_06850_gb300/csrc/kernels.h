@@ -12,15 +12,15 @@ template <class S>
 cudaError_t fine_apply_lp(const Geom& g, const uint32_t* mask, const S* kap, const S* u, S* y, cudaStream_t st,
                           bool mask_input = false);
 template <class S, class To>
-cudaError_t fine_smooth(const Geom& g, const uint32_t* mask, const S* kap, const S* r, const S* e, To* out,
-                        typename Cv<S>::C omega, cudaStream_t st);
+cudaError_t fine_smooth(const Geom& g, const uint32_t* mask, const S* kap, const S* r, const S* e, const S* w,
+                        To* out, typename Cv<S>::C cA, typename Cv<S>::C cB, cudaStream_t st);
 template <class S>
 cudaError_t fine_restrict(const Geom& g, const uint32_t* mask, const S* kap, const S* r, const S* e,
                           const typename Cv<S>::C* phi, typename Cv<S>::C* rc, int L1, cudaStream_t st);
 template <class S, class To>
 cudaError_t fine_prolong_smooth(const Geom& g, const uint32_t* mask, const S* kap, const S* r, const S* e,
-                                const typename Cv<S>::C* phi, const typename Cv<S>::C* ec, To* out,
-                                typename Cv<S>::C omega, int L1, cudaStream_t st);
+                                const typename Cv<S>::C* phi, const typename Cv<S>::C* ec, To* out, S* out2,
+                                typename Cv<S>::C cB, int L1, cudaStream_t st);
 
 // ---- vec.cu : device scalars of the Krylov loop
 struct CgScalars {
@@ -61,6 +61,8 @@ cudaError_t cg_pupdate(const Geom& g, const void* z, int z_kind, double* p, cons
 cudaError_t vec_to_f64(const Geom& g, const void* src, int kind, double* dst, cudaStream_t st);
 cudaError_t fine_prolong_add(const Geom& g, const double* phi, int L1, const double* ec, double* u, cudaStream_t st);
 cudaError_t vec_mask_dir(const Geom& g, const uint32_t* bits, double* v, cudaStream_t st);
+cudaError_t power_start(const Geom& g, const uint32_t* bits, double* v, cudaStream_t st);
+cudaError_t vec_scale(const Geom& g, double a, double* v, cudaStream_t st);
 cudaError_t fill_const(double* a, long long n, double v, cudaStream_t st);
 cudaError_t vec_axpy_pad(const Geom& g, double a, const double* x, double* y, cudaStream_t st);
 cudaError_t sensitivity(const Geom& g, const double* upad, const double* x, double p, double kmin, double kmax,

@@ -62,9 +62,13 @@ struct thermo_ctx {
   double* xd = nullptr;     // design copy (natural)
   double *f = nullptr, *blift = nullptr, *TD = nullptr, *zero64 = nullptr;
   double *u = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *bv = nullptr, *tmp = nullptr, *z64 = nullptr;
-  double *ea64 = nullptr, *eb64 = nullptr;
-  float *r32 = nullptr, *z32 = nullptr, *ea32 = nullptr, *eb32 = nullptr, *tmp32 = nullptr;
-  bf16 *r16 = nullptr, *ea16 = nullptr, *eb16 = nullptr;
+  double *ea64 = nullptr, *eb64 = nullptr, *ec64 = nullptr;
+  float *r32 = nullptr, *z32 = nullptr, *ea32 = nullptr, *eb32 = nullptr, *ec32 = nullptr, *tmp32 = nullptr;
+  bf16 *r16 = nullptr, *ea16 = nullptr, *eb16 = nullptr, *ec16 = nullptr;
+  // fine smoother coefficients: e' = e + sa[k] (e - e_prev) + sb[k] D^-1 (r - A e), k < nsweep
+  int nsweep = 2;
+  double sa[64], sb[64];
+  double lmax = 0.0;
   double* phi64 = nullptr;
   float* phi32 = nullptr;
   // levels 1..nlev (index 0 unused)
@@ -153,6 +157,10 @@ extern "C" thermo_status thermo_default_options(const int grid[3], thermo_option
   opt->max_iter = 10000;
   opt->flexible = -1;
   opt->check_every = 1;
+  opt->smoother = 1;
+  opt->cheb_degree = 4;
+  opt->cheb_ratio = 30.0;
+  opt->power_iters = 15;
   return THERMO_OK;
 }
 
@@ -185,7 +193,10 @@ extern "C" thermo_status thermo_create(const int grid[3], const double h[3], con
   if (b < 2 || b > 8) return fail(ctx, THERMO_EINVAL, "block must be in [2, 8]");
   if (opt.levels < 1 || opt.levels > THERMO_MAX_LEVELS) return fail(ctx, THERMO_EINVAL, "levels out of range");
   if (grid[0] % b || grid[1] % b || grid[2] % b) return fail(ctx, THERMO_EINVAL, "grid must be a multiple of block");
-  if (opt.nu_fine < 1 || opt.nu_coarse < 1) return fail(ctx, THERMO_EINVAL, "smoothing sweeps must be >= 1");
+  if (opt.nu_fine < 1 || opt.nu_coarse < 1 || opt.nu_fine > 64) return fail(ctx, THERMO_EINVAL, "smoothing sweeps must be in [1, 64]");
+  if (opt.smoother != 0 && opt.smoother != 1) return fail(ctx, THERMO_EINVAL, "smoother must be 0 (Jacobi) or 1 (Chebyshev)");
+  if (opt.smoother == 1 && (opt.cheb_degree < 1 || opt.cheb_degree > 64 || !(opt.cheb_ratio > 1.0) || opt.power_iters < 1))
+    return fail(ctx, THERMO_EINVAL, "Chebyshev needs 1 <= degree <= 64, ratio > 1, power_iters >= 1");
   if (opt.nvec[0] < 1 || opt.nvec[0] > 8 || opt.nvec[0] == 7)
     return fail(ctx, THERMO_EINVAL, "nvec[0] must be in {1..6, 8}");
   Geom& g = ctx->g;
@@ -290,9 +301,10 @@ extern "C" thermo_status thermo_create(const int grid[3], const double h[3], con
   }
   CK(dalloc(ctx, &ctx->ea64, ns));
   CK(dalloc(ctx, &ctx->eb64, ns));
-  for (float** pp : {&ctx->r32, &ctx->z32, &ctx->ea32, &ctx->eb32, &ctx->tmp32}) CK(dalloc(ctx, pp, ns));
+  CK(dalloc(ctx, &ctx->ec64, ns));
+  for (float** pp : {&ctx->r32, &ctx->z32, &ctx->ea32, &ctx->eb32, &ctx->ec32, &ctx->tmp32}) CK(dalloc(ctx, pp, ns));
   if (opt.prec == THERMO_MIXED_BF16S) {
-    for (bf16** pp : {&ctx->r16, &ctx->ea16, &ctx->eb16}) CK(dalloc(ctx, pp, ns));
+    for (bf16** pp : {&ctx->r16, &ctx->ea16, &ctx->eb16, &ctx->ec16}) CK(dalloc(ctx, pp, ns));
   }
   CK(dalloc(ctx, &ctx->phi64, ns * ctx->L1));
   CK(dalloc(ctx, &ctx->phi32, ns * ctx->L1));
@@ -402,6 +414,51 @@ extern "C" thermo_status thermo_setup_precond(thermo_ctx* ctx) {
   const Geom& g = ctx->g;
   const int L1 = ctx->L1;
   CK(cudaMemsetAsync(ctx->status_dev, 0, 4 * sizeof(int), st));
+  {
+    // fine smoother coefficients
+    const thermo_options& o = ctx->opt;
+    if (o.smoother == 1) {
+      // lmax(D^-1 A) by power iteration from a fixed start vector (FP64)
+      CK(power_start(g, ctx->bits, ctx->p, st));
+      CK(vec_dot(g, ctx->p, ctx->p, 0, ctx->red, ctx->dscal, st));
+      CK(cudaMemcpyAsync(ctx->dscal_h, ctx->dscal, sizeof(double), cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      CK(vec_scale(g, 1.0 / sqrt(ctx->dscal_h[0]), ctx->p, st));
+      double lam = 0.0;
+      for (int it = 0; it < o.power_iters; ++it) {
+        CK(fine_apply_f64(g, ctx->bits, ctx->k64, ctx->p, ctx->q, nullptr, nullptr, nullptr, st));
+        CK((fine_smooth<double, double>(g, ctx->bits, ctx->k64, ctx->q, nullptr, nullptr, ctx->p, 0.0, 1.0, st)));
+        CK(vec_dot(g, ctx->p, ctx->p, 0, ctx->red, ctx->dscal, st));
+        CK(cudaMemcpyAsync(ctx->dscal_h, ctx->dscal, sizeof(double), cudaMemcpyDeviceToHost, st));
+        CK(cudaStreamSynchronize(st));
+        lam = sqrt(ctx->dscal_h[0]);
+        if (!(lam > 0.0) || !std::isfinite(lam)) return fail(ctx, THERMO_EINVAL, "power iteration failed (lmax = %g)", lam);
+        CK(vec_scale(g, 1.0 / lam, ctx->p, st));
+      }
+      ctx->lmax = lam;
+      // Chebyshev on [lmax/ratio, 1.1 lmax]: three-term recurrence coefficients
+      const double lo = lam / o.cheb_ratio, hi = 1.1 * lam;
+      const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
+      double rho = 1.0 / sigma;
+      ctx->nsweep = o.cheb_degree;
+      ctx->sa[0] = 0.0;
+      ctx->sb[0] = 1.0 / theta;
+      for (int k = 1; k < o.cheb_degree; ++k) {
+        const double rn = 1.0 / (2.0 * sigma - rho);
+        ctx->sa[k] = rn * rho;
+        ctx->sb[k] = 2.0 * rn / delta;
+        rho = rn;
+      }
+      CK(cudaMemsetAsync(ctx->p, 0, g.nsize * sizeof(double), st));
+      CK(cudaMemsetAsync(ctx->q, 0, g.nsize * sizeof(double), st));
+    } else {
+      ctx->nsweep = o.nu_fine;
+      for (int k = 0; k < o.nu_fine; ++k) {
+        ctx->sa[k] = 0.0;
+        ctx->sb[k] = o.omega;
+      }
+    }
+  }
   Lev& l1 = ctx->lev[1];
   CK(level1_eigen(g, ctx->bits, ctx->k64, L1, ctx->phi64, l1.eig, l1.act, ctx->status_dev, st));
   CK(level1_rowsum_corr(g, ctx->bits, ctx->k64, L1, ctx->phi64, l1.ntc, ctx->gcum_dev, l1.Dc, st));
@@ -509,43 +566,60 @@ static cudaError_t coarse_cycle(thermo_ctx* ctx, int l) {
 }
 
 // One V-cycle z = B r on the fine grid; S storage, C = compute, output To.
+// Smoothing is the three-term sweep e' = e + a_k (e - e_prev) + b_k D^-1 (r - A e)
+// (damped Jacobi: a_k = 0, b_k = omega; Chebyshev: the recurrence coefficients),
+// applied from zero before restriction and from the prolonged iterate after.
 template <class S, class To>
-static cudaError_t vcycle_fine(thermo_ctx* ctx, const S* kap, const S* r, S* ea, S* eb, To* z) {
+static cudaError_t vcycle_fine(thermo_ctx* ctx, const S* kap, const S* r, S* b0, S* b1, S* b2, To* z) {
   typedef typename Cv<S>::C C;
   const Geom& g = ctx->g;
   cudaStream_t st = ctx->st;
-  const int nu = ctx->opt.nu_fine, L1 = ctx->L1;
-  const C om = (C)ctx->opt.omega;
-  const C* phi;
-  if (sizeof(C) == 8)
-    phi = (const C*)ctx->phi64;
-  else
-    phi = (const C*)ctx->phi32;
+  const int m = ctx->nsweep, L1 = ctx->L1;
+  const double* sa = ctx->sa;
+  const double* sb = ctx->sb;
+  const C* phi = (sizeof(C) == 8) ? (const C*)ctx->phi64 : (const C*)ctx->phi32;
   Lev& l1 = ctx->lev[1];
   C* rc = (sizeof(C) == 8) ? (C*)l1.r64 : (C*)l1.r32;
   C* ec = (sizeof(C) == 8) ? (C*)l1.e64 : (C*)l1.e32;
+  S* buf[3] = {b0, b1, b2};
   cudaError_t e;
-  S* E = ea;
-  S* F = eb;
-  if ((e = fine_smooth<S, S>(g, ctx->bits, kap, r, nullptr, E, om, st)) != cudaSuccess) return e;
-  for (int s = 1; s < nu; ++s) {
-    if ((e = fine_smooth<S, S>(g, ctx->bits, kap, r, E, F, om, st)) != cudaSuccess) return e;
-    std::swap(E, F);
+  // pre-smoothing from e_0 = 0
+  int cur = 0, prev = -1;
+  if ((e = fine_smooth<S, S>(g, ctx->bits, kap, r, nullptr, nullptr, buf[0], C(0), (C)sb[0], st)) != cudaSuccess)
+    return e;
+  for (int k = 1; k < m; ++k) {
+    const int nxt = prev >= 0 ? 3 - cur - prev : (cur + 1) % 3;
+    const S* w = (sa[k] != 0.0 && prev >= 0) ? buf[prev] : nullptr;
+    if ((e = fine_smooth<S, S>(g, ctx->bits, kap, r, buf[cur], w, buf[nxt], (C)sa[k], (C)sb[k], st)) != cudaSuccess)
+      return e;
+    prev = cur;
+    cur = nxt;
   }
-  if ((e = fine_restrict<S>(g, ctx->bits, kap, r, E, phi, rc, L1, st)) != cudaSuccess) return e;
+  if ((e = fine_restrict<S>(g, ctx->bits, kap, r, buf[cur], phi, rc, L1, st)) != cudaSuccess) return e;
   if (sizeof(C) == 8)
     e = coarse_cycle<double>(ctx, 1);
   else
     e = coarse_cycle<float>(ctx, 1);
   if (e != cudaSuccess) return e;
-  if (nu == 1) return fine_prolong_smooth<S, To>(g, ctx->bits, kap, r, E, phi, ec, z, om, L1, st);
-  if ((e = fine_prolong_smooth<S, S>(g, ctx->bits, kap, r, E, phi, ec, F, om, L1, st)) != cudaSuccess) return e;
-  std::swap(E, F);
-  for (int s = 1; s < nu - 1; ++s) {
-    if ((e = fine_smooth<S, S>(g, ctx->bits, kap, r, E, F, om, st)) != cudaSuccess) return e;
-    std::swap(E, F);
+  // post-smoothing from the prolonged iterate
+  if (m == 1) return fine_prolong_smooth<S, To>(g, ctx->bits, kap, r, buf[cur], phi, ec, z, nullptr, (C)sb[0], L1, st);
+  const int o1 = (cur + 1) % 3, o2 = (cur + 2) % 3;
+  const bool keep = sa[1] != 0.0;
+  if ((e = fine_prolong_smooth<S, S>(g, ctx->bits, kap, r, buf[cur], phi, ec, buf[o1], keep ? buf[o2] : nullptr,
+                                     (C)sb[0], L1, st)) != cudaSuccess)
+    return e;
+  cur = o1;
+  prev = o2;
+  for (int k = 1; k < m; ++k) {
+    const S* w = (sa[k] != 0.0) ? buf[prev] : nullptr;
+    if (k == m - 1) return fine_smooth<S, To>(g, ctx->bits, kap, r, buf[cur], w, z, (C)sa[k], (C)sb[k], st);
+    const int nxt = 3 - cur - prev;
+    if ((e = fine_smooth<S, S>(g, ctx->bits, kap, r, buf[cur], w, buf[nxt], (C)sa[k], (C)sb[k], st)) != cudaSuccess)
+      return e;
+    prev = cur;
+    cur = nxt;
   }
-  return fine_smooth<S, To>(g, ctx->bits, kap, r, E, z, om, st);
+  return cudaSuccess;
 }
 
 // z = B r where r is the FP64 residual already converted to the cycle's
@@ -554,10 +628,13 @@ static cudaError_t apply_precond(thermo_ctx* ctx) {
   const thermo_options& o = ctx->opt;
   const Geom& g = ctx->g;
   if (o.pc == THERMO_PC_NONE) return cudaMemcpyAsync(ctx->z64, ctx->r, g.nsize * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st);
-  if (o.pc == THERMO_PC_JACOBI) return fine_smooth<double, double>(g, ctx->bits, ctx->k64, ctx->r, nullptr, ctx->z64, 1.0, ctx->st);
-  if (o.prec == THERMO_FP64) return vcycle_fine<double, double>(ctx, ctx->k64, ctx->r, ctx->ea64, ctx->eb64, ctx->z64);
-  if (o.prec == THERMO_MIXED) return vcycle_fine<float, float>(ctx, ctx->k32, ctx->r32, ctx->ea32, ctx->eb32, ctx->z32);
-  return vcycle_fine<bf16, float>(ctx, ctx->k16, ctx->r16, ctx->ea16, ctx->eb16, ctx->z32);
+  if (o.pc == THERMO_PC_JACOBI)
+    return fine_smooth<double, double>(g, ctx->bits, ctx->k64, ctx->r, nullptr, nullptr, ctx->z64, 0.0, 1.0, ctx->st);
+  if (o.prec == THERMO_FP64)
+    return vcycle_fine<double, double>(ctx, ctx->k64, ctx->r, ctx->ea64, ctx->eb64, ctx->ec64, ctx->z64);
+  if (o.prec == THERMO_MIXED)
+    return vcycle_fine<float, float>(ctx, ctx->k32, ctx->r32, ctx->ea32, ctx->eb32, ctx->ec32, ctx->z32);
+  return vcycle_fine<bf16, float>(ctx, ctx->k16, ctx->r16, ctx->ea16, ctx->eb16, ctx->ec16, ctx->z32);
 }
 static int zkind(const thermo_ctx* ctx) {
   return (ctx->opt.pc != THERMO_PC_MMG || ctx->opt.prec == THERMO_FP64) ? 0 : 1;
@@ -932,15 +1009,16 @@ extern "C" thermo_status thermo_bench_kernel(thermo_ctx* ctx, int which, int rep
         bytes = n * 4 + M * 2;
         return fine_apply_lp<bf16>(g, ctx->bits, ctx->k16, ctx->ea16, ctx->eb16, st);
       case 3:
-        bytes = n * 12 + M * 4;
-        return fine_smooth<float, float>(g, ctx->bits, ctx->k32, ctx->r32, ctx->ea32, ctx->eb32, 0.6f, st);
+        bytes = n * 16 + M * 4;
+        return fine_smooth<float, float>(g, ctx->bits, ctx->k32, ctx->r32, ctx->ea32, ctx->ec32, ctx->eb32, 0.3f,
+                                         0.6f, st);
       case 4:
         bytes = n * (8 + 4 * L1) + M * 4;
         return fine_restrict<float>(g, ctx->bits, ctx->k32, ctx->r32, ctx->ea32, ctx->phi32, l1.r32, ctx->L1, st);
       case 5:
-        bytes = n * (12 + 4 * L1) + M * 4;
+        bytes = n * (16 + 4 * L1) + M * 4;
         return fine_prolong_smooth<float, float>(g, ctx->bits, ctx->k32, ctx->r32, ctx->ea32, ctx->phi32, l1.e32,
-                                                 ctx->eb32, 0.6f, ctx->L1, st);
+                                                 ctx->eb32, ctx->ec32, 0.6f, ctx->L1, st);
       case 6:
         bytes = (double)l1.cl.ncell * (27.0 * l1.cl.L * l1.cl.L + 2.0 * l1.cl.L) * 4.0;
         return coarse_apply<float>(l1.cl, l1.T32, l1.e32, l1.s32, st);
@@ -965,8 +1043,9 @@ extern "C" thermo_status thermo_bench_kernel(thermo_ctx* ctx, int which, int rep
         return e;
       }
       case 10:
-        bytes = n * 24 + M * 8;
-        return fine_smooth<double, double>(g, ctx->bits, ctx->k64, ctx->r, ctx->ea64, ctx->eb64, 0.6, st);
+        bytes = n * 32 + M * 8;
+        return fine_smooth<double, double>(g, ctx->bits, ctx->k64, ctx->r, ctx->ea64, ctx->ec64, ctx->eb64, 0.3, 0.6,
+                                           st);
       default:
         return cudaErrorInvalidValue;
     }

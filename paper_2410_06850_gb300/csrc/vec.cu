@@ -655,6 +655,36 @@ cudaError_t vec_mask_dir(const Geom& g, const uint32_t* bits, double* v, cudaStr
   return cudaGetLastError();
 }
 
+// deterministic start vector of the power iteration: 1 + (i mod 7)/7 at the
+// natural node index i, zero on Dirichlet nodes
+__global__ void k_power_start(Geom g, const uint32_t* __restrict__ bits, double* __restrict__ v) {
+  const long long n = (long long)g.nx * g.ny * g.nz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % g.nx);
+    const long long t = i / g.nx;
+    const int y = (int)(t % g.ny), z = (int)(t / g.ny);
+    v[nidx(g, x, y, z)] = is_dir(g, bits, x, y, z) ? 0.0 : 1.0 + (double)(i % 7) / 7.0;
+  }
+}
+cudaError_t power_start(const Geom& g, const uint32_t* bits, double* v, cudaStream_t st) {
+  note_launch(), k_power_start<<<grid1((long long)g.nx * g.ny * g.nz), 256, 0, st>>>(g, bits, v);
+  return cudaGetLastError();
+}
+__global__ void __launch_bounds__(VNT) k_scale(Geom g, Rows R, double a, double* __restrict__ v) {
+  for (long long it = blockIdx.x * (long long)VNT + threadIdx.x; it < R.items; it += (long long)gridDim.x * VNT) {
+    const long long i = item_index(g, it, R.ppr);
+    double2 x = ld2<double>(v + i);
+    x.x *= a;
+    x.y *= a;
+    st2<double>(v + i, x);
+  }
+}
+cudaError_t vec_scale(const Geom& g, double a, double* v, cudaStream_t st) {
+  Rows R = rows_of(g);
+  note_launch(), k_scale<<<vec_blocks(R.items), VNT, 0, st>>>(g, R, a, v);
+  return cudaGetLastError();
+}
+
 __global__ void k_fill(double* __restrict__ a, long long n, double v) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     a[i] = v;

@@ -34,7 +34,9 @@ class thermo_options(C.Structure):
     _fields_ = [("levels", C.c_int), ("block", C.c_int), ("group", C.c_int * MAX_LEVELS),
                 ("nvec", C.c_int * MAX_LEVELS), ("nu_fine", C.c_int), ("nu_coarse", C.c_int),
                 ("omega", C.c_double), ("prec", C.c_int), ("pc", C.c_int), ("guess", C.c_int),
-                ("max_iter", C.c_int), ("flexible", C.c_int), ("check_every", C.c_int)]
+                ("max_iter", C.c_int), ("flexible", C.c_int), ("check_every", C.c_int),
+                ("smoother", C.c_int), ("cheb_degree", C.c_int), ("cheb_ratio", C.c_double),
+                ("power_iters", C.c_int)]
 
 
 class thermo_solve_info(C.Structure):

@@ -213,3 +213,91 @@ def test_mmg_pcg_matches_direct_solve(density, kmin):
     _, ij = krylov.pcg(P["A"], P["b"], precond=krylov.jacobi_precond(P["A"]), tol=1e-12,
                        maxit=20000)
     assert info["iters"] * 3 < ij["iters"]
+
+
+def _cheb_poly(lam, lo, hi, m):
+    """Scaled Chebyshev polynomial T_m((hi+lo-2 lam)/(hi-lo)) / T_m((hi+lo)/(hi-lo))."""
+    def T(x):
+        x = np.asarray(x, float)
+        out = np.empty_like(x)
+        inside = np.abs(x) <= 1
+        out[inside] = np.cos(m * np.arccos(x[inside]))
+        xo = x[~inside]
+        out[~inside] = np.sign(xo) ** m * np.cosh(m * np.arccosh(np.abs(xo)))
+        return out
+    return T((hi + lo - 2 * lam) / (hi - lo)) / T(np.array([(hi + lo) / (hi - lo)]))[0]
+
+
+def test_lmax_estimate_below_and_close_to_true():
+    P = _prob(N=6, seed=12, kmin=1e-4)
+    A = P["A"].toarray()
+    D = np.diag(A)
+    free = ~P["mask"]
+    Af = A[np.ix_(free, free)]
+    Df = D[free]
+    lam_true = np.linalg.eigvalsh(Af / np.sqrt(Df)[:, None] / np.sqrt(Df)[None, :]).max()
+    est = mmg.lmax_estimate(P["A"], D, free.astype(float), 15)
+    assert est <= lam_true * (1 + 1e-12)
+    assert est >= 0.85 * lam_true
+
+
+@pytest.mark.parametrize("m", [2, 3, 4])
+def test_chebyshev_smoother_is_scaled_chebyshev_polynomial(m):
+    """The smoother's error propagation (r = A e*, start e = 0, error e* - e)
+    equals p(D^-1 A) with p the scaled Chebyshev polynomial on [lo, hi]."""
+    P = _prob(N=4, seed=13, kmin=1e-3)
+    o = mmg.MMGOptions(block=2, nvec=(4,), group=(), smoother="chebyshev", cheb_degree=m)
+    H = mmg.MMG(P, o)
+    A = P["A"].toarray()
+    D = np.diag(A)
+    free = ~P["mask"]
+    Af = A[np.ix_(free, free)]
+    s = 1 / np.sqrt(D[free])
+    lam, V = np.linalg.eigh(Af * s[:, None] * s[None, :])
+    lo, hi = H.lmax / 30.0, 1.1 * H.lmax
+    p = _cheb_poly(lam, lo, hi, m)
+    Efree = (s[:, None] * V) @ np.diag(p) @ (V.T / s[None, :])   # D^-1/2 p(C) D^1/2
+    n = A.shape[0]
+    idx = np.flatnonzero(free)
+    for j in [0, 7, len(idx) - 1]:
+        estar = np.zeros(n)
+        estar[idx[j]] = 1.0
+        e = H._chebyshev(A @ estar, np.zeros(n))
+        np.testing.assert_allclose((estar - e)[free], Efree[:, j], atol=1e-12)
+
+
+def test_vcycle_closed_form_with_chebyshev():
+    P = _prob(N=8, seed=22)
+    o = mmg.MMGOptions(block=2, nvec=(4, 6), group=(2,), smoother="chebyshev", cheb_degree=3)
+    H = mmg.MMG(P, o)
+    A = P["A"].toarray()
+    D = np.diag(A)
+    free = ~P["mask"]
+    s = 1 / np.sqrt(D)
+    lam, V = np.linalg.eigh(A * s[:, None] * s[None, :])
+    lo, hi = H.lmax / 30.0, 1.1 * H.lmax
+    Sfine = (s[:, None] * V) @ np.diag(_cheb_poly(lam, lo, hi, 3)) @ (V.T / s[None, :])
+    mats = [lev.A.toarray() for lev in H.levels]
+    Ps = [lev.P.toarray() for lev in H.levels]
+    L = H.levels[0].L
+    A1 = mats[0]
+    W1 = np.zeros_like(A1)
+    for c in range(A1.shape[0] // L):
+        sl = slice(c * L, (c + 1) * L)
+        off = np.abs(A1[sl]).sum(axis=1) - np.abs(A1[sl, sl]).sum(axis=1)
+        W1[sl, sl] = np.linalg.inv(A1[sl, sl] + np.diag(off))
+    I1 = np.eye(A1.shape[0])
+    S1 = I1 - W1 @ A1
+    E1 = S1 @ (I1 - Ps[1] @ np.linalg.inv(mats[1]) @ Ps[1].T @ A1) @ S1
+    B1 = (I1 - E1) @ np.linalg.inv(A1)
+    # Dirichlet rows are identities; the smoother leaves them at zero
+    Sf = np.where(free[:, None] & free[None, :], Sfine, 0.0)
+    I = np.eye(A.shape[0])
+    Sf = Sf + np.diag((~free).astype(float)) * 0.0
+    E = Sf @ (I - Ps[0] @ B1 @ Ps[0].T @ A) @ Sf
+    Ainv = np.linalg.inv(A)
+    B = (I - E) @ Ainv
+    for j in np.flatnonzero(free)[[0, 11, 100, -1]]:
+        ej = np.zeros(A.shape[0])
+        ej[j] = 1.0
+        np.testing.assert_allclose(H(ej)[free], B[free, j], rtol=1e-9, atol=1e-12 * np.abs(B).max())
