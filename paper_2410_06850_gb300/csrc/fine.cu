@@ -1,14 +1,19 @@
 // Fine-grid kernels: matrix-free Q1 operator and the fine part of the
 // multigrid cycle (Sec. 3, Algorithm 1).
 //
-// One z-marching tile engine serves every fine-grid pass.  A CTA owns a
-// TX x TY tile of nodes (block-aligned; the tile on the high face of an axis
-// also owns the closing node plane) and marches over ZC node planes.  Per
-// plane it stages the next node plane of the input field (with a one-node
-// halo) and the next element plane of conductivity in shared memory (double
-// buffered, one barrier per plane); each thread keeps its 3x3 column of the
-// two previous node planes and 2x2 conductivities of the previous element
-// plane in registers, so a node costs 9 + 4 shared loads.
+// One z-marching engine serves every fine-grid pass.  A CTA (4 warps) owns a
+// TX x TY tile of nodes (TX <= 32 columns = lanes, TY = 4 rows per warp, so a
+// warp covers exactly one row of level-1 blocks) and marches over ZC node
+// planes.  Planes of the input field (with a one-node halo), of the element
+// conductivity and of the Dirichlet bitmask are staged in shared memory by
+// 16-byte cp.async copies through a 7-stage ring, so four planes are in
+// flight while one is computed.  In the FP32/BF16 kernels each lane keeps
+// the 3x3 windows of its rows for the two previous planes in registers
+// (z unrolled by three, so the windows rotate without moves) and reads only
+// the new plane from shared memory; the FP64 kernel (ALU-bound) reads its
+// windows from the resident stages.  The tile on the high face of an axis
+// also owns the closing node plane: lane TX-1 computes the extra column and
+// the last warp a fifth row.
 //
 // Operator (node-centred gather of A = sum_e kappa_e K0_e, K0[a][b] =
 // c[a ^ b]): with the 8 elements around node i indexed (dx,dy,dz),
@@ -16,16 +21,36 @@
 //           + c7 sum_diag kappa v  [+ c1/c2/c4 axis terms, non-cubic boxes]
 // where K8 is the sum of the 8 conductivities and zp/yp/xp are sums of the
 // two elements sharing an edge (Sec. 2.2 Eq. (5) realised for Q1).
-// Dirichlet nodes: inputs are masked to zero on load (no coupling to
-// Gamma_D columns) and the row is the identity.
+// Dirichlet rows are identities.  Inputs of the hot kernels vanish on
+// Gamma_D by construction (Krylov directions, cycle iterates); the
+// MASKIN variants zero them on load for arbitrary inputs.
 #include "common.cuh"
 #include "kernels.h"
 
 namespace thermo {
 
-enum FineOp { F_APPLY = 0, F_SMOOTH = 1, F_DIAG = 2, F_RESTRICT = 3, F_PSMOOTH = 4 };
+enum FineOp { F_APPLY = 0, F_SMOOTH = 1, F_RESTRICT = 3 };
 
-constexpr int FINE_NT = 320;  // >= (TX+1)(TY+1) = 297 for 32 x 8 tiles
+constexpr int FW = 4;            // warps per CTA
+constexpr int FNT = 32 * FW;     // threads per CTA
+constexpr int RYW = 4;           // rows per warp (= level-1 block edge)
+constexpr int TYM = FW * RYW;    // rows per tile (max)
+constexpr int VHM = TYM + 3;     // staged node rows: y0-1 .. y0+TY+1
+constexpr int KHM = TYM + 2;     // staged element rows: y0-1 .. y0+TY
+constexpr int MWR = 2;           // mask words staged per row
+constexpr int FNS = 7;           // ring stages
+
+template <class S>
+struct Tile {
+  static constexpr int EPC = 16 / (int)sizeof(S);      // elements per 16-byte chunk
+  static constexpr int SX = EPC >= 8 ? 8 : 4;           // staged rows start at x0 - SX
+  static constexpr int W = sizeof(S) == 2 ? 48 : 40;    // staged row width (elements)
+  static constexpr int CPR = W / EPC;                   // chunks per row
+  static constexpr size_t VB = (size_t)VHM * W * sizeof(S);
+  static constexpr size_t KB = (size_t)KHM * W * sizeof(S);
+  static constexpr size_t MB = (size_t)(TYM + 1) * MWR * 4;
+  static constexpr size_t STB = (VB + KB + MB + 15) & ~(size_t)15;  // bytes per stage
+};
 
 template <class S, class To>
 struct FineArgs {
@@ -37,10 +62,8 @@ struct FineArgs {
   To* out;
   const uint32_t* mask;
   const C* phi;     // level-1 basis [nsize][L1]
-  const C* ec;      // level-1 correction [cells][L1]
   C* rc;            // level-1 restricted residual [cells][L1]
   const S* w;       // SMOOTH: previous iterate of the three-term recurrence (may be null)
-  S* out2;          // PSMOOTH: also store the prolonged iterate (may be null)
   C cA;             // coefficient of (v - w)
   C omega;          // coefficient of D^-1 (r - A v)
   double* partial;  // dot partials, one per CTA
@@ -102,257 +125,329 @@ __device__ __forceinline__ void cp_wait() {
   asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
 }
 
-// Stage layout (per plane): the node tile spans x in [x0 - SX, x0 - SX + VW),
-// y in [y0 - 1, y0 + TY + 2); the element tile spans x in [x0 - SX, x0 - SX + KW),
-// y in [y0 - 1, y0 + TY + 1).  SX = 2 for 2-byte storage (4-byte copy units
-// must start on an even index), else 1.  Copies move U = 4 bytes (or one
-// element if wider) per cp.async.
-template <class S>
-struct Stage {
-  static constexpr int SX = sizeof(S) == 2 ? 2 : 1;
-  static constexpr int EPU = sizeof(S) == 2 ? 2 : 1;  // elements per copy unit
-};
-
-template <class S, class To, int OP, bool CUBE, int L1, bool DOT, bool MASKIN, int NS>
-__global__ void __launch_bounds__(FINE_NT) fine_tile(FineArgs<S, To> a) {
+template <class S, class To, int OP, bool CUBE, int L1, bool DOT, bool MASKIN, bool ROLL>
+__global__ void __launch_bounds__(FNT) fine_tile(FineArgs<S, To> a) {
   typedef typename Cv<S>::C C;
-  constexpr int SX = Stage<S>::SX, EPU = Stage<S>::EPU;
+  typedef Tile<S> T;
+  constexpr int SX = T::SX, W = T::W, CPR = T::CPR, EPC = T::EPC;
   constexpr int LP = L1 > 0 ? L1 : 1;
   const Geom& g = a.g;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int TX = g.TX, TY = g.TY;
-  const int VW = ((TX + 2 + SX) + EPU - 1) / EPU * EPU, VH = TY + 3;
-  const int KW = ((TX + 1 + SX) + EPU - 1) / EPU * EPU, KH = TY + 2;
-  const int VS = VW * VH, KS = KW * KH;  // elements per stage
-  S* vbuf = reinterpret_cast<S*>(smem_raw);                       // [NS][VS]
-  S* kbuf = vbuf + NS * VS;                                       // [NS][KS]
-  size_t off = ((size_t)NS * (VS + KS) * sizeof(S) + 15) & ~(size_t)15;
-  C* phis = reinterpret_cast<C*>(smem_raw + off);                 // [NS][VS][L1] (PSMOOTH)
-  if (OP == F_PSMOOTH) off += (size_t)NS * VS * LP * sizeof(C);
-  C* red = reinterpret_cast<C*>(smem_raw + off);                  // RESTRICT scratch
-  __shared__ double dsh[32];
+  __shared__ double dsh[33];
   __shared__ C cc[8];
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   if (tid < 8) cc[tid] = (C)g.c[tid];
-  const int tx = tid % (TX + 1), ty = tid / (TX + 1);
+  const int TX = g.TX, TY = g.TY;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const bool lastx = (x0 + TX == g.Nx), lasty = (y0 + TY == g.Ny);
   const int zs = blockIdx.z * g.ZC;
   const int ze = (zs + g.ZC == g.Nz) ? g.Nz : zs + g.ZC - 1;
-  const int x = x0 + tx, y = y0 + ty;
-  const bool mapped = ty <= TY;
-  const bool active = mapped && (tx < TX || lastx) && (ty < TY || lasty);
-  const int rtx = mapped ? tx : 0, rty = mapped ? ty : 0;
+  const int nwa = TY / RYW;
+  const bool wact = w < nwa;
+  const bool row5 = wact && lasty && w == nwa - 1;  // this warp also owns row y0 + TY
+  const bool xact = lane < TX;
+  const bool xtra = lastx && lane == TX - 1;        // this lane also owns column x0 + TX
+  const int x = x0 + lane;
+  const int yw = y0 + w * RYW;
+  const int lrow = w * RYW;                          // staged row of y = yw - 1
+  const int lcol = lane + SX - 1;                    // staged column of x - 1
 
-  // per-thread copy slots (computed once): smem index and offset within a plane
-  const int nvu = VS / EPU, nku = KS / EPU;
-  const int vslots = (nvu + FINE_NT - 1) / FINE_NT, kslots = (nku + FINE_NT - 1) / FINE_NT;
-  int vso[3], vgo[3], kso[3], kgo[3];
+  // ---- per-thread copy slots (computed once)
+  const int nvch = (TY + 3) * CPR, nkch = (TY + 2) * CPR, nmw = (TY + 1) * MWR;
+  int vso[3], vgo[3], kso[3], kgo[3], mso = -1, mgo = 0;
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
-    const int u = tid + k * FINE_NT;
-    vso[k] = -1;
-    kso[k] = -1;
-    if (k < vslots && u < nvu) {
-      const int e = u * EPU, lx = e % VW, ly = e / VW;
-      vso[k] = e;
-      vgo[k] = (int)(ly * g.P + lx);
+    const int c = tid + k * FNT;
+    vso[k] = kso[k] = -1;
+    vgo[k] = kgo[k] = 0;
+    if (c < nvch) {
+      const int row = c / CPR, ch = c - row * CPR;
+      vso[k] = row * W + ch * EPC;
+      vgo[k] = (int)(row * g.P) + ch * EPC;
     }
-    if (k < kslots && u < nku) {
-      const int e = u * EPU, lx = e % KW, ly = e / KW;
-      kso[k] = e;
-      kgo[k] = (int)(ly * g.P + lx);
+    if (c < nkch) {
+      const int row = c / CPR, ch = c - row * CPR;
+      kso[k] = row * W + ch * EPC;
+      kgo[k] = (int)(row * g.P) + ch * EPC;
     }
   }
-  const long long vbase0 = nidx(g, x0 - SX, y0 - 1, 0) - (long long)g.RYn * g.P;  // plane -1 offset base
-  const long long kbase0 = eidx(g, x0 - SX, y0 - 1, 0) - (long long)g.RYe * g.P;
-  const long long vpl = (long long)g.RYn * g.P, kpl = (long long)g.RYe * g.P;
-  // node plane zz lives in stage (zz - zs + 1) % NS, element plane kk in (kk - zs + 1) % NS
-  auto issue = [&](int zz, int kk) {
-    if (OP != F_DIAG && zz <= ze + 1) {
-      S* dst = vbuf + ((zz - zs + 1) % NS) * VS;
-      const S* src = a.v + vbase0 + (long long)(zz + 1) * vpl;
-#pragma unroll
-      for (int k = 0; k < 3; ++k)
-        if (vso[k] >= 0) cp_async_n(dst + vso[k], src + vgo[k], EPU * (int)sizeof(S));
-      if (OP == F_PSMOOTH) {
-        C* pd = phis + ((zz - zs + 1) % NS) * VS * LP;
-        const C* ps = a.phi + (vbase0 + (long long)(zz + 1) * vpl) * LP;
+  if (tid < nmw) {
+    const int row = tid / MWR, j = tid - row * MWR;
+    mso = row * MWR + j;
+    mgo = (int)(row * g.mwr) + j;
+  }
+  const S* vsrc = a.v + nidx(g, x0 - SX, y0 - 1, -1);  // node plane -1
+  const S* ksrc = a.kap + eidx(g, x0 - SX, y0 - 1, -1);
+  const uint32_t* msrc = a.mask + mword(g, x0, y0, -1);
+  const long long vpl = (long long)g.RYn * g.P, kpl = (long long)g.RYe * g.P, mpl = (long long)g.RYn * g.mwr;
+  auto stage_of = [&](int q) { return (q - zs + 1) % FNS; };
+  auto sv = [&](int q) { return reinterpret_cast<S*>(smem_raw + (size_t)stage_of(q) * T::STB); };
+  auto sk = [&](int q) { return reinterpret_cast<S*>(smem_raw + (size_t)stage_of(q) * T::STB + T::VB); };
+  auto sm = [&](int q) {
+    return reinterpret_cast<uint32_t*>(smem_raw + (size_t)stage_of(q) * T::STB + T::VB + T::KB);
+  };
+  // group q: node plane q, element plane q-1, mask plane q-1 (all in stage_of(q))
+  auto issue = [&](int q) {
+    if (q <= ze + 1) {
+      if (a.v) {
+        S* d = sv(q);
+        const S* src = vsrc + (long long)(q + 1) * vpl;
 #pragma unroll
         for (int k = 0; k < 3; ++k)
-          if (vso[k] >= 0)
-            for (int q = 0; q < EPU; ++q) {
-              const int e = vso[k] + q;
-              const long long go = (long long)vgo[k] + q;
-              if (LP * sizeof(C) % 16 == 0) {
-                for (int j = 0; j < LP; j += 16 / (int)sizeof(C)) cp_async_n(pd + e * LP + j, ps + go * LP + j, 16);
-              } else {
-                for (int j = 0; j < LP; ++j) cp_async_n(pd + e * LP + j, ps + go * LP + j, (int)sizeof(C));
-              }
-            }
+          if (vso[k] >= 0) cp_async_n(d + vso[k], src + vgo[k], 16);
       }
-    }
-    if (kk >= zs - 1 && kk <= ze) {
-      S* dst = kbuf + ((kk - zs + 1) % NS) * KS;
-      const S* src = a.kap + kbase0 + (long long)(kk + 1) * kpl;
+      const int qk = q - 1;
+      if (qk >= zs - 1 && qk <= ze) {
+        S* d = sk(q);
+        const S* src = ksrc + (long long)(qk + 1) * kpl;
 #pragma unroll
-      for (int k = 0; k < 3; ++k)
-        if (kso[k] >= 0) cp_async_n(dst + kso[k], src + kgo[k], EPU * (int)sizeof(S));
+        for (int k = 0; k < 3; ++k)
+          if (kso[k] >= 0) cp_async_n(d + kso[k], src + kgo[k], 16);
+        if (mso >= 0) cp_async_n(sm(q) + mso, msrc + (long long)(qk + 1) * mpl + mgo, 4);
+      }
     }
     cp_commit();
   };
 
-  C vm[3][3], v0[3][3], vp[3][3], km[2][2], kp[2][2];
+  // ---- per-lane state
+  constexpr int NRM = RYW + 1;                    // rows incl. the closing row
+  C VA[NRM + 2][3], VB[NRM + 2][3], VC[NRM + 2][3];
+  C KA[NRM + 1][2], KB[NRM + 1][2], KC[NRM + 1][2];
 #pragma unroll
-  for (int i = 0; i < 3; ++i)
+  for (int r = 0; r < NRM + 2; ++r)
 #pragma unroll
-    for (int j = 0; j < 3; ++j) vm[i][j] = v0[i][j] = vp[i][j] = C(0);
+    for (int c = 0; c < 3; ++c) VA[r][c] = VB[r][c] = VC[r][c] = C(0);
 #pragma unroll
-  for (int i = 0; i < 2; ++i)
+  for (int r = 0; r < NRM + 1; ++r)
 #pragma unroll
-    for (int j = 0; j < 2; ++j) km[i][j] = kp[i][j] = C(0);
+    for (int c = 0; c < 2; ++c) KA[r][c] = KB[r][c] = KC[r][c] = C(0);
   C acc[LP];
 #pragma unroll
   for (int j = 0; j < LP; ++j) acc[j] = C(0);
   double dacc = 0.0;
+  const int nbz = g.nbz;
 
-  // prologue: node planes zs-1 .. zs+NS-3, element planes zs-2 .. zs+NS-4
-  for (int j = 0; j < NS - 1; ++j) issue(zs - 1 + j, zs - 2 + j);
-
-  for (int t = zs - 2; t <= ze; ++t) {
-    cp_wait<NS - 2>();
-    __syncthreads();
-    const int vst = (t + 1 - zs + 1) % NS, kst = (t - zs + 1 + NS) % NS;
-    S* vb = vbuf + vst * VS;
-    if ((OP == F_PSMOOTH && L1 > 0) || MASKIN) {
-      // in-place fix-up of the landed node plane: prolongation and/or masking
-      const int zz = t + 1;
-#pragma unroll
-      for (int k = 0; k < 3; ++k)
-        if (vso[k] >= 0)
-          for (int q = 0; q < EPU; ++q) {
-            const int e = vso[k] + q;
-            const int lx = e % VW, ly = e / VW;
-            const int xx = x0 - SX + lx, yy = y0 - 1 + ly;
-            C val = Cv<S>::ld(vb + e);
-            if (OP == F_PSMOOTH && L1 > 0 && xx >= 0 && yy >= 0 && zz >= 0 && xx <= g.Nx && yy <= g.Ny &&
-                zz <= g.Nz) {
-              const long long cell = blk_of(xx, g.b, g.nbx) +
-                                     (long long)g.nbx * (blk_of(yy, g.b, g.nby) + (long long)g.nby * blk_of(zz, g.b, g.nbz));
-              const C* ph = phis + (vst * VS + e) * LP;
-#pragma unroll
-              for (int j = 0; j < LP; ++j) val += ph[j] * a.ec[cell * LP + j];
-            }
-            if (MASKIN && is_dir(g, a.mask, xx, yy, zz)) val = C(0);
-            Cv<S>::st(vb + e, val);
-          }
-      __syncthreads();
-    }
-    if (OP != F_DIAG) {
-#pragma unroll
-      for (int oy = 0; oy < 3; ++oy)
-#pragma unroll
-        for (int ox = 0; ox < 3; ++ox) vp[oy][ox] = Cv<S>::ld(vb + (rty + oy) * VW + rtx + ox + SX - 1);
-    }
-    if (t >= zs - 1) {
-      const S* kb = kbuf + kst * KS;
-#pragma unroll
-      for (int dy = 0; dy < 2; ++dy)
-#pragma unroll
-        for (int dx = 0; dx < 2; ++dx) kp[dy][dx] = Cv<S>::ld(kb + (rty + dy) * KW + rtx + dx + SX - 1);
-    }
-    // prefetch: node plane t+NS into the stage of node plane t, element plane t+NS-1
-    issue(t + NS, t + NS - 1);
-    if (t >= zs && active) {
-      C K8;
-      const C Av = stencil<C, CUBE>(vm, v0, vp, km, kp, cc, K8);
-      const long long n = nidx(g, x, y, t);
-      const bool dir = is_dir(g, a.mask, x, y, t);
-      if (OP == F_APPLY) {
-        C yv = Av;
-        if (dir) yv = Cv<S>::ld(a.v + n);
-        Cv<To>::st(a.out + n, yv);
-        if (DOT) dacc += (double)v0[1][1] * (double)yv;
-      } else if (OP == F_SMOOTH || OP == F_PSMOOTH) {
-        // e' = v + cA (v - w) + omega D^-1 (r - A v)  (Jacobi: cA = 0)
-        const C rr = Cv<S>::ld(a.r + n);
-        C e = v0[1][1] + a.omega * (rr - Av) / (cc[0] * K8);
-        if (OP == F_SMOOTH && a.w) e += a.cA * (v0[1][1] - Cv<S>::ld(a.w + n));
-        if (dir) e = C(0);
-        Cv<To>::st(a.out + n, e);
-        if (OP == F_PSMOOTH && a.out2) Cv<S>::st(a.out2 + n, dir ? C(0) : v0[1][1]);
-      } else if (OP == F_DIAG) {
-        const C rr = Cv<S>::ld(a.r + n);
-        C e = a.omega * rr / (cc[0] * K8);
-        if (dir) e = C(0);
-        Cv<To>::st(a.out + n, e);
-      } else if (OP == F_RESTRICT) {
-        const C rr = Cv<S>::ld(a.r + n);
-        const C s = dir ? C(0) : rr - Av;
+  // one output node: Av from windows; epilogue by OP
+  auto node = [&](int xx, int yy, int t, const C (&vm)[3][3], const C (&v0)[3][3], const C (&vp)[3][3],
+                  const C (&km)[2][2], const C (&kp)[2][2], uint32_t mword_bits) {
+    C K8;
+    const C Av0 = stencil<C, CUBE>(vm, v0, vp, km, kp, cc, K8);
+    const C Av = a.v ? Av0 : C(0);  // sweep from e = 0: only the diagonal is needed
+    const long long n = nidx(g, xx, yy, t);
+    const bool dir = (mword_bits >> (xx & 31)) & 1u;
+    if (OP == F_APPLY) {
+      C yv = Av;
+      if (dir) yv = MASKIN ? Cv<S>::ld(a.v + n) : C(0);
+      Cv<To>::st(a.out + n, yv);
+      if (DOT) dacc += (double)v0[1][1] * (double)yv;
+    } else if (OP == F_SMOOTH) {
+      const C rr = Cv<S>::ld(a.r + n);
+      C e = a.omega * (rr - Av) / (cc[0] * K8);
+      if (a.v) e += v0[1][1];
+      if (a.w) e += a.cA * (v0[1][1] - Cv<S>::ld(a.w + n));
+      if (dir) e = C(0);
+      Cv<To>::st(a.out + n, e);
+    } else if (OP == F_RESTRICT) {
+      const C rr = Cv<S>::ld(a.r + n);
+      const C s = dir ? C(0) : rr - Av;
+      if (L1 == 4 && sizeof(C) == 4) {
+        const float4 ph = *reinterpret_cast<const float4*>(a.phi + n * 4);
+        acc[0] += s * (C)ph.x;
+        acc[1] += s * (C)ph.y;
+        acc[2] += s * (C)ph.z;
+        acc[3 % LP] += s * (C)ph.w;
+      } else {
 #pragma unroll
         for (int j = 0; j < LP; ++j) acc[j] += s * a.phi[n * LP + j];
       }
     }
-    if (OP == F_RESTRICT && L1 > 0 && t >= zs) {
-      const int bz = blk_of(t, g.b, g.nbz);
-      const int zend = (bz == g.nbz - 1) ? g.Nz : bz * g.b + g.b - 1;
-      if (t == zend) {  // uniform across the CTA
-        if (mapped) {
+  };
+
+  // windows of the extra column / FP64 path, read from three resident stages
+  auto win_smem = [&](int t, int r, int col, C (&vm)[3][3], C (&v0)[3][3], C (&vp)[3][3], C (&km)[2][2],
+                      C (&kp)[2][2]) {
+    const S* a0 = sv(t - 1);
+    const S* a1 = sv(t);
+    const S* a2 = sv(t + 1);
+    const S* k0 = sk(t);      // element plane t-1 lives with node plane t
+    const S* k1 = sk(t + 1);  // element plane t
 #pragma unroll
-          for (int j = 0; j < L1; ++j) red[(ty * (TX + 1) + tx) * L1 + j] = active ? acc[j] : C(0);
-        }
-        __syncthreads();
-        const int nlx = TX / g.b, nly = TY / g.b;
-        for (int o = tid; o < nlx * nly * L1; o += FINE_NT) {
-          const int j = o % L1, lb = o / L1, lbx = lb % nlx, lby = lb / nlx;
-          const int xa = lbx * g.b, xb = (lbx == nlx - 1 && lastx) ? TX + 1 : xa + g.b;
-          const int ya = lby * g.b, yb = (lby == nly - 1 && lasty) ? TY + 1 : ya + g.b;
-          C s = C(0);
-          for (int yy = ya; yy < yb; ++yy)
-            for (int xx = xa; xx < xb; ++xx) s += red[(yy * (TX + 1) + xx) * L1 + j];
-          const long long cell = (x0 / g.b + lbx) + (long long)g.nbx * ((y0 / g.b + lby) + (long long)g.nby * bz);
-          a.rc[cell * L1 + j] = s;
-        }
+    for (int oy = 0; oy < 3; ++oy)
 #pragma unroll
-        for (int j = 0; j < L1; ++j) acc[j] = C(0);
+      for (int ox = 0; ox < 3; ++ox) {
+        const int o = (lrow + r + oy) * W + col + ox;
+        vm[oy][ox] = Cv<S>::ld(a0 + o);
+        v0[oy][ox] = Cv<S>::ld(a1 + o);
+        vp[oy][ox] = Cv<S>::ld(a2 + o);
+      }
+#pragma unroll
+    for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+      for (int dx = 0; dx < 2; ++dx) {
+        const int o = (lrow + r + dy) * W + col + dx;
+        km[dy][dx] = Cv<S>::ld(k0 + o);
+        kp[dy][dx] = Cv<S>::ld(k1 + o);
+      }
+  };
+
+  auto restrict_flush = [&](int t) {
+    if (OP == F_RESTRICT && L1 > 0) {
+      const int bz = blk_of(t, 4, nbz);
+      const int zend = (bz == nbz - 1) ? g.Nz : bz * 4 + 3;
+      if (t == zend) {
+#pragma unroll
+        for (int j = 0; j < LP; ++j) {
+          C v = xact ? acc[j] : C(0);
+          v += __shfl_xor_sync(0xffffffffu, v, 1);
+          v += __shfl_xor_sync(0xffffffffu, v, 2);
+          if (wact && xact && (lane & 3) == 0) {
+            const long long cell = (long long)((x0 + lane) >> 2) + (long long)g.nbx * ((yw >> 2) + (long long)g.nby * bz);
+            a.rc[cell * LP + j] = v;
+          }
+          acc[j] = C(0);
+        }
       }
     }
-#pragma unroll
-    for (int i = 0; i < 3; ++i)
-#pragma unroll
-      for (int j = 0; j < 3; ++j) {
-        vm[i][j] = v0[i][j];
-        v0[i][j] = vp[i][j];
+  };
+
+  // step t with rotating roles (Vm, V0, Vp) and (Km, Kp)
+  auto step = [&](int t, C (&Vm)[NRM + 2][3], C (&V0)[NRM + 2][3], C (&Vp)[NRM + 2][3], C (&Km)[NRM + 1][2],
+                  C (&Kp)[NRM + 1][2]) {
+    cp_wait<FNS - 4>();
+    __syncthreads();
+    if (MASKIN && a.v) {
+      // zero the landed node plane t+1 on Gamma_D (inputs may be arbitrary there)
+      S* d = sv(t + 1);
+      for (int i = tid; i < (TY + 3) * W; i += FNT) {
+        const int ly = i / W, lx = i - ly * W;
+        const int xx = x0 - SX + lx, yy = y0 - 1 + ly;
+        if (is_dir(g, a.mask, xx, yy, t + 1)) Cv<S>::st(d + i, C(0));
       }
+      __syncthreads();
+    }
+    if (ROLL && wact) {
+      const S* s1 = sv(t + 1);
+      const S* k1 = sk(t + 1);
 #pragma unroll
-    for (int i = 0; i < 2; ++i)
+      for (int r = 0; r < RYW + 2; ++r)
 #pragma unroll
-      for (int j = 0; j < 2; ++j) km[i][j] = kp[i][j];
+        for (int c = 0; c < 3; ++c) Vp[r][c] = Cv<S>::ld(s1 + (lrow + r) * W + lcol + c);
+      if (row5)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) Vp[RYW + 2][c] = Cv<S>::ld(s1 + (lrow + RYW + 2) * W + lcol + c);
+#pragma unroll
+      for (int r = 0; r < RYW + 1; ++r)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) Kp[r][c] = Cv<S>::ld(k1 + (lrow + r) * W + lcol + c);
+      if (row5)
+#pragma unroll
+        for (int c = 0; c < 2; ++c) Kp[RYW + 1][c] = Cv<S>::ld(k1 + (lrow + RYW + 1) * W + lcol + c);
+    }
+    issue(t + FNS - 2);
+    if (t >= zs && wact) {
+      const uint32_t* ms = sm(t + 1);
+      auto mrow = [&](int r, int xx) { return ms[(w * RYW + r) * MWR + ((xx >> 5) - (x0 >> 5))]; };
+      if (ROLL) {
+        if (xact) {
+#pragma unroll
+          for (int r = 0; r < RYW; ++r)
+            node(x, yw + r, t, *reinterpret_cast<const C(*)[3][3]>(&Vm[r][0]),
+                 *reinterpret_cast<const C(*)[3][3]>(&V0[r][0]), *reinterpret_cast<const C(*)[3][3]>(&Vp[r][0]),
+                 *reinterpret_cast<const C(*)[2][2]>(&Km[r][0]), *reinterpret_cast<const C(*)[2][2]>(&Kp[r][0]),
+                 mrow(r, x));
+          if (row5)
+            node(x, yw + RYW, t, *reinterpret_cast<const C(*)[3][3]>(&Vm[RYW][0]),
+                 *reinterpret_cast<const C(*)[3][3]>(&V0[RYW][0]), *reinterpret_cast<const C(*)[3][3]>(&Vp[RYW][0]),
+                 *reinterpret_cast<const C(*)[2][2]>(&Km[RYW][0]), *reinterpret_cast<const C(*)[2][2]>(&Kp[RYW][0]),
+                 mrow(RYW, x));
+        }
+      } else if (xact) {
+        const int nr = row5 ? RYW + 1 : RYW;
+        for (int r = 0; r < nr; ++r) {
+          C vm[3][3], v0[3][3], vp[3][3], km[2][2], kp[2][2];
+          win_smem(t, r, lcol, vm, v0, vp, km, kp);
+          node(x, yw + r, t, vm, v0, vp, km, kp, mrow(r, x));
+        }
+      }
+      if (xtra) {
+        const int nr = row5 ? RYW + 1 : RYW;
+        for (int r = 0; r < nr; ++r) {
+          C vm[3][3], v0[3][3], vp[3][3], km[2][2], kp[2][2];
+          win_smem(t, r, lcol + 1, vm, v0, vp, km, kp);
+          node(x + 1, yw + r, t, vm, v0, vp, km, kp, mrow(r, x + 1));
+        }
+      }
+    }
+    if (t >= zs) restrict_flush(t);
+  };
+
+  for (int q = zs - 1; q < zs - 1 + (FNS - 3); ++q) issue(q);
+  for (int t = zs - 2; t <= ze; t += 3) {
+    step(t, VA, VB, VC, KA, KB);
+    if (t + 1 > ze) break;
+    step(t + 1, VB, VC, VA, KB, KC);
+    if (t + 2 > ze) break;
+    step(t + 2, VC, VA, VB, KC, KA);
   }
   cp_wait<0>();
 
   if (DOT) {
-    const double s = block_sum<FINE_NT>(dacc, dsh);
+    for (int o = 16; o > 0; o >>= 1) dacc += __shfl_down_sync(0xffffffffu, dacc, o);
+    __syncthreads();
+    if (lane == 0) dsh[w] = dacc;
     __shared__ bool last;
+    __syncthreads();
     const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
     const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     if (tid == 0) {
+      double s = 0.0;
+      for (int i = 0; i < FW; ++i) s += dsh[i];
       a.partial[bid] = s;
       __threadfence();
-      const unsigned prev = atomicAdd(a.counter, 1u);
-      last = (prev == nblk - 1);
+      last = (atomicAdd(a.counter, 1u) == nblk - 1);
     }
     __syncthreads();
     if (last) {
       __threadfence();
       double v = 0.0;
-      for (unsigned i = tid; i < nblk; i += FINE_NT) v += __ldcg(a.partial + i);
-      v = block_sum<FINE_NT>(v, dsh);
+      for (unsigned i = tid; i < nblk; i += FNT) v += __ldcg(a.partial + i);
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if (lane == 0) dsh[w] = v;
+      __syncthreads();
       if (tid == 0) {
-        *a.dot = v;
+        double s = 0.0;
+        for (int i = 0; i < FW; ++i) s += dsh[i];
+        *a.dot = s;
         *a.counter = 0u;
       }
     }
+  }
+}
+
+// e[n] += sum_j Phi[n][j] ec[cell(n)][j]  (level-1 prolongation, in place)
+template <class S, int L1>
+__global__ void k_prolong(Geom g, const typename Cv<S>::C* __restrict__ phi, const typename Cv<S>::C* __restrict__ ec,
+                          S* __restrict__ e) {
+  typedef typename Cv<S>::C C;
+  const long long rows = (long long)g.ny * g.nz;
+  for (long long it = blockIdx.x * (long long)blockDim.x + threadIdx.x; it < rows * g.nx;
+       it += (long long)gridDim.x * blockDim.x) {
+    const long long row = it / g.nx;
+    const int x = (int)(it - row * g.nx);
+    const int y = (int)(row % g.ny), z = (int)(row / g.ny);
+    const long long n = nidx(g, x, y, z);
+    const long long cell =
+        blk_of(x, 4, g.nbx) + (long long)g.nbx * (blk_of(y, 4, g.nby) + (long long)g.nby * blk_of(z, 4, g.nbz));
+    C s = C(0);
+    if (L1 == 4 && sizeof(C) == 4) {
+      const float4 p = *reinterpret_cast<const float4*>(phi + n * 4);
+      const float4 c = *reinterpret_cast<const float4*>(ec + cell * 4);
+      s = (C)(p.x * c.x + p.y * c.y + p.z * c.z + p.w * c.w);
+    } else {
+#pragma unroll
+      for (int j = 0; j < L1; ++j) s += phi[n * L1 + j] * ec[cell * L1 + j];
+    }
+    Cv<S>::st(e + n, Cv<S>::ld(e + n) + s);
   }
 }
 
@@ -361,28 +456,14 @@ __global__ void __launch_bounds__(FINE_NT) fine_tile(FineArgs<S, To> a) {
 
 static dim3 fine_grid(const Geom& g) { return dim3(g.Nx / g.TX, g.Ny / g.TY, g.Nz / g.ZC); }
 
-constexpr int FINE_NS = 6;  // planes in the cp.async ring (NS - 1 in flight)
-
-template <class S>
-static size_t fine_smem(const Geom& g, int op, int L1) {
-  typedef typename Cv<S>::C C;
-  const int SX = Stage<S>::SX, EPU = Stage<S>::EPU;
-  const int VW = ((g.TX + 2 + SX) + EPU - 1) / EPU * EPU, VH = g.TY + 3;
-  const int KW = ((g.TX + 1 + SX) + EPU - 1) / EPU * EPU, KH = g.TY + 2;
-  const int LP = L1 > 0 ? L1 : 1;
-  size_t n = ((size_t)FINE_NS * (VW * VH + KW * KH) * sizeof(S) + 15) & ~(size_t)15;
-  if (op == F_PSMOOTH) n += (size_t)FINE_NS * VW * VH * LP * sizeof(C);
-  if (op == F_RESTRICT) n += (size_t)(g.TX + 1) * (g.TY + 1) * LP * sizeof(C);
-  return n;
-}
-
 template <class S, class To, int OP, int L1, bool DOT, bool MASKIN = false>
-static cudaError_t launch_fine(const FineArgs<S, To>& a, int L1rt, cudaStream_t st) {
-  const size_t sm = fine_smem<S>(a.g, OP, L1rt);
-  auto k = a.g.cube ? fine_tile<S, To, OP, true, L1, DOT, MASKIN, FINE_NS>
-                    : fine_tile<S, To, OP, false, L1, DOT, MASKIN, FINE_NS>;
+static cudaError_t launch_fine(const FineArgs<S, To>& a, cudaStream_t st) {
+  constexpr bool ROLL = sizeof(S) <= 4;
+  const size_t sm = (size_t)FNS * Tile<S>::STB;
+  auto k = a.g.cube ? fine_tile<S, To, OP, true, L1, DOT, MASKIN, ROLL>
+                    : fine_tile<S, To, OP, false, L1, DOT, MASKIN, ROLL>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  note_launch(), k<<<fine_grid(a.g), FINE_NT, sm, st>>>(a);
+  note_launch(), k<<<fine_grid(a.g), FNT, sm, st>>>(a);
   return cudaGetLastError();
 }
 
@@ -409,14 +490,14 @@ cudaError_t fine_apply_f64(const Geom& g, const uint32_t* mask, const double* ka
   auto a = fargs<double, double>(g, mask, kap);
   a.v = u;
   a.out = y;
-  if (mask_input) return launch_fine<double, double, F_APPLY, 0, false, true>(a, 0, st);
+  if (mask_input) return launch_fine<double, double, F_APPLY, 0, false, true>(a, st);
   if (dot) {
     a.partial = partial;
     a.counter = counter;
     a.dot = dot;
-    return launch_fine<double, double, F_APPLY, 0, true>(a, 0, st);
+    return launch_fine<double, double, F_APPLY, 0, true>(a, st);
   }
-  return launch_fine<double, double, F_APPLY, 0, false>(a, 0, st);
+  return launch_fine<double, double, F_APPLY, 0, false>(a, st);
 }
 
 template <class S>
@@ -425,8 +506,8 @@ cudaError_t fine_apply_lp(const Geom& g, const uint32_t* mask, const S* kap, con
   auto a = fargs<S, S>(g, mask, kap);
   a.v = u;
   a.out = y;
-  if (mask_input) return launch_fine<S, S, F_APPLY, 0, false, true>(a, 0, st);
-  return launch_fine<S, S, F_APPLY, 0, false>(a, 0, st);
+  if (mask_input) return launch_fine<S, S, F_APPLY, 0, false, true>(a, st);
+  return launch_fine<S, S, F_APPLY, 0, false>(a, st);
 }
 template cudaError_t fine_apply_lp<float>(const Geom&, const uint32_t*, const float*, const float*, float*, cudaStream_t,
                                           bool);
@@ -445,7 +526,6 @@ template cudaError_t fine_apply_lp<bf16>(const Geom&, const uint32_t*, const bf1
     default: return cudaErrorInvalidValue;                       \
   }
 
-// Fine part of the cycle, storage S (double / float / bf16), compute C.
 // One sweep e' = e + cA (e - w) + cB D^-1 (r - A e); e == nullptr: e' = cB D^-1 r.
 template <class S, class To>
 cudaError_t fine_smooth(const Geom& g, const uint32_t* mask, const S* kap, const S* r, const S* e, const S* w,
@@ -453,12 +533,11 @@ cudaError_t fine_smooth(const Geom& g, const uint32_t* mask, const S* kap, const
   auto a = fargs<S, To>(g, mask, kap);
   a.r = r;
   a.v = e;
-  a.w = w;
+  a.w = (e != nullptr) ? w : nullptr;
   a.out = out;
   a.cA = cA;
   a.omega = cB;
-  if (e == nullptr) return launch_fine<S, To, F_DIAG, 0, false>(a, 0, st);
-  return launch_fine<S, To, F_SMOOTH, 0, false>(a, 0, st);
+  return launch_fine<S, To, F_SMOOTH, 0, false>(a, st);
 }
 
 template <class S>
@@ -469,33 +548,24 @@ cudaError_t fine_restrict(const Geom& g, const uint32_t* mask, const S* kap, con
   a.v = e;
   a.phi = phi;
   a.rc = rc;
-  L1_DISPATCH(L1, return (launch_fine<S, S, F_RESTRICT, LL, false>(a, LL, st)));
+  L1_DISPATCH(L1, return (launch_fine<S, S, F_RESTRICT, LL, false>(a, st)));
   return cudaSuccess;
 }
 
-// v = e + Phi ec (prolongation), out = v + cB D^-1 (r - A v); out2 (optional) = v
-template <class S, class To>
-cudaError_t fine_prolong_smooth(const Geom& g, const uint32_t* mask, const S* kap, const S* r, const S* e,
-                                const typename Cv<S>::C* phi, const typename Cv<S>::C* ec, To* out, S* out2,
-                                typename Cv<S>::C cB, int L1, cudaStream_t st) {
-  auto a = fargs<S, To>(g, mask, kap);
-  a.r = r;
-  a.v = e;
-  a.phi = phi;
-  a.ec = ec;
-  a.out = out;
-  a.out2 = out2;
-  a.omega = cB;
-  L1_DISPATCH(L1, return (launch_fine<S, To, F_PSMOOTH, LL, false>(a, LL, st)));
-  return cudaSuccess;
+// e += Phi ec (level-1 prolongation, in place)
+template <class S>
+cudaError_t fine_prolong(const Geom& g, const typename Cv<S>::C* phi, const typename Cv<S>::C* ec, S* e, int L1,
+                         cudaStream_t st) {
+  const long long n = (long long)g.nx * g.ny * g.nz;
+  long long nb = (n + 255) / 256;
+  if (nb > 152 * 16) nb = 152 * 16;
+  L1_DISPATCH(L1, (note_launch(), k_prolong<S, LL><<<(unsigned)nb, 256, 0, st>>>(g, phi, ec, e)));
+  return cudaGetLastError();
 }
 
 #define INST_FINE(S, To)                                                                                        \
   template cudaError_t fine_smooth<S, To>(const Geom&, const uint32_t*, const S*, const S*, const S*, const S*, \
-                                          To*, Cv<S>::C, Cv<S>::C, cudaStream_t);                              \
-  template cudaError_t fine_prolong_smooth<S, To>(const Geom&, const uint32_t*, const S*, const S*, const S*,  \
-                                                  const Cv<S>::C*, const Cv<S>::C*, To*, S*, Cv<S>::C, int,    \
-                                                  cudaStream_t);
+                                          To*, Cv<S>::C, Cv<S>::C, cudaStream_t);
 INST_FINE(double, double)
 INST_FINE(float, float)
 INST_FINE(bf16, bf16)
@@ -506,5 +576,8 @@ template cudaError_t fine_restrict<float>(const Geom&, const uint32_t*, const fl
                                           const float*, float*, int, cudaStream_t);
 template cudaError_t fine_restrict<bf16>(const Geom&, const uint32_t*, const bf16*, const bf16*, const bf16*,
                                          const float*, float*, int, cudaStream_t);
+template cudaError_t fine_prolong<double>(const Geom&, const double*, const double*, double*, int, cudaStream_t);
+template cudaError_t fine_prolong<float>(const Geom&, const float*, const float*, float*, int, cudaStream_t);
+template cudaError_t fine_prolong<bf16>(const Geom&, const float*, const float*, bf16*, int, cudaStream_t);
 
 }  // namespace thermo

@@ -17,10 +17,9 @@ cudaError_t fine_smooth(const Geom& g, const uint32_t* mask, const S* kap, const
 template <class S>
 cudaError_t fine_restrict(const Geom& g, const uint32_t* mask, const S* kap, const S* r, const S* e,
                           const typename Cv<S>::C* phi, typename Cv<S>::C* rc, int L1, cudaStream_t st);
-template <class S, class To>
-cudaError_t fine_prolong_smooth(const Geom& g, const uint32_t* mask, const S* kap, const S* r, const S* e,
-                                const typename Cv<S>::C* phi, const typename Cv<S>::C* ec, To* out, S* out2,
-                                typename Cv<S>::C cB, int L1, cudaStream_t st);
+template <class S>
+cudaError_t fine_prolong(const Geom& g, const typename Cv<S>::C* phi, const typename Cv<S>::C* ec, S* e, int L1,
+                         cudaStream_t st);
 
 // ---- vec.cu : device scalars of the Krylov loop
 struct CgScalars {

@@ -190,7 +190,7 @@ extern "C" thermo_status thermo_create(const int grid[3], const double h[3], con
     if (grid[k] <= 0 || !(h[k] > 0.0)) return fail(ctx, THERMO_EINVAL, "grid and h must be positive");
   }
   const int b = opt.block;
-  if (b < 2 || b > 8) return fail(ctx, THERMO_EINVAL, "block must be in [2, 8]");
+  if (b != 4) return fail(ctx, THERMO_EINVAL, "block must be 4 (fine kernels assign one block row per warp)");
   if (opt.levels < 1 || opt.levels > THERMO_MAX_LEVELS) return fail(ctx, THERMO_EINVAL, "levels out of range");
   if (grid[0] % b || grid[1] % b || grid[2] % b) return fail(ctx, THERMO_EINVAL, "grid must be a multiple of block");
   if (opt.nu_fine < 1 || opt.nu_coarse < 1 || opt.nu_fine > 64) return fail(ctx, THERMO_EINVAL, "smoothing sweeps must be in [1, 64]");
@@ -240,16 +240,22 @@ extern "C" thermo_status thermo_create(const int grid[3], const double h[3], con
   g.nbx = g.Nx / b;
   g.nby = g.Ny / b;
   g.nbz = g.Nz / b;
-  g.TX = pick_tile(g.Nx, b, 32);
-  g.TY = pick_tile(g.Ny, b, 8);
+  g.TX = (g.Nx % 32 == 0) ? 32 : (g.Nx % 16 == 0 ? 16 : (g.Nx % 8 == 0 ? 8 : 0));
+  g.TY = pick_tile(g.Ny, b, 16);
   g.ZC = 0;
-  for (int zc : {32, 16, 8, 4, 2}) {
-    if (zc % b == 0 && g.Nz % zc == 0 && (g.Nz >= 4 * zc || zc == b)) {
+  if (g.TX && g.TY) {
+    // planes per CTA: the largest chunk that still gives >= 8 CTAs per SM
+    const long long cols = (long long)(g.Nx / g.TX) * (g.Ny / g.TY);
+    for (int zc : {32, 16, 8, 4}) {
+      if (g.Nz % zc) continue;
+      if (!g.ZC) g.ZC = zc;
+      if (cols * (g.Nz / zc) >= 152LL * 8) {
+        g.ZC = zc;
+        break;
+      }
       g.ZC = zc;
-      break;
     }
   }
-  if (!g.ZC) g.ZC = pick_tile(g.Nz, b, g.Nz);
   if (!g.TX || !g.TY || !g.ZC) return fail(ctx, THERMO_EINVAL, "unsupported grid / block combination");
   ctx->L1 = opt.nvec[0];
   ctx->nnode = (long long)g.nx * g.ny * g.nz;
@@ -601,19 +607,13 @@ static cudaError_t vcycle_fine(thermo_ctx* ctx, const S* kap, const S* r, S* b0,
   else
     e = coarse_cycle<float>(ctx, 1);
   if (e != cudaSuccess) return e;
-  // post-smoothing from the prolonged iterate
-  if (m == 1) return fine_prolong_smooth<S, To>(g, ctx->bits, kap, r, buf[cur], phi, ec, z, nullptr, (C)sb[0], L1, st);
-  const int o1 = (cur + 1) % 3, o2 = (cur + 2) % 3;
-  const bool keep = sa[1] != 0.0;
-  if ((e = fine_prolong_smooth<S, S>(g, ctx->bits, kap, r, buf[cur], phi, ec, buf[o1], keep ? buf[o2] : nullptr,
-                                     (C)sb[0], L1, st)) != cudaSuccess)
-    return e;
-  cur = o1;
-  prev = o2;
-  for (int k = 1; k < m; ++k) {
-    const S* w = (sa[k] != 0.0) ? buf[prev] : nullptr;
+  // prolongation (in place) and post-smoothing from the prolonged iterate
+  if ((e = fine_prolong<S>(g, phi, ec, buf[cur], L1, st)) != cudaSuccess) return e;
+  prev = -1;
+  for (int k = 0; k < m; ++k) {
+    const S* w = (k > 0 && sa[k] != 0.0) ? buf[prev] : nullptr;
     if (k == m - 1) return fine_smooth<S, To>(g, ctx->bits, kap, r, buf[cur], w, z, (C)sa[k], (C)sb[k], st);
-    const int nxt = 3 - cur - prev;
+    const int nxt = prev >= 0 ? 3 - cur - prev : (cur + 1) % 3;
     if ((e = fine_smooth<S, S>(g, ctx->bits, kap, r, buf[cur], w, buf[nxt], (C)sa[k], (C)sb[k], st)) != cudaSuccess)
       return e;
     prev = cur;
@@ -1016,9 +1016,8 @@ extern "C" thermo_status thermo_bench_kernel(thermo_ctx* ctx, int which, int rep
         bytes = n * (8 + 4 * L1) + M * 4;
         return fine_restrict<float>(g, ctx->bits, ctx->k32, ctx->r32, ctx->ea32, ctx->phi32, l1.r32, ctx->L1, st);
       case 5:
-        bytes = n * (16 + 4 * L1) + M * 4;
-        return fine_prolong_smooth<float, float>(g, ctx->bits, ctx->k32, ctx->r32, ctx->ea32, ctx->phi32, l1.e32,
-                                                 ctx->eb32, ctx->ec32, 0.6f, ctx->L1, st);
+        bytes = n * (8 + 4 * L1);
+        return fine_prolong<float>(g, ctx->phi32, l1.e32, ctx->ea32, ctx->L1, st);
       case 6:
         bytes = (double)l1.cl.ncell * (27.0 * l1.cl.L * l1.cl.L + 2.0 * l1.cl.L) * 4.0;
         return coarse_apply<float>(l1.cl, l1.T32, l1.e32, l1.s32, st);
