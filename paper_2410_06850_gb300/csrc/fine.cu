@@ -63,7 +63,7 @@ struct FineArgs {
   const uint32_t* mask;
   const C* phi;     // level-1 basis [nsize][L1]
   C* rc;            // level-1 restricted residual [cells][L1]
-  const S* w;       // SMOOTH: previous iterate of the three-term recurrence (may be null)
+  const S* w;       // SMOOTH: previous iterate of the three-term recurrence (null: zero)
   C cA;             // coefficient of (v - w)
   C omega;          // coefficient of D^-1 (r - A v)
   double* partial;  // dot partials, one per CTA
@@ -244,7 +244,7 @@ __global__ void __launch_bounds__(FNT) fine_tile(FineArgs<S, To> a) {
       const C rr = Cv<S>::ld(a.r + n);
       C e = a.omega * (rr - Av) / (cc[0] * K8);
       if (a.v) e += v0[1][1];
-      if (a.w) e += a.cA * (v0[1][1] - Cv<S>::ld(a.w + n));
+      if (a.cA != C(0)) e += a.cA * (v0[1][1] - (a.w ? Cv<S>::ld(a.w + n) : C(0)));  // w == null: w = 0
       if (dir) e = C(0);
       Cv<To>::st(a.out + n, e);
     } else if (OP == F_RESTRICT) {
