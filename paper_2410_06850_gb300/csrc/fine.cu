@@ -38,18 +38,35 @@ constexpr int TYM = FW * RYW;    // rows per tile (max)
 constexpr int VHM = TYM + 3;     // staged node rows: y0-1 .. y0+TY+1
 constexpr int KHM = TYM + 2;     // staged element rows: y0-1 .. y0+TY
 constexpr int MWR = 2;           // mask words staged per row
-constexpr int FNS = 7;           // ring stages
 
-template <class S>
-struct Tile {
+// Per-stage shared-memory layout of one pass.  Every stage holds one plane of:
+// the input field with halo (rows y0-1..y0+TY+1, columns from x0-SX), the
+// element conductivity (rows y0-1..y0+TY), the Dirichlet mask words (rows
+// y0..y0+TY), and the centre-only arrays the epilogue reads (rows y0..y0+TY,
+// columns from x0): r and w for sweeps, r and Phi for the restriction.
+template <class S, int OP, int LP>
+struct Lay {
+  typedef typename Cv<S>::C C;
   static constexpr int EPC = 16 / (int)sizeof(S);      // elements per 16-byte chunk
-  static constexpr int SX = EPC >= 8 ? 8 : 4;           // staged rows start at x0 - SX
-  static constexpr int W = sizeof(S) == 2 ? 48 : 40;    // staged row width (elements)
-  static constexpr int CPR = W / EPC;                   // chunks per row
-  static constexpr size_t VB = (size_t)VHM * W * sizeof(S);
-  static constexpr size_t KB = (size_t)KHM * W * sizeof(S);
-  static constexpr size_t MB = (size_t)(TYM + 1) * MWR * 4;
-  static constexpr size_t STB = (VB + KB + MB + 15) & ~(size_t)15;  // bytes per stage
+  static constexpr int SX = EPC >= 8 ? 8 : 4;           // halo rows start at x0 - SX
+  static constexpr int W = sizeof(S) == 2 ? 48 : 40;    // halo row width (elements)
+  static constexpr int CPR = W / EPC;                   // chunks per halo row
+  static constexpr int CW = 40;                         // centre row width (elements)
+  static constexpr int CCPR = CW / EPC;                 // chunks per centre row
+  static constexpr int PN = 33;                         // Phi nodes per staged row
+  static constexpr bool HR = OP == F_SMOOTH || OP == F_RESTRICT;
+  static constexpr bool HW = OP == F_SMOOTH;
+  static constexpr bool HP = OP == F_RESTRICT && sizeof(S) <= 4 && (LP * sizeof(C)) % 16 == 0;
+  static constexpr int PCN = HP ? (int)(LP * sizeof(C) / 16) : 1;  // Phi chunks per node
+  static constexpr int NS = sizeof(S) == 8 ? 4 : 6;     // ring stages
+  static constexpr size_t al(size_t x) { return (x + 15) & ~(size_t)15; }
+  static constexpr size_t oV = 0;
+  static constexpr size_t oK = al(oV + (size_t)VHM * W * sizeof(S));
+  static constexpr size_t oM = al(oK + (size_t)KHM * W * sizeof(S));
+  static constexpr size_t oR = al(oM + (size_t)(TYM + 1) * MWR * 4);
+  static constexpr size_t oW = al(oR + (HR ? (size_t)(TYM + 1) * CW * sizeof(S) : 0));
+  static constexpr size_t oP = al(oW + (HW ? (size_t)(TYM + 1) * CW * sizeof(S) : 0));
+  static constexpr size_t STB = al(oP + (HP ? (size_t)(TYM + 1) * PN * LP * sizeof(C) : 0));
 };
 
 template <class S, class To>
@@ -128,9 +145,9 @@ __device__ __forceinline__ void cp_wait() {
 template <class S, class To, int OP, bool CUBE, int L1, bool DOT, bool MASKIN, bool ROLL>
 __global__ void __launch_bounds__(FNT) fine_tile(FineArgs<S, To> a) {
   typedef typename Cv<S>::C C;
-  typedef Tile<S> T;
-  constexpr int SX = T::SX, W = T::W, CPR = T::CPR, EPC = T::EPC;
   constexpr int LP = L1 > 0 ? L1 : 1;
+  typedef Lay<S, OP, LP> T;
+  constexpr int SX = T::SX, W = T::W, CPR = T::CPR, EPC = T::EPC, CW = T::CW, CCPR = T::CCPR, FNS = T::NS;
   const Geom& g = a.g;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ double dsh[33];
@@ -176,17 +193,48 @@ __global__ void __launch_bounds__(FNT) fine_tile(FineArgs<S, To> a) {
     mso = row * MWR + j;
     mgo = (int)(row * g.mwr) + j;
   }
+  // centre arrays: r / w chunks (rows y0..y0+TY) and Phi chunks
+  constexpr int NRS = (TYM + 1) * CCPR / FNT + 1;
+  constexpr int NPS = T::HP ? ((TYM + 1) * T::PN * T::PCN) / FNT + 1 : 1;
+  int rso[NRS], rgo[NRS], pso[NPS], pgo[NPS];
+  const int nrch = (TY + 1) * CCPR, npch = (TY + 1) * (TX + 1) * T::PCN;
+#pragma unroll
+  for (int k = 0; k < NRS; ++k) {
+    const int c = tid + k * FNT;
+    rso[k] = -1;
+    rgo[k] = 0;
+    if (T::HR && c < nrch) {
+      const int row = c / CCPR, ch = c - row * CCPR;
+      rso[k] = row * CW + ch * EPC;
+      rgo[k] = (int)(row * g.P) + ch * EPC;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < NPS; ++k) {
+    const int c = tid + k * FNT;
+    pso[k] = -1;
+    pgo[k] = 0;
+    if (T::HP && c < npch) {
+      const int row = c / ((TX + 1) * T::PCN), rem = c - row * ((TX + 1) * T::PCN);
+      const int nd = rem / T::PCN, ch = rem - nd * T::PCN;
+      pso[k] = (row * T::PN + nd) * LP + ch * (16 / (int)sizeof(C));
+      pgo[k] = (int)((row * g.P + nd) * LP) + ch * (16 / (int)sizeof(C));
+    }
+  }
   const S* vsrc = a.v + nidx(g, x0 - SX, y0 - 1, -1);  // node plane -1
   const S* ksrc = a.kap + eidx(g, x0 - SX, y0 - 1, -1);
   const uint32_t* msrc = a.mask + mword(g, x0, y0, -1);
+  const long long c0n = nidx(g, x0, y0, -1);            // centre origin, node plane -1
   const long long vpl = (long long)g.RYn * g.P, kpl = (long long)g.RYe * g.P, mpl = (long long)g.RYn * g.mwr;
   auto stage_of = [&](int q) { return (q - zs + 1) % FNS; };
-  auto sv = [&](int q) { return reinterpret_cast<S*>(smem_raw + (size_t)stage_of(q) * T::STB); };
-  auto sk = [&](int q) { return reinterpret_cast<S*>(smem_raw + (size_t)stage_of(q) * T::STB + T::VB); };
-  auto sm = [&](int q) {
-    return reinterpret_cast<uint32_t*>(smem_raw + (size_t)stage_of(q) * T::STB + T::VB + T::KB);
-  };
-  // group q: node plane q, element plane q-1, mask plane q-1 (all in stage_of(q))
+  auto sbase = [&](int q) { return smem_raw + (size_t)stage_of(q) * T::STB; };
+  auto sv = [&](int q) { return reinterpret_cast<S*>(sbase(q) + T::oV); };
+  auto sk = [&](int q) { return reinterpret_cast<S*>(sbase(q) + T::oK); };
+  auto sm = [&](int q) { return reinterpret_cast<uint32_t*>(sbase(q) + T::oM); };
+  auto sr = [&](int q) { return reinterpret_cast<S*>(sbase(q) + T::oR); };
+  auto sw = [&](int q) { return reinterpret_cast<S*>(sbase(q) + T::oW); };
+  auto sp = [&](int q) { return reinterpret_cast<C*>(sbase(q) + T::oP); };
+  // group q: node plane q, element plane q-1, mask + centre arrays of plane q-1 (all in stage_of(q))
   auto issue = [&](int q) {
     if (q <= ze + 1) {
       if (a.v) {
@@ -204,6 +252,24 @@ __global__ void __launch_bounds__(FNT) fine_tile(FineArgs<S, To> a) {
         for (int k = 0; k < 3; ++k)
           if (kso[k] >= 0) cp_async_n(d + kso[k], src + kgo[k], 16);
         if (mso >= 0) cp_async_n(sm(q) + mso, msrc + (long long)(qk + 1) * mpl + mgo, 4);
+        if (qk >= zs) {
+          const long long cb = c0n + (long long)(qk + 1) * vpl;
+          if (T::HR) {
+#pragma unroll
+            for (int k = 0; k < NRS; ++k)
+              if (rso[k] >= 0) cp_async_n(sr(q) + rso[k], a.r + cb + rgo[k], 16);
+          }
+          if (T::HW && a.w) {
+#pragma unroll
+            for (int k = 0; k < NRS; ++k)
+              if (rso[k] >= 0) cp_async_n(sw(q) + rso[k], a.w + cb + rgo[k], 16);
+          }
+          if (T::HP) {
+#pragma unroll
+            for (int k = 0; k < NPS; ++k)
+              if (pso[k] >= 0) cp_async_n(sp(q) + pso[k], a.phi + cb * LP + pgo[k], 16);
+          }
+        }
       }
     }
     cp_commit();
@@ -235,27 +301,32 @@ __global__ void __launch_bounds__(FNT) fine_tile(FineArgs<S, To> a) {
     const C Av = a.v ? Av0 : C(0);  // sweep from e = 0: only the diagonal is needed
     const long long n = nidx(g, xx, yy, t);
     const bool dir = (mword_bits >> (xx & 31)) & 1u;
+    const int ci = (yy - y0) * CW + (xx - x0);              // staged centre index
+    const int pi = ((yy - y0) * T::PN + (xx - x0)) * LP;    // staged Phi index
     if (OP == F_APPLY) {
       C yv = Av;
       if (dir) yv = MASKIN ? Cv<S>::ld(a.v + n) : C(0);
       Cv<To>::st(a.out + n, yv);
       if (DOT) dacc += (double)v0[1][1] * (double)yv;
     } else if (OP == F_SMOOTH) {
-      const C rr = Cv<S>::ld(a.r + n);
+      const C rr = Cv<S>::ld(sr(t + 1) + ci);
       C e = a.omega * (rr - Av) / (cc[0] * K8);
       if (a.v) e += v0[1][1];
-      if (a.cA != C(0)) e += a.cA * (v0[1][1] - (a.w ? Cv<S>::ld(a.w + n) : C(0)));  // w == null: w = 0
+      if (a.cA != C(0)) e += a.cA * (v0[1][1] - (a.w ? Cv<S>::ld(sw(t + 1) + ci) : C(0)));  // w == null: w = 0
       if (dir) e = C(0);
       Cv<To>::st(a.out + n, e);
     } else if (OP == F_RESTRICT) {
-      const C rr = Cv<S>::ld(a.r + n);
+      const C rr = Cv<S>::ld(sr(t + 1) + ci);
       const C s = dir ? C(0) : rr - Av;
-      if (L1 == 4 && sizeof(C) == 4) {
-        const float4 ph = *reinterpret_cast<const float4*>(a.phi + n * 4);
+      if (T::HP && L1 == 4 && sizeof(C) == 4) {
+        const float4 ph = *reinterpret_cast<const float4*>(sp(t + 1) + pi);
         acc[0] += s * (C)ph.x;
         acc[1] += s * (C)ph.y;
         acc[2] += s * (C)ph.z;
         acc[3 % LP] += s * (C)ph.w;
+      } else if (T::HP) {
+#pragma unroll
+        for (int j = 0; j < LP; ++j) acc[j] += s * sp(t + 1)[pi + j];
       } else {
 #pragma unroll
         for (int j = 0; j < LP; ++j) acc[j] += s * a.phi[n * LP + j];
@@ -459,7 +530,8 @@ static dim3 fine_grid(const Geom& g) { return dim3(g.Nx / g.TX, g.Ny / g.TY, g.N
 template <class S, class To, int OP, int L1, bool DOT, bool MASKIN = false>
 static cudaError_t launch_fine(const FineArgs<S, To>& a, cudaStream_t st) {
   constexpr bool ROLL = sizeof(S) <= 4;
-  const size_t sm = (size_t)FNS * Tile<S>::STB;
+  typedef Lay<S, OP, (L1 > 0 ? L1 : 1)> T;
+  const size_t sm = (size_t)T::NS * T::STB;
   auto k = a.g.cube ? fine_tile<S, To, OP, true, L1, DOT, MASKIN, ROLL>
                     : fine_tile<S, To, OP, false, L1, DOT, MASKIN, ROLL>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
