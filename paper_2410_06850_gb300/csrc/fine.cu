@@ -1,19 +1,20 @@
 // Fine-grid kernels: matrix-free Q1 operator and the fine part of the
 // multigrid cycle (Sec. 3, Algorithm 1).
 //
-// One z-marching engine serves every fine-grid pass.  A CTA (4 warps) owns a
-// TX x TY tile of nodes (TX <= 32 columns = lanes, TY = 4 rows per warp, so a
-// warp covers exactly one row of level-1 blocks) and marches over ZC node
-// planes.  Planes of the input field (with a one-node halo), of the element
-// conductivity and of the Dirichlet bitmask are staged in shared memory by
-// 16-byte cp.async copies through a 7-stage ring, so four planes are in
-// flight while one is computed.  In the FP32/BF16 kernels each lane keeps
-// the 3x3 windows of its rows for the two previous planes in registers
-// (z unrolled by three, so the windows rotate without moves) and reads only
-// the new plane from shared memory; the FP64 kernel (ALU-bound) reads its
-// windows from the resident stages.  The tile on the high face of an axis
-// also owns the closing node plane: lane TX-1 computes the extra column and
-// the last warp a fifth row.
+// One z-marching engine serves every fine-grid pass.  A CTA owns a TX x TY
+// tile of nodes (TX <= 32 columns = lanes, TY <= 8 rows = one warp each) and
+// marches over ZC node planes.  Each plane of the input field (one-node
+// halo), of the element conductivity, of the Dirichlet bitmask and of the
+// centre-only arrays of the epilogue (r, w, or Phi) is staged into shared
+// memory by one elected thread with TMA tensor copies
+// (cp.async.bulk.tensor) into a ring of stages, each guarded by an
+// mbarrier with a byte-count transaction; three planes stay resident for
+// the stencil and the rest are in flight.  Every lane keeps the 3x3 windows
+// of its node for the two previous planes in registers (z unrolled by three
+// so the windows rotate without moves) and reads only the new plane.  The
+// tile on the high face of an axis also owns the closing node plane: an
+// extra warp computes the closing column (lanes = rows) and the closing row
+// (lanes = columns) from the resident stages.
 //
 // Operator (node-centred gather of A = sum_e kappa_e K0_e, K0[a][b] =
 // c[a ^ b]): with the 8 elements around node i indexed (dx,dy,dz),
@@ -22,8 +23,13 @@
 // where K8 is the sum of the 8 conductivities and zp/yp/xp are sums of the
 // two elements sharing an edge (Sec. 2.2 Eq. (5) realised for Q1).
 // Dirichlet rows are identities.  Inputs of the hot kernels vanish on
-// Gamma_D by construction (Krylov directions, cycle iterates); the
-// MASKIN variants zero them on load for arbitrary inputs.
+// Gamma_D by construction (Krylov directions, cycle iterates); the MASKIN
+// variants zero them on load for arbitrary inputs.
+#include <cuda.h>
+
+#include <mutex>
+#include <unordered_map>
+
 #include "common.cuh"
 #include "kernels.h"
 
@@ -31,61 +37,65 @@ namespace thermo {
 
 enum FineOp { F_APPLY = 0, F_SMOOTH = 1, F_RESTRICT = 3 };
 
-constexpr int FW = 4;            // warps per CTA
-constexpr int FNT = 32 * FW;     // threads per CTA
-constexpr int RYW = 4;           // rows per warp (= level-1 block edge)
-constexpr int TYM = FW * RYW;    // rows per tile (max)
-constexpr int VHM = TYM + 3;     // staged node rows: y0-1 .. y0+TY+1
-constexpr int KHM = TYM + 2;     // staged element rows: y0-1 .. y0+TY
-constexpr int MWR = 2;           // mask words staged per row
+constexpr int TYM = 8;            // rows per tile (max), one warp each
+constexpr int FNT = 32 * (TYM + 1);  // + one warp for the closing column / row
+constexpr int MBW = 8;            // staged mask words per row
+constexpr int CWD = 40;           // staged centre row width (elements)
+constexpr int PNODE = 33;         // Phi nodes per staged centre row
 
-// Per-stage shared-memory layout of one pass.  Every stage holds one plane of:
-// the input field with halo (rows y0-1..y0+TY+1, columns from x0-SX), the
-// element conductivity (rows y0-1..y0+TY), the Dirichlet mask words (rows
-// y0..y0+TY), and the centre-only arrays the epilogue reads (rows y0..y0+TY,
-// columns from x0): r and w for sweeps, r and Phi for the restriction.
-template <class S, int OP, int LP>
-struct Lay {
+template <class S>
+struct Halo {
+  static constexpr int SX = sizeof(S) == 2 ? 8 : 4;   // halo rows start at x0 - SX (16-byte aligned)
+  static constexpr int W = sizeof(S) == 2 ? 48 : 40;  // halo row width (elements)
+};
+template <class C, int LP>
+struct PhiBox {  // staged Phi row width in elements of C (16-byte multiple)
+  static constexpr int PW = ((PNODE * LP * (int)sizeof(C) + 15) / 16) * 16 / (int)sizeof(C);
+};
+
+// Stage layout (bytes; 128-aligned parts): halo field, conductivity, mask,
+// centre r, centre w, centre Phi.
+template <class S, int OP, int LP, bool HWW>
+struct FLay {
   typedef typename Cv<S>::C C;
-  static constexpr int EPC = 16 / (int)sizeof(S);      // elements per 16-byte chunk
-  static constexpr int SX = EPC >= 8 ? 8 : 4;           // halo rows start at x0 - SX
-  static constexpr int W = sizeof(S) == 2 ? 48 : 40;    // halo row width (elements)
-  static constexpr int CPR = W / EPC;                   // chunks per halo row
-  static constexpr int CW = 40;                         // centre row width (elements)
-  static constexpr int CCPR = CW / EPC;                 // chunks per centre row
-  static constexpr int PN = 33;                         // Phi nodes per staged row
+  static constexpr size_t A = 128;
+  static constexpr size_t up(size_t x) { return (x + A - 1) / A * A; }
   static constexpr bool HR = OP == F_SMOOTH || OP == F_RESTRICT;
-  static constexpr bool HW = OP == F_SMOOTH;
-  static constexpr bool HP = OP == F_RESTRICT && sizeof(S) <= 4 && (LP * sizeof(C)) % 16 == 0;
-  static constexpr int PCN = HP ? (int)(LP * sizeof(C) / 16) : 1;  // Phi chunks per node
-  static constexpr int NS = sizeof(S) == 8 ? 4 : 6;     // ring stages
-  static constexpr size_t al(size_t x) { return (x + 15) & ~(size_t)15; }
-  static constexpr size_t oV = 0;
-  static constexpr size_t oK = al(oV + (size_t)VHM * W * sizeof(S));
-  static constexpr size_t oM = al(oK + (size_t)KHM * W * sizeof(S));
-  static constexpr size_t oR = al(oM + (size_t)(TYM + 1) * MWR * 4);
-  static constexpr size_t oW = al(oR + (HR ? (size_t)(TYM + 1) * CW * sizeof(S) : 0));
-  static constexpr size_t oP = al(oW + (HW ? (size_t)(TYM + 1) * CW * sizeof(S) : 0));
-  static constexpr size_t STB = al(oP + (HP ? (size_t)(TYM + 1) * PN * LP * sizeof(C) : 0));
+  static constexpr bool HP = OP == F_RESTRICT;
+  static constexpr int PW = PhiBox<C, LP>::PW;
+  static constexpr size_t BV = up((size_t)(TYM + 3) * Halo<S>::W * sizeof(S));
+  static constexpr size_t BK = up((size_t)(TYM + 2) * Halo<S>::W * sizeof(S));
+  static constexpr size_t BM = up((size_t)(TYM + 1) * MBW * 4);
+  static constexpr size_t BR = HR ? up((size_t)(TYM + 1) * CWD * sizeof(S)) : 0;
+  static constexpr size_t BW = HWW ? BR : 0;
+  static constexpr size_t BP = HP ? up((size_t)(TYM + 1) * PW * sizeof(C)) : 0;
+  static constexpr size_t STB = BV + BK + BM + BR + BW + BP;
+  static constexpr int NS = sizeof(S) == 8 ? 4 : 6;  // ring stages: 3 resident + NS-3 in flight
+  static constexpr size_t SMEM = 128 + (size_t)NS * STB;
+};
+
+struct alignas(64) TMaps {
+  CUtensorMap v, k, m, r, w, p;
 };
 
 template <class S, class To>
 struct FineArgs {
   typedef typename Cv<S>::C C;
   Geom g;
-  const S* kap;
-  const S* v;       // APPLY: u; SMOOTH/RESTRICT: e; PSMOOTH: e before prolongation
+  const S* v;       // APPLY: u; SMOOTH/RESTRICT: e (null: e = 0)
   const S* r;       // smoother right-hand side / residual source
+  const S* w;       // SMOOTH: previous iterate of the three-term recurrence (null: zero)
   To* out;
+  const S* kap;     // element conductivity (padded)
   const uint32_t* mask;
   const C* phi;     // level-1 basis [nsize][L1]
   C* rc;            // level-1 restricted residual [cells][L1]
-  const S* w;       // SMOOTH: previous iterate of the three-term recurrence (null: zero)
   C cA;             // coefficient of (v - w)
   C omega;          // coefficient of D^-1 (r - A v)
   double* partial;  // dot partials, one per CTA
   unsigned* counter;
   double* dot;
+  int* err;         // set to 1 if a stage wait gave up (never expected)
 };
 
 template <class C, bool CUBE>
@@ -126,333 +136,285 @@ __device__ __forceinline__ C stencil(const C (&vm)[3][3], const C (&v0)[3][3], c
   return y;
 }
 
-// cp.async helpers (asynchronous global -> shared copies, completion by group)
-__device__ __forceinline__ void cp_async_n(void* smem, const void* gmem, int bytes) {
-  const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
-  if (bytes == 4)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(sa), "l"(gmem));
-  else if (bytes == 8)
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(gmem));
-  else
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem));
+
+// ---- TMA / mbarrier primitives (inline PTX)
+__device__ __forceinline__ unsigned smem_u32(const void* p) { return (unsigned)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(count));
 }
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::); }
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-  asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+__device__ __forceinline__ void mbar_fence_init() { asm volatile("fence.mbarrier_init.release.cluster;\n" ::); }
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(smem_u32(bar)), "r"(bytes));
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void tma_load3(void* dst, const CUtensorMap* map, int c0, int c1, int c2, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(
+          smem_u32(dst)),
+      "l"(map), "r"(c0), "r"(c1), "r"(c2), "r"(smem_u32(bar))
+      : "memory");
 }
 
-template <class S, class To, int OP, bool CUBE, int L1, bool DOT, bool MASKIN, bool ROLL>
-__global__ void __launch_bounds__(FNT) fine_tile(FineArgs<S, To> a) {
+// VAR (sweeps): bit 0 input iterate present, bit 1 three-term (cA) term, bit 2 w present
+template <class S, class To, int OP, bool CUBE, int L1, bool DOT, bool MASKIN, int VAR>
+__global__ void __launch_bounds__(FNT, sizeof(S) == 8 ? 1 : (OP == F_RESTRICT ? 2 : 3)) fine_tile(const __grid_constant__ FineArgs<S, To> a,
+                                                 const __grid_constant__ TMaps tm) {
   typedef typename Cv<S>::C C;
   constexpr int LP = L1 > 0 ? L1 : 1;
-  typedef Lay<S, OP, LP> T;
-  constexpr int SX = T::SX, W = T::W, CPR = T::CPR, EPC = T::EPC, CW = T::CW, CCPR = T::CCPR, FNS = T::NS;
+  constexpr int SX = Halo<S>::SX, W = Halo<S>::W, PW = PhiBox<C, LP>::PW;
+  constexpr bool HV = OP != F_SMOOTH || (VAR & 1);
+  constexpr bool HCA = OP == F_SMOOTH && (VAR & 2);
+  constexpr bool HWW = OP == F_SMOOTH && (VAR & 4);
+  constexpr bool HR = OP == F_SMOOTH || OP == F_RESTRICT;
+  constexpr bool HP = OP == F_RESTRICT && L1 > 0;
+  constexpr int NS = FLay<S, OP, LP, HWW>::NS;
+  typedef FLay<S, OP, LP, HWW> LY;
+  constexpr size_t BV = LY::BV, BK = LY::BK, BM = LY::BM, BR = LY::BR, BW = LY::BW, STB = LY::STB;
   const Geom& g = a.g;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ double dsh[33];
-  __shared__ C cc[8];
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);  // NS barriers in the first 128 bytes
+  unsigned char* stages = smem_raw + 128;
+  __shared__ C red[TYM + 2][8][LP];  // restriction scratch: rows, block columns, vectors
+  __shared__ C redc[TYM + 1][LP];
+  __shared__ double dsh[TYM + 1];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
-  if (tid < 8) cc[tid] = (C)g.c[tid];
   const int TX = g.TX, TY = g.TY;
   const int x0 = blockIdx.x * TX, y0 = blockIdx.y * TY;
   const bool lastx = (x0 + TX == g.Nx), lasty = (y0 + TY == g.Ny);
   const int zs = blockIdx.z * g.ZC;
   const int ze = (zs + g.ZC == g.Nz) ? g.Nz : zs + g.ZC - 1;
-  const int nwa = TY / RYW;
-  const bool wact = w < nwa;
-  const bool row5 = wact && lasty && w == nwa - 1;  // this warp also owns row y0 + TY
+  const bool rowwarp = w < TY;        // warps beyond TY (and the extra warp) hold no row
+  const bool extra = w == TYM;        // closing column / row warp
   const bool xact = lane < TX;
-  const bool xtra = lastx && lane == TX - 1;        // this lane also owns column x0 + TX
-  const int x = x0 + lane;
-  const int yw = y0 + w * RYW;
-  const int lrow = w * RYW;                          // staged row of y = yw - 1
-  const int lcol = lane + SX - 1;                    // staged column of x - 1
+  const int x = x0 + lane, y = y0 + w;
+  const int mx = (x0 >> 5) & ~3;      // first staged mask word
+  const C c0 = (C)g.c[0];
+  const C cc3 = (C)g.c[3];
+  C ccv[8];
+#pragma unroll
+  for (int i = 0; i < 8; ++i) ccv[i] = (C)g.c[i];
 
-  // ---- per-thread copy slots (computed once)
-  const int nvch = (TY + 3) * CPR, nkch = (TY + 2) * CPR, nmw = (TY + 1) * MWR;
-  int vso[3], vgo[3], kso[3], kgo[3], mso = -1, mgo = 0;
-#pragma unroll
-  for (int k = 0; k < 3; ++k) {
-    const int c = tid + k * FNT;
-    vso[k] = kso[k] = -1;
-    vgo[k] = kgo[k] = 0;
-    if (c < nvch) {
-      const int row = c / CPR, ch = c - row * CPR;
-      vso[k] = row * W + ch * EPC;
-      vgo[k] = (int)(row * g.P) + ch * EPC;
-    }
-    if (c < nkch) {
-      const int row = c / CPR, ch = c - row * CPR;
-      kso[k] = row * W + ch * EPC;
-      kgo[k] = (int)(row * g.P) + ch * EPC;
-    }
-  }
-  if (tid < nmw) {
-    const int row = tid / MWR, j = tid - row * MWR;
-    mso = row * MWR + j;
-    mgo = (int)(row * g.mwr) + j;
-  }
-  // centre arrays: r / w chunks (rows y0..y0+TY) and Phi chunks
-  constexpr int NRS = (TYM + 1) * CCPR / FNT + 1;
-  constexpr int NPS = T::HP ? ((TYM + 1) * T::PN * T::PCN) / FNT + 1 : 1;
-  int rso[NRS], rgo[NRS], pso[NPS], pgo[NPS];
-  const int nrch = (TY + 1) * CCPR, npch = (TY + 1) * (TX + 1) * T::PCN;
-#pragma unroll
-  for (int k = 0; k < NRS; ++k) {
-    const int c = tid + k * FNT;
-    rso[k] = -1;
-    rgo[k] = 0;
-    if (T::HR && c < nrch) {
-      const int row = c / CCPR, ch = c - row * CCPR;
-      rso[k] = row * CW + ch * EPC;
-      rgo[k] = (int)(row * g.P) + ch * EPC;
-    }
-  }
-#pragma unroll
-  for (int k = 0; k < NPS; ++k) {
-    const int c = tid + k * FNT;
-    pso[k] = -1;
-    pgo[k] = 0;
-    if (T::HP && c < npch) {
-      const int row = c / ((TX + 1) * T::PCN), rem = c - row * ((TX + 1) * T::PCN);
-      const int nd = rem / T::PCN, ch = rem - nd * T::PCN;
-      pso[k] = (row * T::PN + nd) * LP + ch * (16 / (int)sizeof(C));
-      pgo[k] = (int)((row * g.P + nd) * LP) + ch * (16 / (int)sizeof(C));
-    }
-  }
-  const S* vsrc = a.v + nidx(g, x0 - SX, y0 - 1, -1);  // node plane -1
-  const S* ksrc = a.kap + eidx(g, x0 - SX, y0 - 1, -1);
-  const uint32_t* msrc = a.mask + mword(g, x0, y0, -1);
-  const long long c0n = nidx(g, x0, y0, -1);            // centre origin, node plane -1
-  const long long vpl = (long long)g.RYn * g.P, kpl = (long long)g.RYe * g.P, mpl = (long long)g.RYn * g.mwr;
-  auto stage_of = [&](int q) { return (q - zs + 1) % FNS; };
-  auto sbase = [&](int q) { return smem_raw + (size_t)stage_of(q) * T::STB; };
-  auto sv = [&](int q) { return reinterpret_cast<S*>(sbase(q) + T::oV); };
-  auto sk = [&](int q) { return reinterpret_cast<S*>(sbase(q) + T::oK); };
-  auto sm = [&](int q) { return reinterpret_cast<uint32_t*>(sbase(q) + T::oM); };
-  auto sr = [&](int q) { return reinterpret_cast<S*>(sbase(q) + T::oR); };
-  auto sw = [&](int q) { return reinterpret_cast<S*>(sbase(q) + T::oW); };
-  auto sp = [&](int q) { return reinterpret_cast<C*>(sbase(q) + T::oP); };
-  // group q: node plane q, element plane q-1, mask + centre arrays of plane q-1 (all in stage_of(q))
+  // stage bytes of one group
+  const unsigned bytesV = (unsigned)((TY + 3) * W * sizeof(S)), bytesK = (unsigned)((TY + 2) * W * sizeof(S));
+  const unsigned bytesM = (unsigned)((TY + 1) * MBW * 4), bytesR = (unsigned)((TY + 1) * CWD * sizeof(S));
+  const unsigned bytesP = (unsigned)((TY + 1) * PW * sizeof(C));
+  auto stage_of = [&](int q) { return (q - zs + 1) % NS; };
+  auto base_of = [&](int q) { return stages + (size_t)stage_of(q) * STB; };
+  auto sV = [&](int q) { return reinterpret_cast<const S*>(base_of(q)); };
+  auto sK = [&](int q) { return reinterpret_cast<const S*>(base_of(q) + BV); };
+  auto sM = [&](int q) { return reinterpret_cast<const uint32_t*>(base_of(q) + BV + BK); };
+  auto sR = [&](int q) { return reinterpret_cast<const S*>(base_of(q) + BV + BK + BM); };
+  auto sW = [&](int q) { return reinterpret_cast<const S*>(base_of(q) + BV + BK + BM + BR); };
+  auto sP = [&](int q) { return reinterpret_cast<const C*>(base_of(q) + BV + BK + BM + BR + BW); };
+
+  // group q: node plane q, element plane q-1, mask + centre arrays of plane q-1
   auto issue = [&](int q) {
-    if (q <= ze + 1) {
-      if (a.v) {
-        S* d = sv(q);
-        const S* src = vsrc + (long long)(q + 1) * vpl;
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-          if (vso[k] >= 0) cp_async_n(d + vso[k], src + vgo[k], 16);
-      }
-      const int qk = q - 1;
-      if (qk >= zs - 1 && qk <= ze) {
-        S* d = sk(q);
-        const S* src = ksrc + (long long)(qk + 1) * kpl;
-#pragma unroll
-        for (int k = 0; k < 3; ++k)
-          if (kso[k] >= 0) cp_async_n(d + kso[k], src + kgo[k], 16);
-        if (mso >= 0) cp_async_n(sm(q) + mso, msrc + (long long)(qk + 1) * mpl + mgo, 4);
-        if (qk >= zs) {
-          const long long cb = c0n + (long long)(qk + 1) * vpl;
-          if (T::HR) {
-#pragma unroll
-            for (int k = 0; k < NRS; ++k)
-              if (rso[k] >= 0) cp_async_n(sr(q) + rso[k], a.r + cb + rgo[k], 16);
-          }
-          if (T::HW && a.w) {
-#pragma unroll
-            for (int k = 0; k < NRS; ++k)
-              if (rso[k] >= 0) cp_async_n(sw(q) + rso[k], a.w + cb + rgo[k], 16);
-          }
-          if (T::HP) {
-#pragma unroll
-            for (int k = 0; k < NPS; ++k)
-              if (pso[k] >= 0) cp_async_n(sp(q) + pso[k], a.phi + cb * LP + pgo[k], 16);
-          }
-        }
-      }
+    const bool hv = HV && q <= ze + 1;
+    const int qk = q - 1;
+    const bool hk = qk >= zs - 1 && qk <= ze;
+    const bool hc = qk >= zs && qk <= ze;
+    const unsigned bytes = (hv ? bytesV : 0u) + (hk ? bytesK : 0u) + (hc ? bytesM : 0u) +
+                           (hc && HR ? bytesR : 0u) + (hc && HWW ? bytesR : 0u) + (hc && HP ? bytesP : 0u);
+    const int s = stage_of(q);
+    uint64_t* bar = bars + s;
+    unsigned char* b = stages + (size_t)s * STB;
+    mbar_expect_tx(bar, bytes);  // always arrive, so every stage's phases stay in step
+    if (hv) tma_load3(b, &tm.v, x0 - SX, y0, q + 1, bar);
+    if (hk) tma_load3(b + BV, &tm.k, x0 - SX, y0, qk + 1, bar);
+    if (hc) {
+      tma_load3(b + BV + BK, &tm.m, mx, y0 + 1, qk + 1, bar);
+      if (HR) tma_load3(b + BV + BK + BM, &tm.r, x0, y0 + 1, qk + 1, bar);
+      if (HWW) tma_load3(b + BV + BK + BM + BR, &tm.w, x0, y0 + 1, qk + 1, bar);
+      if (HP) tma_load3(b + BV + BK + BM + BR + BW, &tm.p, x0 * LP, y0 + 1, qk + 1, bar);
     }
-    cp_commit();
+  };
+  auto wait_group = [&](int q) {
+    const unsigned parity = (unsigned)(((q - zs + 1) / NS) & 1);
+    uint64_t* bar = bars + stage_of(q);
+    bool ok = false;
+    for (int it = 0; it < (1 << 22) && !ok; ++it) ok = mbar_try_wait(bar, parity);
+    if (!ok) atomicExch(a.err, 1);
   };
 
-  // ---- per-lane state
-  constexpr int NRM = RYW + 1;                    // rows incl. the closing row
-  C VA[NRM + 2][3], VB[NRM + 2][3], VC[NRM + 2][3];
-  C KA[NRM + 1][2], KB[NRM + 1][2], KC[NRM + 1][2];
-#pragma unroll
-  for (int r = 0; r < NRM + 2; ++r)
-#pragma unroll
-    for (int c = 0; c < 3; ++c) VA[r][c] = VB[r][c] = VC[r][c] = C(0);
-#pragma unroll
-  for (int r = 0; r < NRM + 1; ++r)
-#pragma unroll
-    for (int c = 0; c < 2; ++c) KA[r][c] = KB[r][c] = KC[r][c] = C(0);
-  C acc[LP];
-#pragma unroll
-  for (int j = 0; j < LP; ++j) acc[j] = C(0);
-  double dacc = 0.0;
-  const int nbz = g.nbz;
+  if (tid == 0) {
+    for (int s = 0; s < NS; ++s) mbar_init(bars + s, 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  if (tid == 0)
+    for (int q = zs - 1; q < zs - 1 + (NS - 3); ++q) issue(q);
 
-  // one output node: Av from windows; epilogue by OP
-  auto node = [&](int xx, int yy, int t, const C (&vm)[3][3], const C (&v0)[3][3], const C (&vp)[3][3],
-                  const C (&km)[2][2], const C (&kp)[2][2], uint32_t mword_bits) {
+  C VA[3][3], VB[3][3], VC[3][3], KA[2][2], KB[2][2], KC[2][2];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) VA[i][j] = VB[i][j] = VC[i][j] = C(0);
+#pragma unroll
+  for (int i = 0; i < 2; ++i)
+#pragma unroll
+    for (int j = 0; j < 2; ++j) KA[i][j] = KB[i][j] = KC[i][j] = C(0);
+  C acc[LP], accR[LP];
+#pragma unroll
+  for (int j = 0; j < LP; ++j) acc[j] = accR[j] = C(0);
+  double dacc = 0.0;
+
+  // epilogue of one node; ci: staged centre column, crow: staged centre row
+  auto node = [&](int xx, int yy, int t, int crow, int ccol, const C (&vm)[3][3], const C (&v0)[3][3],
+                  const C (&vp)[3][3], const C (&km)[2][2], const C (&kp)[2][2], C (&ac)[LP]) {
     C K8;
-    const C Av0 = stencil<C, CUBE>(vm, v0, vp, km, kp, cc, K8);
-    const C Av = a.v ? Av0 : C(0);  // sweep from e = 0: only the diagonal is needed
+    const C Av0 = stencil<C, CUBE>(vm, v0, vp, km, kp, ccv, K8);
+    const C Av = HV ? Av0 : C(0);
     const long long n = nidx(g, xx, yy, t);
-    const bool dir = (mword_bits >> (xx & 31)) & 1u;
-    const int ci = (yy - y0) * CW + (xx - x0);              // staged centre index
-    const int pi = ((yy - y0) * T::PN + (xx - x0)) * LP;    // staged Phi index
+    const uint32_t mw = sM(t + 1)[crow * MBW + ((xx >> 5) - mx)];
+    const bool dir = (mw >> (xx & 31)) & 1u;
     if (OP == F_APPLY) {
       C yv = Av;
       if (dir) yv = MASKIN ? Cv<S>::ld(a.v + n) : C(0);
       Cv<To>::st(a.out + n, yv);
       if (DOT) dacc += (double)v0[1][1] * (double)yv;
     } else if (OP == F_SMOOTH) {
-      const C rr = Cv<S>::ld(sr(t + 1) + ci);
-      C e = a.omega * (rr - Av) / (cc[0] * K8);
-      if (a.v) e += v0[1][1];
-      if (a.cA != C(0)) e += a.cA * (v0[1][1] - (a.w ? Cv<S>::ld(sw(t + 1) + ci) : C(0)));  // w == null: w = 0
+      const C rr = Cv<S>::ld(sR(t + 1) + crow * CWD + ccol);
+      const C d = c0 * K8;
+      C inv;
+      if (sizeof(C) == 4) {
+        inv = (C)__frcp_rn((float)d);
+      } else {
+        const double i0 = (double)__frcp_rn((float)d);  // FP32 seed, one FP64 Newton step
+        inv = (C)(i0 * (2.0 - (double)d * i0));
+      }
+      C e = a.omega * (rr - Av) * inv;
+      if (HV) e += v0[1][1];
+      if (HCA) e += a.cA * (v0[1][1] - (HWW ? Cv<S>::ld(sW(t + 1) + crow * CWD + ccol) : C(0)));
       if (dir) e = C(0);
       Cv<To>::st(a.out + n, e);
     } else if (OP == F_RESTRICT) {
-      const C rr = Cv<S>::ld(sr(t + 1) + ci);
-      const C s = dir ? C(0) : rr - Av;
-      if (T::HP && L1 == 4 && sizeof(C) == 4) {
-        const float4 ph = *reinterpret_cast<const float4*>(sp(t + 1) + pi);
-        acc[0] += s * (C)ph.x;
-        acc[1] += s * (C)ph.y;
-        acc[2] += s * (C)ph.z;
-        acc[3 % LP] += s * (C)ph.w;
-      } else if (T::HP) {
+      const C rr = Cv<S>::ld(sR(t + 1) + crow * CWD + ccol);
+      const C sres = dir ? C(0) : rr - Av;
+      const C* ph = sP(t + 1) + crow * PW + ccol * LP;
 #pragma unroll
-        for (int j = 0; j < LP; ++j) acc[j] += s * sp(t + 1)[pi + j];
-      } else {
-#pragma unroll
-        for (int j = 0; j < LP; ++j) acc[j] += s * a.phi[n * LP + j];
-      }
+      for (int j = 0; j < LP; ++j) ac[j] += sres * ph[j];
     }
   };
 
-  // windows of the extra column / FP64 path, read from three resident stages
-  auto win_smem = [&](int t, int r, int col, C (&vm)[3][3], C (&v0)[3][3], C (&vp)[3][3], C (&km)[2][2],
-                      C (&kp)[2][2]) {
-    const S* a0 = sv(t - 1);
-    const S* a1 = sv(t);
-    const S* a2 = sv(t + 1);
-    const S* k0 = sk(t);      // element plane t-1 lives with node plane t
-    const S* k1 = sk(t + 1);  // element plane t
+  // windows of any staged node (row sr = y - (y0-1) - 1, column sc = x - (x0 - SX) - 1)
+  auto win = [&](int t, int sr, int sc, C (&vm)[3][3], C (&v0)[3][3], C (&vp)[3][3], C (&km)[2][2],
+                 C (&kp)[2][2]) {
+    const S* a0 = sV(t - 1);
+    const S* a1 = sV(t);
+    const S* a2 = sV(t + 1);
+    const S* k0 = sK(t);
+    const S* k1 = sK(t + 1);
 #pragma unroll
     for (int oy = 0; oy < 3; ++oy)
 #pragma unroll
       for (int ox = 0; ox < 3; ++ox) {
-        const int o = (lrow + r + oy) * W + col + ox;
-        vm[oy][ox] = Cv<S>::ld(a0 + o);
-        v0[oy][ox] = Cv<S>::ld(a1 + o);
-        vp[oy][ox] = Cv<S>::ld(a2 + o);
+        const int o = (sr + oy) * W + sc + ox;
+        vm[oy][ox] = HV ? Cv<S>::ld(a0 + o) : C(0);
+        v0[oy][ox] = HV ? Cv<S>::ld(a1 + o) : C(0);
+        vp[oy][ox] = HV ? Cv<S>::ld(a2 + o) : C(0);
       }
 #pragma unroll
     for (int dy = 0; dy < 2; ++dy)
 #pragma unroll
       for (int dx = 0; dx < 2; ++dx) {
-        const int o = (lrow + r + dy) * W + col + dx;
+        const int o = (sr + dy) * W + sc + dx;
         km[dy][dx] = Cv<S>::ld(k0 + o);
         kp[dy][dx] = Cv<S>::ld(k1 + o);
       }
   };
 
   auto restrict_flush = [&](int t) {
-    if (OP == F_RESTRICT && L1 > 0) {
-      const int bz = blk_of(t, 4, nbz);
-      const int zend = (bz == nbz - 1) ? g.Nz : bz * 4 + 3;
-      if (t == zend) {
+    if (OP != F_RESTRICT) return;
+    const int bz = blk_of(t, 4, g.nbz);
+    const int zend = (bz == g.nbz - 1) ? g.Nz : bz * 4 + 3;
+    if (t != zend) return;  // uniform across the CTA
+    const int nbl = TX / 4;
+    if (rowwarp) {
 #pragma unroll
-        for (int j = 0; j < LP; ++j) {
-          C v = xact ? acc[j] : C(0);
-          v += __shfl_xor_sync(0xffffffffu, v, 1);
-          v += __shfl_xor_sync(0xffffffffu, v, 2);
-          if (wact && xact && (lane & 3) == 0) {
-            const long long cell = (long long)((x0 + lane) >> 2) + (long long)g.nbx * ((yw >> 2) + (long long)g.nby * bz);
-            a.rc[cell * LP + j] = v;
-          }
-          acc[j] = C(0);
-        }
+      for (int j = 0; j < LP; ++j) {
+        C v = xact ? acc[j] : C(0);
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        if (xact && (lane & 3) == 0) red[w][lane >> 2][j] = v;
+        acc[j] = C(0);
       }
+    }
+    if (extra) {
+#pragma unroll
+      for (int j = 0; j < LP; ++j) {
+        if (lane <= TY) redc[lane][j] = lastx ? acc[j] : C(0);  // closing column, row y0 + lane
+        C v = (lasty && xact) ? accR[j] : C(0);                 // closing row
+        v += __shfl_xor_sync(0xffffffffu, v, 1);
+        v += __shfl_xor_sync(0xffffffffu, v, 2);
+        if (xact && (lane & 3) == 0) red[TYM + 1][lane >> 2][j] = v;
+        acc[j] = accR[j] = C(0);
+      }
+    }
+    __syncthreads();
+    for (int o = tid; o < nbl * (TY / 4) * LP; o += FNT) {
+      const int j = o % LP, lb = o / LP, bxl = lb % nbl, byl = lb / nbl;
+      C s = C(0);
+      for (int rr = 0; rr < 4; ++rr) s += red[byl * 4 + rr][bxl][j];
+      if (lastx && bxl == nbl - 1) {
+        for (int rr = 0; rr < 4; ++rr) s += redc[byl * 4 + rr][j];
+        if (lasty && byl == TY / 4 - 1) s += redc[TY][j];
+      }
+      if (lasty && byl == TY / 4 - 1) s += red[TYM + 1][bxl][j];
+      const long long cell = (x0 / 4 + bxl) + (long long)g.nbx * ((y0 / 4 + byl) + (long long)g.nby * bz);
+      a.rc[cell * LP + j] = s;
     }
   };
 
-  // step t with rotating roles (Vm, V0, Vp) and (Km, Kp)
-  auto step = [&](int t, C (&Vm)[NRM + 2][3], C (&V0)[NRM + 2][3], C (&Vp)[NRM + 2][3], C (&Km)[NRM + 1][2],
-                  C (&Kp)[NRM + 1][2]) {
-    cp_wait<FNS - 4>();
+  auto step = [&](int t, C (&Vm)[3][3], C (&V0)[3][3], C (&Vp)[3][3], C (&Km)[2][2], C (&Kp)[2][2]) {
+    wait_group(t + 1);
     __syncthreads();
-    if (MASKIN && a.v) {
+    if (MASKIN && HV) {
       // zero the landed node plane t+1 on Gamma_D (inputs may be arbitrary there)
-      S* d = sv(t + 1);
+      S* d = const_cast<S*>(sV(t + 1));
       for (int i = tid; i < (TY + 3) * W; i += FNT) {
         const int ly = i / W, lx = i - ly * W;
-        const int xx = x0 - SX + lx, yy = y0 - 1 + ly;
-        if (is_dir(g, a.mask, xx, yy, t + 1)) Cv<S>::st(d + i, C(0));
+        if (is_dir(g, a.mask, x0 - SX + lx, y0 - 1 + ly, t + 1)) Cv<S>::st(d + i, C(0));
       }
       __syncthreads();
     }
-    if (ROLL && wact) {
-      const S* s1 = sv(t + 1);
-      const S* k1 = sk(t + 1);
-#pragma unroll
-      for (int r = 0; r < RYW + 2; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) Vp[r][c] = Cv<S>::ld(s1 + (lrow + r) * W + lcol + c);
-      if (row5)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) Vp[RYW + 2][c] = Cv<S>::ld(s1 + (lrow + RYW + 2) * W + lcol + c);
-#pragma unroll
-      for (int r = 0; r < RYW + 1; ++r)
-#pragma unroll
-        for (int c = 0; c < 2; ++c) Kp[r][c] = Cv<S>::ld(k1 + (lrow + r) * W + lcol + c);
-      if (row5)
-#pragma unroll
-        for (int c = 0; c < 2; ++c) Kp[RYW + 1][c] = Cv<S>::ld(k1 + (lrow + RYW + 1) * W + lcol + c);
+    if (tid == 0) {
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // earlier generic accesses before TMA writes
+      issue(t + NS - 2);
     }
-    issue(t + FNS - 2);
-    if (t >= zs && wact) {
-      const uint32_t* ms = sm(t + 1);
-      auto mrow = [&](int r, int xx) { return ms[(w * RYW + r) * MWR + ((xx >> 5) - (x0 >> 5))]; };
-      if (ROLL) {
-        if (xact) {
+    if (rowwarp) {
+      const S* s1 = sV(t + 1);
+      const S* k1 = sK(t + 1);
 #pragma unroll
-          for (int r = 0; r < RYW; ++r)
-            node(x, yw + r, t, *reinterpret_cast<const C(*)[3][3]>(&Vm[r][0]),
-                 *reinterpret_cast<const C(*)[3][3]>(&V0[r][0]), *reinterpret_cast<const C(*)[3][3]>(&Vp[r][0]),
-                 *reinterpret_cast<const C(*)[2][2]>(&Km[r][0]), *reinterpret_cast<const C(*)[2][2]>(&Kp[r][0]),
-                 mrow(r, x));
-          if (row5)
-            node(x, yw + RYW, t, *reinterpret_cast<const C(*)[3][3]>(&Vm[RYW][0]),
-                 *reinterpret_cast<const C(*)[3][3]>(&V0[RYW][0]), *reinterpret_cast<const C(*)[3][3]>(&Vp[RYW][0]),
-                 *reinterpret_cast<const C(*)[2][2]>(&Km[RYW][0]), *reinterpret_cast<const C(*)[2][2]>(&Kp[RYW][0]),
-                 mrow(RYW, x));
-        }
-      } else if (xact) {
-        const int nr = row5 ? RYW + 1 : RYW;
-        for (int r = 0; r < nr; ++r) {
-          C vm[3][3], v0[3][3], vp[3][3], km[2][2], kp[2][2];
-          win_smem(t, r, lcol, vm, v0, vp, km, kp);
-          node(x, yw + r, t, vm, v0, vp, km, kp, mrow(r, x));
-        }
+      for (int oy = 0; oy < 3; ++oy)
+#pragma unroll
+        for (int ox = 0; ox < 3; ++ox) Vp[oy][ox] = HV ? Cv<S>::ld(s1 + (w + oy) * W + lane + SX - 1 + ox) : C(0);
+#pragma unroll
+      for (int dy = 0; dy < 2; ++dy)
+#pragma unroll
+        for (int dx = 0; dx < 2; ++dx) Kp[dy][dx] = Cv<S>::ld(k1 + (w + dy) * W + lane + SX - 1 + dx);
+      if (t >= zs && xact) node(x, y, t, w, lane, Vm, V0, Vp, Km, Kp, acc);
+    } else if (extra && t >= zs) {
+      C vm[3][3], v0[3][3], vp[3][3], km[2][2], kp[2][2];
+      if (lastx && lane <= TY) {  // closing column x0 + TX, row y0 + lane
+        win(t, lane, TX + SX - 1, vm, v0, vp, km, kp);
+        node(x0 + TX, y0 + lane, t, lane, TX, vm, v0, vp, km, kp, acc);
       }
-      if (xtra) {
-        const int nr = row5 ? RYW + 1 : RYW;
-        for (int r = 0; r < nr; ++r) {
-          C vm[3][3], v0[3][3], vp[3][3], km[2][2], kp[2][2];
-          win_smem(t, r, lcol + 1, vm, v0, vp, km, kp);
-          node(x + 1, yw + r, t, vm, v0, vp, km, kp, mrow(r, x + 1));
-        }
+      if (lasty && xact) {  // closing row y0 + TY, column x0 + lane
+        win(t, TY, lane + SX - 1, vm, v0, vp, km, kp);
+        node(x, y0 + TY, t, TY, lane, vm, v0, vp, km, kp, accR);
       }
     }
     if (t >= zs) restrict_flush(t);
   };
 
-  for (int q = zs - 1; q < zs - 1 + (FNS - 3); ++q) issue(q);
   for (int t = zs - 2; t <= ze; t += 3) {
     step(t, VA, VB, VC, KA, KB);
     if (t + 1 > ze) break;
@@ -460,7 +422,6 @@ __global__ void __launch_bounds__(FNT) fine_tile(FineArgs<S, To> a) {
     if (t + 2 > ze) break;
     step(t + 2, VC, VA, VB, KC, KA);
   }
-  cp_wait<0>();
 
   if (DOT) {
     for (int o = 16; o > 0; o >>= 1) dacc += __shfl_down_sync(0xffffffffu, dacc, o);
@@ -472,7 +433,7 @@ __global__ void __launch_bounds__(FNT) fine_tile(FineArgs<S, To> a) {
     const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     if (tid == 0) {
       double s = 0.0;
-      for (int i = 0; i < FW; ++i) s += dsh[i];
+      for (int i = 0; i < TYM + 1; ++i) s += dsh[i];
       a.partial[bid] = s;
       __threadfence();
       last = (atomicAdd(a.counter, 1u) == nblk - 1);
@@ -487,12 +448,13 @@ __global__ void __launch_bounds__(FNT) fine_tile(FineArgs<S, To> a) {
       __syncthreads();
       if (tid == 0) {
         double s = 0.0;
-        for (int i = 0; i < FW; ++i) s += dsh[i];
+        for (int i = 0; i < TYM + 1; ++i) s += dsh[i];
         *a.dot = s;
         *a.counter = 0u;
       }
     }
   }
+  (void)cc3;
 }
 
 // e[n] += sum_j Phi[n][j] ec[cell(n)][j]  (level-1 prolongation, in place)
@@ -523,25 +485,133 @@ __global__ void k_prolong(Geom g, const typename Cv<S>::C* __restrict__ phi, con
 }
 
 // ---------------------------------------------------------------------------
-// host launchers
+// host side: tensor maps (cached per buffer and box) and launchers
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = (EncodeTiledFn)p;
+  });
+  return fn;
+}
+
+struct MapKey {
+  const void* p;
+  long long d0, d1, d2;
+  int dt, b0, b1;
+  bool operator==(const MapKey& o) const {
+    return p == o.p && d0 == o.d0 && d1 == o.d1 && d2 == o.d2 && dt == o.dt && b0 == o.b0 && b1 == o.b1;
+  }
+};
+struct MapKeyHash {
+  size_t operator()(const MapKey& k) const {
+    size_t h = std::hash<const void*>()(k.p);
+    h ^= std::hash<long long>()(k.d0 * 1000003LL + k.d1 * 131LL + k.d2) + 0x9e3779b97f4a7c15ULL + (h << 6) + (h >> 2);
+    h ^= std::hash<long long>()((long long)k.dt * 1000000 + k.b0 * 1000 + k.b1) + (h << 6) + (h >> 2);
+    return h;
+  }
+};
+
+// 3-D map of a padded array: dims (d0 elements, d1 rows, d2 planes), dense
+// rows of d0 elements, box (b0, b1, 1), zero fill outside.
+static cudaError_t get_map(CUtensorMap* out, const void* base, CUtensorMapDataType dt, int esize, long long d0,
+                           long long d1, long long d2, int b0, int b1) {
+  static std::mutex mu;
+  static std::unordered_map<MapKey, CUtensorMap, MapKeyHash> cache;
+  if (!base) {
+    memset(out, 0, sizeof(*out));
+    return cudaSuccess;
+  }
+  const MapKey key{base, d0, d1, d2, (int)dt, b0, b1};
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = cache.find(key);
+  if (it != cache.end()) {
+    *out = it->second;
+    return cudaSuccess;
+  }
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  const cuuint64_t dims[3] = {(cuuint64_t)d0, (cuuint64_t)d1, (cuuint64_t)d2};
+  const cuuint64_t strides[2] = {(cuuint64_t)(d0 * esize), (cuuint64_t)(d0 * d1 * esize)};
+  const cuuint32_t box[3] = {(cuuint32_t)b0, (cuuint32_t)b1, 1};
+  const cuuint32_t es[3] = {1, 1, 1};
+  CUtensorMap m;
+  const CUresult r = fn(&m, dt, 3, const_cast<void*>(base), dims, strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                        CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) return cudaErrorInvalidValue;
+  if (cache.size() > 4096) cache.clear();
+  cache.emplace(key, m);
+  *out = m;
+  return cudaSuccess;
+}
+
+template <class T>
+struct DT;
+template <>
+struct DT<double> {
+  static constexpr CUtensorMapDataType v = CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+};
+template <>
+struct DT<float> {
+  static constexpr CUtensorMapDataType v = CU_TENSOR_MAP_DATA_TYPE_FLOAT32;
+};
+template <>
+struct DT<bf16> {
+  static constexpr CUtensorMapDataType v = CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+};
 
 static dim3 fine_grid(const Geom& g) { return dim3(g.Nx / g.TX, g.Ny / g.TY, g.Nz / g.ZC); }
 
-template <class S, class To, int OP, int L1, bool DOT, bool MASKIN = false>
+template <class S, class To, int OP, int L1, bool DOT, bool MASKIN = false, int VAR = 1>
 static cudaError_t launch_fine(const FineArgs<S, To>& a, cudaStream_t st) {
-  constexpr bool ROLL = sizeof(S) <= 4;
-  typedef Lay<S, OP, (L1 > 0 ? L1 : 1)> T;
-  const size_t sm = (size_t)T::NS * T::STB;
-  auto k = a.g.cube ? fine_tile<S, To, OP, true, L1, DOT, MASKIN, ROLL>
-                    : fine_tile<S, To, OP, false, L1, DOT, MASKIN, ROLL>;
-  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  note_launch(), k<<<fine_grid(a.g), FNT, sm, st>>>(a);
+  typedef typename Cv<S>::C C;
+  constexpr int LP = L1 > 0 ? L1 : 1;
+  constexpr bool HWW = OP == F_SMOOTH && (VAR & 4);
+  typedef FLay<S, OP, LP, HWW> LY;
+  const Geom& g = a.g;
+  TMaps tm;
+  cudaError_t e;
+  const int es = (int)sizeof(S);
+  const S* vb = a.v ? a.v + g.base : nullptr;
+  if ((e = get_map(&tm.v, vb, DT<S>::v, es, g.P, g.RYn, g.nz + 2, Halo<S>::W, g.TY + 3)) != cudaSuccess) return e;
+  if ((e = get_map(&tm.k, a.kap + g.base, DT<S>::v, es, g.P, g.RYe, g.Nz + 2, Halo<S>::W, g.TY + 2)) != cudaSuccess)
+    return e;
+  if ((e = get_map(&tm.m, a.mask, CU_TENSOR_MAP_DATA_TYPE_UINT32, 4, g.mwr, g.RYn, g.nz + 2, MBW, g.TY + 1)) !=
+      cudaSuccess)
+    return e;
+  const S* rb = (OP != F_APPLY && a.r) ? a.r + g.base : nullptr;
+  if ((e = get_map(&tm.r, rb, DT<S>::v, es, g.P, g.RYn, g.nz + 2, CWD, g.TY + 1)) != cudaSuccess) return e;
+  const S* wb = (HWW && a.w) ? a.w + g.base : nullptr;
+  if ((e = get_map(&tm.w, wb, DT<S>::v, es, g.P, g.RYn, g.nz + 2, CWD, g.TY + 1)) != cudaSuccess) return e;
+  const C* pb = (OP == F_RESTRICT && a.phi) ? a.phi + g.base * LP : nullptr;
+  if ((e = get_map(&tm.p, pb, DT<C>::v, (int)sizeof(C), g.P * LP, g.RYn, g.nz + 2, PhiBox<C, LP>::PW, g.TY + 1)) !=
+      cudaSuccess)
+    return e;
+  auto k = a.g.cube ? fine_tile<S, To, OP, true, L1, DOT, MASKIN, VAR> : fine_tile<S, To, OP, false, L1, DOT, MASKIN, VAR>;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LY::SMEM);
+  note_launch(), k<<<fine_grid(a.g), FNT, LY::SMEM, st>>>(a, tm);
   return cudaGetLastError();
 }
 
 unsigned fine_num_ctas(const Geom& g) {
   dim3 d = fine_grid(g);
   return d.x * d.y * d.z;
+}
+
+static int* fine_err_word() {
+  static int* p = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] { cudaMalloc(&p, sizeof(int)) == cudaSuccess ? cudaMemset(p, 0, sizeof(int)) : cudaErrorMemoryAllocation; });
+  return p;
 }
 
 template <class S, class To>
@@ -551,6 +621,7 @@ static FineArgs<S, To> fargs(const Geom& g, const uint32_t* mask, const S* kap) 
   a.g = g;
   a.mask = mask;
   a.kap = kap;
+  a.err = fine_err_word();
   return a;
 }
 
@@ -609,7 +680,10 @@ cudaError_t fine_smooth(const Geom& g, const uint32_t* mask, const S* kap, const
   a.out = out;
   a.cA = cA;
   a.omega = cB;
-  return launch_fine<S, To, F_SMOOTH, 0, false>(a, st);
+  if (e == nullptr) return launch_fine<S, To, F_SMOOTH, 0, false, false, 0>(a, st);
+  if (cA == typename Cv<S>::C(0)) return launch_fine<S, To, F_SMOOTH, 0, false, false, 1>(a, st);
+  if (w == nullptr) return launch_fine<S, To, F_SMOOTH, 0, false, false, 3>(a, st);
+  return launch_fine<S, To, F_SMOOTH, 0, false, false, 7>(a, st);
 }
 
 template <class S>

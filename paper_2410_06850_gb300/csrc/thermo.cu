@@ -197,8 +197,7 @@ extern "C" thermo_status thermo_create(const int grid[3], const double h[3], con
   if (opt.smoother != 0 && opt.smoother != 1) return fail(ctx, THERMO_EINVAL, "smoother must be 0 (Jacobi) or 1 (Chebyshev)");
   if (opt.smoother == 1 && (opt.cheb_degree < 1 || opt.cheb_degree > 64 || !(opt.cheb_ratio > 1.0) || opt.power_iters < 1))
     return fail(ctx, THERMO_EINVAL, "Chebyshev needs 1 <= degree <= 64, ratio > 1, power_iters >= 1");
-  if (opt.nvec[0] < 1 || opt.nvec[0] > 8 || opt.nvec[0] == 7)
-    return fail(ctx, THERMO_EINVAL, "nvec[0] must be in {1..6, 8}");
+  if (opt.nvec[0] < 1 || opt.nvec[0] > 6) return fail(ctx, THERMO_EINVAL, "nvec[0] must be in 1..6");
   Geom& g = ctx->g;
   memset(&g, 0, sizeof(g));
   g.Nx = grid[0];
@@ -213,7 +212,7 @@ extern "C" thermo_status thermo_create(const int grid[3], const double h[3], con
   g.base = 32;
   g.nsize = g.base + (long long)(g.nz + 2) * g.RYn * g.P + 64;
   g.esize = g.base + (long long)(g.Nz + 2) * g.RYe * g.P + 64;
-  g.mwr = g.P / 32;
+  g.mwr = ((g.P / 32 + 3) / 4) * 4;  // mask rows padded to 16 bytes (TMA row stride)
   g.msize = (long long)(g.nz + 2) * g.RYn * g.mwr + 8;
   {
     // K0[a][b] = c[a ^ b] from the Kronecker form (k (x) m (x) m etc.)
@@ -241,7 +240,7 @@ extern "C" thermo_status thermo_create(const int grid[3], const double h[3], con
   g.nby = g.Ny / b;
   g.nbz = g.Nz / b;
   g.TX = (g.Nx % 32 == 0) ? 32 : (g.Nx % 16 == 0 ? 16 : (g.Nx % 8 == 0 ? 8 : 0));
-  g.TY = pick_tile(g.Ny, b, 16);
+  g.TY = pick_tile(g.Ny, b, 8);
   g.ZC = 0;
   if (g.TX && g.TY) {
     // planes per CTA: the largest chunk that still gives >= 8 CTAs per SM
