@@ -192,6 +192,12 @@ void thermo_destroy(thermo_ctx *ctx);
  * THERMO_MIXED_BF16S (BF16 data, FP32 math).  u, y: device double[nodes]. */
 thermo_status thermo_apply(thermo_ctx *ctx, int precision, const double *u, double *y);
 
+/* q = A p and pq = p^T A p with the fused FP64 kernel of the CG loop (the
+ * operator of Sec. 2.2 Eq. (5) and the CG reduction of Sec. 4).  p, q device
+ * double[nodes]; p must vanish on Gamma_D (as CG directions do); pq host.
+ * Deterministic (fixed reduction order).  Synchronises the stream. */
+thermo_status thermo_apply_dot(thermo_ctx *ctx, const double *p, double *q, double *pq);
+
 /* z = B r: one MMG V-cycle (Algorithm 1) in the context's precision.
  * r, z: device double[nodes]; entries of r on Gamma_D are ignored (treated as
  * zero) and z vanishes there.  Requires setup_precond. */

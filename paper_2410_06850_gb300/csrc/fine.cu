@@ -71,7 +71,7 @@ struct FLay {
   static constexpr size_t BP = HP ? up((size_t)(TYM + 1) * PW * sizeof(C)) : 0;
   static constexpr size_t STB = BV + BK + BM + BR + BW + BP;
   static constexpr int NS = sizeof(S) == 8 ? 4 : 6;  // ring stages: 3 resident + NS-3 in flight
-  static constexpr size_t SMEM = 128 + (size_t)NS * STB;
+  static constexpr size_t SMEM = 256 + (size_t)NS * STB;  // + barriers + alignment slack
 };
 
 struct alignas(64) TMaps {
@@ -179,9 +179,12 @@ __global__ void __launch_bounds__(FNT, sizeof(S) == 8 ? 1 : (OP == F_RESTRICT ? 
   typedef FLay<S, OP, LP, HWW> LY;
   constexpr size_t BV = LY::BV, BK = LY::BK, BM = LY::BM, BR = LY::BR, BW = LY::BW, STB = LY::STB;
   const Geom& g = a.g;
-  extern __shared__ __align__(128) unsigned char smem_raw[];
+  extern __shared__ __align__(128) unsigned char smem_dyn[];
+  // TMA destinations must be 128-byte aligned: align the dynamic base by hand
+  unsigned char* smem_raw = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem_raw);  // NS barriers in the first 128 bytes
   unsigned char* stages = smem_raw + 128;
+  __shared__ int stage_bad;  // a stage wait gave up: skip the remaining waits (results invalid, flagged)
   __shared__ C red[TYM + 2][8][LP];  // restriction scratch: rows, block columns, vectors
   __shared__ C redc[TYM + 1][LP];
   __shared__ double dsh[TYM + 1];
@@ -237,14 +240,23 @@ __global__ void __launch_bounds__(FNT, sizeof(S) == 8 ? 1 : (OP == F_RESTRICT ? 
     }
   };
   auto wait_group = [&](int q) {
+    if (stage_bad) return;
     const unsigned parity = (unsigned)(((q - zs + 1) / NS) & 1);
     uint64_t* bar = bars + stage_of(q);
     bool ok = false;
-    for (int it = 0; it < (1 << 22) && !ok; ++it) ok = mbar_try_wait(bar, parity);
-    if (!ok) atomicExch(a.err, 1);
+    const long long t0 = clock64();
+    while (!ok) {
+      ok = mbar_try_wait(bar, parity);
+      if (!ok && clock64() - t0 > (1LL << 31)) break;  // ~1 s: give up, flag, never hang
+    }
+    if (!ok) {
+      stage_bad = 1;
+      atomicExch(a.err, 1);
+    }
   };
 
   if (tid == 0) {
+    stage_bad = 0;
     for (int s = 0; s < NS; ++s) mbar_init(bars + s, 1);
     mbar_fence_init();
   }
@@ -403,7 +415,9 @@ __global__ void __launch_bounds__(FNT, sizeof(S) == 8 ? 1 : (OP == F_RESTRICT ? 
       if (t >= zs && xact) node(x, y, t, w, lane, Vm, V0, Vp, Km, Kp, acc);
     } else if (extra && t >= zs) {
       C vm[3][3], v0[3][3], vp[3][3], km[2][2], kp[2][2];
-      if (lastx && lane <= TY) {  // closing column x0 + TX, row y0 + lane
+      // closing column x0 + TX, row y0 + lane; row y0 + TY only in the last tile row (else the
+      // next tile owns that node and a second evaluation would count twice in the dot)
+      if (lastx && (lane < TY || (lasty && lane == TY))) {
         win(t, lane, TX + SX - 1, vm, v0, vp, km, kp);
         node(x0 + TX, y0 + lane, t, lane, TX, vm, v0, vp, km, kp, acc);
       }
@@ -612,6 +626,15 @@ static int* fine_err_word() {
   static std::once_flag once;
   std::call_once(once, [] { cudaMalloc(&p, sizeof(int)) == cudaSuccess ? cudaMemset(p, 0, sizeof(int)) : cudaErrorMemoryAllocation; });
   return p;
+}
+
+int fine_stage_errors(bool reset) {
+  int* p = fine_err_word();
+  int h = 0;
+  if (!p) return 0;
+  cudaMemcpy(&h, p, sizeof(int), cudaMemcpyDeviceToHost);
+  if (reset && h) cudaMemset(p, 0, sizeof(int));
+  return h;
 }
 
 template <class S, class To>

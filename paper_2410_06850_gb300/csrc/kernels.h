@@ -6,6 +6,7 @@ namespace thermo {
 
 // ---- fine.cu
 unsigned fine_num_ctas(const Geom& g);
+int fine_stage_errors(bool reset);  // nonzero if a fine kernel gave up waiting for a TMA stage
 cudaError_t fine_apply_f64(const Geom& g, const uint32_t* mask, const double* kap, const double* u, double* y,
                            double* partial, unsigned* counter, double* dot, cudaStream_t st, bool mask_input = false);
 template <class S>

@@ -800,6 +800,7 @@ extern "C" thermo_status thermo_solve(thermo_ctx* ctx, const double* rhs, double
   inf.rel_res_true = bnorm > 0 ? sqrt(ctx->sc_h->rr) / bnorm : 0.0;
   CK(unpack_nodes(g, ctx->u, u, st));
   CK(cudaStreamSynchronize(st));
+  if (fine_stage_errors(true)) result = fail(ctx, THERMO_ECUDA, "a fine-grid kernel timed out waiting for its TMA stage");
   inf.iters = it;
   inf.restarts = restarts;
   inf.t_solve_ms = now_ms() - t0;
@@ -851,6 +852,21 @@ extern "C" thermo_status thermo_apply(thermo_ctx* ctx, int precision, const doub
     return fail(ctx, THERMO_EINVAL, "unknown precision %d", precision);
   }
   CK(unpack_nodes(g, ctx->q, y, st));
+  return THERMO_OK;
+}
+
+extern "C" thermo_status thermo_apply_dot(thermo_ctx* ctx, const double* p, double* q, double* pq) {
+  if (!ctx) return THERMO_EINVAL;
+  if (!p || !q || !pq) return fail(ctx, THERMO_EINVAL, "NULL argument");
+  if (!ctx->have_density) return fail(ctx, THERMO_ESTATE, "apply before set_density");
+  const Geom& g = ctx->g;
+  cudaStream_t st = ctx->st;
+  CK(pack_nodes(g, p, ctx->tmp, st));
+  CK(fine_apply_f64(g, ctx->bits, ctx->k64, ctx->tmp, ctx->q, ctx->red.partial, ctx->red.counter, ctx->dscal, st));
+  CK(unpack_nodes(g, ctx->q, q, st));
+  CK(cudaMemcpyAsync(ctx->dscal_h, ctx->dscal, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  *pq = ctx->dscal_h[0];
   return THERMO_OK;
 }
 

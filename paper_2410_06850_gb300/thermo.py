@@ -27,7 +27,7 @@ EXPORTED = ["thermo_default_options", "thermo_create", "thermo_set_density", "th
             "thermo_solve", "thermo_sensitivity", "thermo_compliance", "thermo_last_error",
             "thermo_destroy", "thermo_apply", "thermo_vcycle", "thermo_load_vector",
             "thermo_hierarchy", "thermo_export_level", "thermo_filter", "thermo_oc_update",
-            "thermo_launch_count", "thermo_bench_kernel"]
+            "thermo_launch_count", "thermo_bench_kernel", "thermo_apply_dot"]
 
 
 class thermo_options(C.Structure):
@@ -87,6 +87,7 @@ def lib():
         L.thermo_launch_count.argtypes = []
         L.thermo_launch_count.restype = C.c_longlong
         L.thermo_bench_kernel.argtypes = [vp, i, i, dp, dp]
+        L.thermo_apply_dot.argtypes = [vp, vp, vp, dp]
         for n in EXPORTED:
             if n not in ("thermo_last_error", "thermo_destroy", "thermo_launch_count"):
                 getattr(L, n).restype = C.c_int
@@ -217,6 +218,14 @@ class Solver:
         y = torch.empty_like(u)
         self._check(lib().thermo_apply(self.ctx, int(precision), _ptr(u), _ptr(y)))
         return y
+
+    def apply_dot(self, p):
+        """(q, p.q) with the fused FP64 kernel of the CG loop (p must vanish on Gamma_D)."""
+        p = _dev(p, torch.float64)
+        q = torch.empty_like(p)
+        d = C.c_double()
+        self._check(lib().thermo_apply_dot(self.ctx, _ptr(p), _ptr(q), C.byref(d)))
+        return q, d.value
 
     def vcycle(self, r):
         r = _dev(r, torch.float64)

@@ -62,3 +62,22 @@ def test_load_vector_matches_oracle():
     f = s.load_vector().cpu().numpy()
     np.testing.assert_allclose(f, P["f"], rtol=1e-14, atol=0)
     s.close()
+
+
+@pytest.mark.parametrize("N", [8, 16, 32, 64])
+def test_fused_apply_dot_matches(N):
+    """The fused q = A p, p.Ap kernel of the CG loop equals the plain apply and
+    the dot product (p zero on Gamma_D, as for CG directions)."""
+    pr = small_problem(N, kind="rand", kmin=1e-4)
+    P = oracle_problem(pr)
+    s = gpu_solver(pr, prec=0)
+    n = P["A"].shape[0]
+    p = W.uniform01(11, n) - 0.4
+    p[P["mask"]] = 0.0
+    q, pq = s.apply_dot(torch.as_tensor(p))
+    q = q.cpu().numpy()
+    ref = P["A"] @ p
+    scale = np.abs(P["A"]).dot(np.abs(p))
+    assert (np.abs(q - ref) / np.maximum(scale, 1e-300)).max() < 1e-13
+    assert abs(pq - p @ ref) <= 1e-12 * abs(p @ ref)
+    s.close()
