@@ -259,6 +259,37 @@ long long thermo_launch_count(void);
 thermo_status thermo_bench_kernel(thermo_ctx *ctx, int which, int reps, double *ms_per_launch,
                                   double *bytes_per_launch);
 
+/* Kernel-class timers (no counterpart in the paper: measurement support).
+ * When enabled, every launch of the classes below issued by thermo_solve is
+ * bracketed by a pair of CUDA events recorded on the context stream; the
+ * pairs are folded into per-class totals when thermo_solve returns (it
+ * synchronises there).  At most 4096 launches per class and solve are timed;
+ * later ones are counted in neither total.
+ *   THERMO_KT_APPLY64  fine FP64 operator apply with the fused p.Ap (CG loop)
+ *   THERMO_KT_SMOOTH   fine smoother sweeps of the V-cycle (all variants)
+ *   THERMO_KT_RESTRICT fine fused residual + restriction
+ *   THERMO_KT_PROLONG  fine prolongation
+ *   THERMO_KT_COARSE   everything below the fine grid in one V-cycle
+ *   THERMO_KT_CGVEC    CG vector kernels (update, beta, direction, conversion)
+ * bytes/flops are the algorithmic DRAM bytes and floating-point operations of
+ * the timed launches (see the kernel descriptions in the design notes):
+ * compulsory traffic of each array once, 0 where not defined (coarse). */
+enum {
+  THERMO_KT_APPLY64 = 0,
+  THERMO_KT_SMOOTH = 1,
+  THERMO_KT_RESTRICT = 2,
+  THERMO_KT_PROLONG = 3,
+  THERMO_KT_COARSE = 4,
+  THERMO_KT_CGVEC = 5,
+  THERMO_KT_COUNT = 6
+};
+/* enable != 0 creates the events (once) and zeroes the totals; 0 stops timing. */
+thermo_status thermo_kernel_timers(thermo_ctx *ctx, int enable);
+/* Totals since the last enable: summed event time (ms), timed launches,
+ * algorithmic bytes and flops.  Any output may be NULL. */
+thermo_status thermo_kernel_time(thermo_ctx *ctx, int kclass, double *ms, long long *launches, double *bytes,
+                                 double *flops);
+
 #ifdef __cplusplus
 }
 #endif

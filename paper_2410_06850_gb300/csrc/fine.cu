@@ -92,6 +92,7 @@ struct FineArgs {
   C* rc;            // level-1 restricted residual [cells][L1]
   C cA;             // coefficient of (v - w)
   C omega;          // coefficient of D^-1 (r - A v)
+  C cc[8];          // K0 coefficients c[a ^ b] in the compute type (converted on the host)
   double* partial;  // dot partials, one per CTA
   unsigned* counter;
   double* dot;
@@ -199,11 +200,9 @@ __global__ void __launch_bounds__(FNT, sizeof(S) == 8 ? 1 : (OP == F_RESTRICT ? 
   const bool xact = lane < TX;
   const int x = x0 + lane, y = y0 + w;
   const int mx = (x0 >> 5) & ~3;      // first staged mask word
-  const C c0 = (C)g.c[0];
-  const C cc3 = (C)g.c[3];
-  C ccv[8];
-#pragma unroll
-  for (int i = 0; i < 8; ++i) ccv[i] = (C)g.c[i];
+  // compute-type coefficients straight from the parameter bank (no FP64 conversions per node)
+  const C* ccv = a.cc;
+  const C c0 = a.cc[0];
 
   // stage bytes of one group
   const unsigned bytesV = (unsigned)((TY + 3) * W * sizeof(S)), bytesK = (unsigned)((TY + 2) * W * sizeof(S));
@@ -468,7 +467,6 @@ __global__ void __launch_bounds__(FNT, sizeof(S) == 8 ? 1 : (OP == F_RESTRICT ? 
       }
     }
   }
-  (void)cc3;
 }
 
 // e[n] += sum_j Phi[n][j] ec[cell(n)][j]  (level-1 prolongation, in place)
@@ -645,6 +643,7 @@ static FineArgs<S, To> fargs(const Geom& g, const uint32_t* mask, const S* kap) 
   a.mask = mask;
   a.kap = kap;
   a.err = fine_err_word();
+  for (int i = 0; i < 8; ++i) a.cc[i] = (typename Cv<S>::C)g.c[i];
   return a;
 }
 

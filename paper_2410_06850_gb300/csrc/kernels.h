@@ -61,6 +61,7 @@ cudaError_t cg_pupdate(const Geom& g, const void* z, int z_kind, double* p, cons
 cudaError_t vec_to_f64(const Geom& g, const void* src, int kind, double* dst, cudaStream_t st);
 cudaError_t fine_prolong_add(const Geom& g, const double* phi, int L1, const double* ec, double* u, cudaStream_t st);
 cudaError_t vec_mask_dir(const Geom& g, const uint32_t* bits, double* v, cudaStream_t st);
+cudaError_t vec_copy_dir(const Geom& g, const uint32_t* bits, const double* src, double* dst, cudaStream_t st);
 cudaError_t power_start(const Geom& g, const uint32_t* bits, double* v, cudaStream_t st);
 cudaError_t vec_scale(const Geom& g, double a, double* v, cudaStream_t st);
 cudaError_t fill_const(double* a, long long n, double v, cudaStream_t st);

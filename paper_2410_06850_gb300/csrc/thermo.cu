@@ -46,8 +46,19 @@ struct Lev {
 
 }  // namespace
 
+// event-pair timer of one kernel class (see thermo_kernel_timers)
+struct KTimer {
+  static const int CAP = 4096;
+  std::vector<cudaEvent_t> ev;  // 2 * CAP events, created on enable
+  int used = 0;                 // pairs recorded in the current solve
+  double ms = 0.0, bytes = 0.0, flops = 0.0, pend_bytes = 0.0, pend_flops = 0.0;
+  long long launches = 0;
+};
+
 struct thermo_ctx {
   std::string err;
+  bool kt_on = false;
+  KTimer kt[THERMO_KT_COUNT];
   cudaStream_t st = nullptr;
   thermo_options opt;
   Geom g;
@@ -375,6 +386,8 @@ extern "C" thermo_status thermo_create(const int grid[3], const double h[3], con
 extern "C" void thermo_destroy(thermo_ctx* ctx) {
   if (!ctx) return;
   if (ctx->st) cudaStreamSynchronize(ctx->st);
+  for (KTimer& t : ctx->kt)
+    for (cudaEvent_t e : t.ev) cudaEventDestroy(e);
   for (void* v : ctx->allocs) cudaFree(v);
   if (ctx->sc_h) cudaFreeHost(ctx->sc_h);
   if (ctx->status_h) cudaFreeHost(ctx->status_h);
@@ -541,6 +554,43 @@ const double* lvP<double>(Lev& l) { return l.Psi64; }
 template <>
 const float* lvP<float>(Lev& l) { return l.Psi32; }
 
+// ---- kernel-class timers: begin/end bracket one launch on the context stream
+static inline void kt_begin(thermo_ctx* ctx, int c) {
+  if (!ctx->kt_on) return;
+  KTimer& t = ctx->kt[c];
+  if (t.used < KTimer::CAP) cudaEventRecord(t.ev[2 * t.used], ctx->st);
+}
+static inline void kt_end(thermo_ctx* ctx, int c, double bytes, double flops = 0.0) {
+  if (!ctx->kt_on) return;
+  KTimer& t = ctx->kt[c];
+  if (t.used >= KTimer::CAP) return;
+  cudaEventRecord(t.ev[2 * t.used + 1], ctx->st);
+  ++t.used;
+  t.pend_bytes += bytes;
+  t.pend_flops += flops;
+}
+// after the stream has been synchronised: fold the recorded pairs into the totals
+static void kt_fold(thermo_ctx* ctx) {
+  if (!ctx->kt_on) return;
+  for (KTimer& t : ctx->kt) {
+    for (int i = 0; i < t.used; ++i) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, t.ev[2 * i], t.ev[2 * i + 1]) == cudaSuccess) t.ms += ms;
+    }
+    t.launches += t.used;
+    t.bytes += t.pend_bytes;
+    t.flops += t.pend_flops;
+    t.used = 0;
+    t.pend_bytes = t.pend_flops = 0.0;
+  }
+}
+// algorithmic DRAM bytes of the fine kernels: every array touched once
+static double fine_bytes(const Geom& g, double s_node, double s_elem) {
+  const double n = (double)(g.Nx + 1) * (g.Ny + 1) * (g.Nz + 1);
+  const double m = (double)g.Nx * g.Ny * g.Nz;
+  return n * s_node + m * s_elem + n / 8.0;  // + Dirichlet bitmask
+}
+
 template <class T>
 static cudaError_t coarse_cycle(thermo_ctx* ctx, int l) {
   cudaStream_t st = ctx->st;
@@ -587,34 +637,57 @@ static cudaError_t vcycle_fine(thermo_ctx* ctx, const S* kap, const S* r, S* b0,
   C* rc = (sizeof(C) == 8) ? (C*)l1.r64 : (C*)l1.r32;
   C* ec = (sizeof(C) == 8) ? (C*)l1.e64 : (C*)l1.e32;
   S* buf[3] = {b0, b1, b2};
+  const double s = sizeof(S), c = sizeof(C);
+  // algorithmic bytes of one sweep: r, kappa, mask, output; + iterate v, + previous iterate w
+  auto sweep_bytes = [&](bool hv, bool hw, double so) {
+    return ctx->kt_on ? fine_bytes(g, s + so + (hv ? s : 0.0) + (hw ? s : 0.0), s) : 0.0;
+  };
   cudaError_t e;
   // pre-smoothing from e_0 = 0
   int cur = 0, prev = -1;
+  kt_begin(ctx, THERMO_KT_SMOOTH);
   if ((e = fine_smooth<S, S>(g, ctx->bits, kap, r, nullptr, nullptr, buf[0], C(0), (C)sb[0], st)) != cudaSuccess)
     return e;
+  kt_end(ctx, THERMO_KT_SMOOTH, sweep_bytes(false, false, s));
   for (int k = 1; k < m; ++k) {
     const int nxt = prev >= 0 ? 3 - cur - prev : (cur + 1) % 3;
     const S* w = (sa[k] != 0.0 && prev >= 0) ? buf[prev] : nullptr;
+    kt_begin(ctx, THERMO_KT_SMOOTH);
     if ((e = fine_smooth<S, S>(g, ctx->bits, kap, r, buf[cur], w, buf[nxt], (C)sa[k], (C)sb[k], st)) != cudaSuccess)
       return e;
+    kt_end(ctx, THERMO_KT_SMOOTH, sweep_bytes(true, w != nullptr, s));
     prev = cur;
     cur = nxt;
   }
+  kt_begin(ctx, THERMO_KT_RESTRICT);
   if ((e = fine_restrict<S>(g, ctx->bits, kap, r, buf[cur], phi, rc, L1, st)) != cudaSuccess) return e;
+  kt_end(ctx, THERMO_KT_RESTRICT, ctx->kt_on ? fine_bytes(g, 2 * s + L1 * c, s) + (double)l1.cl.ncell * L1 * c : 0.0);
+  kt_begin(ctx, THERMO_KT_COARSE);
   if (sizeof(C) == 8)
     e = coarse_cycle<double>(ctx, 1);
   else
     e = coarse_cycle<float>(ctx, 1);
   if (e != cudaSuccess) return e;
+  kt_end(ctx, THERMO_KT_COARSE, 0.0);
   // prolongation (in place) and post-smoothing from the prolonged iterate
+  kt_begin(ctx, THERMO_KT_PROLONG);
   if ((e = fine_prolong<S>(g, phi, ec, buf[cur], L1, st)) != cudaSuccess) return e;
+  kt_end(ctx, THERMO_KT_PROLONG,
+         (double)ctx->nnode * (2 * s + L1 * c) + (double)l1.cl.ncell * L1 * c);  // v in/out, Phi, e_c
   prev = -1;
   for (int k = 0; k < m; ++k) {
     const S* w = (k > 0 && sa[k] != 0.0) ? buf[prev] : nullptr;
-    if (k == m - 1) return fine_smooth<S, To>(g, ctx->bits, kap, r, buf[cur], w, z, (C)sa[k], (C)sb[k], st);
+    if (k == m - 1) {
+      kt_begin(ctx, THERMO_KT_SMOOTH);
+      e = fine_smooth<S, To>(g, ctx->bits, kap, r, buf[cur], w, z, (C)sa[k], (C)sb[k], st);
+      kt_end(ctx, THERMO_KT_SMOOTH, sweep_bytes(true, w != nullptr, (double)sizeof(To)));
+      return e;
+    }
     const int nxt = prev >= 0 ? 3 - cur - prev : (cur + 1) % 3;
+    kt_begin(ctx, THERMO_KT_SMOOTH);
     if ((e = fine_smooth<S, S>(g, ctx->bits, kap, r, buf[cur], w, buf[nxt], (C)sa[k], (C)sb[k], st)) != cudaSuccess)
       return e;
+    kt_end(ctx, THERMO_KT_SMOOTH, sweep_bytes(true, w != nullptr, s));
     prev = cur;
     cur = nxt;
   }
@@ -712,6 +785,8 @@ extern "C" thermo_status thermo_solve(thermo_ctx* ctx, const double* rhs, double
   } else {
     CK(cudaMemcpyAsync(ctx->u, ctx->TD, g.nsize * sizeof(double), cudaMemcpyDeviceToDevice, st));
   }
+  // the Dirichlet rows are identities: every iterate carries u_D = b_D
+  CK(vec_copy_dir(g, ctx->bits, b, ctx->u, st));
   if (mmg && (o.guess == THERMO_GUESS_COARSE || o.guess == THERMO_GUESS_WARM_COARSE)) {
     thermo_status s = true_residual(ctx, b);
     if (s != THERMO_OK) return s;
@@ -751,10 +826,20 @@ extern "C" thermo_status thermo_solve(thermo_ctx* ctx, const double* rhs, double
     s = start_cycle();
     if (s != THERMO_OK) return s;
     const int check = o.check_every < 1 ? 1 : o.check_every;
+    // algorithmic bytes / flops of the loop's own kernels (timers only)
+    const double zs = zkind(ctx) == 0 ? 8.0 : (zkind(ctx) == 1 ? 4.0 : 2.0);
+    const double rs = rkind(ctx) == 0 ? 0.0 : (rkind(ctx) == 1 ? 4.0 : 2.0);
+    const double apply_bytes = ctx->kt_on ? fine_bytes(g, 16.0, 8.0) : 0.0;
+    const double apply_flops = 2.0 * (g.cube ? 21.0 : 27.0) * (double)ctx->nnode;
+    const double nn = (double)ctx->nnode;
     while (true) {
+      kt_begin(ctx, THERMO_KT_APPLY64);
       CK(fine_apply_f64(g, ctx->bits, ctx->k64, ctx->p, ctx->q, ctx->red.partial, ctx->red.counter, &ctx->sc->pq, st));
+      kt_end(ctx, THERMO_KT_APPLY64, apply_bytes, apply_flops);
+      kt_begin(ctx, THERMO_KT_CGVEC);
       CK(cg_update(g, ctx->u, ctx->r, ctx->p, ctx->q, flexible ? zptr(ctx) : nullptr, zkind(ctx), rptr(ctx),
                    rkind(ctx), ctx->sc, ctx->red, st));
+      kt_end(ctx, THERMO_KT_CGVEC, nn * (4 * 8.0 + 2 * 8.0 + rs + (flexible ? zs : 0.0)));
       ++it;
       if (it % check == 0 || it >= o.max_iter) {
         s = read_scalars(ctx);
@@ -785,8 +870,12 @@ extern "C" thermo_status thermo_solve(thermo_ctx* ctx, const double* rhs, double
         }
       }
       CK(apply_precond(ctx));
+      kt_begin(ctx, THERMO_KT_CGVEC);
       CK(cg_beta_dot(g, ctx->r, zptr(ctx), zkind(ctx), flexible, ctx->sc, ctx->red, st));
+      kt_end(ctx, THERMO_KT_CGVEC, nn * (8.0 + zs));
+      kt_begin(ctx, THERMO_KT_CGVEC);
       CK(cg_pupdate(g, zptr(ctx), zkind(ctx), ctx->p, ctx->sc, 0, st));
+      kt_end(ctx, THERMO_KT_CGVEC, nn * (zs + 16.0));
     }
   }
   // final true residual (FP64)
@@ -800,6 +889,7 @@ extern "C" thermo_status thermo_solve(thermo_ctx* ctx, const double* rhs, double
   inf.rel_res_true = bnorm > 0 ? sqrt(ctx->sc_h->rr) / bnorm : 0.0;
   CK(unpack_nodes(g, ctx->u, u, st));
   CK(cudaStreamSynchronize(st));
+  kt_fold(ctx);
   if (fine_stage_errors(true)) result = fail(ctx, THERMO_ECUDA, "a fine-grid kernel timed out waiting for its TMA stage");
   inf.iters = it;
   inf.restarts = restarts;
@@ -994,6 +1084,38 @@ extern "C" thermo_status thermo_oc_update(thermo_ctx* ctx, double* x, const doub
 }
 
 extern "C" long long thermo_launch_count(void) { return thermo::launch_count(); }
+
+extern "C" thermo_status thermo_kernel_timers(thermo_ctx* ctx, int enable) {
+  if (!ctx) return THERMO_EINVAL;
+  if (!enable) {
+    ctx->kt_on = false;
+    return THERMO_OK;
+  }
+  CK(cudaStreamSynchronize(ctx->st));
+  for (KTimer& t : ctx->kt) {
+    if (t.ev.empty()) {
+      t.ev.resize(2 * KTimer::CAP);
+      for (cudaEvent_t& e : t.ev) CK(cudaEventCreate(&e));
+    }
+    t.used = 0;
+    t.ms = t.bytes = t.flops = t.pend_bytes = t.pend_flops = 0.0;
+    t.launches = 0;
+  }
+  ctx->kt_on = true;
+  return THERMO_OK;
+}
+
+extern "C" thermo_status thermo_kernel_time(thermo_ctx* ctx, int kclass, double* ms, long long* launches,
+                                            double* bytes, double* flops) {
+  if (!ctx) return THERMO_EINVAL;
+  if (kclass < 0 || kclass >= THERMO_KT_COUNT) return fail(ctx, THERMO_EINVAL, "kernel class %d out of range", kclass);
+  const KTimer& t = ctx->kt[kclass];
+  if (ms) *ms = t.ms;
+  if (launches) *launches = t.launches;
+  if (bytes) *bytes = t.bytes;
+  if (flops) *flops = t.flops;
+  return THERMO_OK;
+}
 
 // Time `reps` back-to-back launches of one internal kernel on the context's
 // buffers with CUDA events on the context stream (see thermo.h).

@@ -655,6 +655,22 @@ cudaError_t vec_mask_dir(const Geom& g, const uint32_t* bits, double* v, cudaStr
   return cudaGetLastError();
 }
 
+// dst = src on the Dirichlet nodes (padded layout); other nodes untouched
+__global__ void k_copy_dir(Geom g, const uint32_t* __restrict__ bits, const double* __restrict__ src,
+                           double* __restrict__ dst) {
+  const long long n = (long long)g.nx * g.ny * g.nz;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const int x = (int)(i % g.nx);
+    const long long t = i / g.nx;
+    const int y = (int)(t % g.ny), z = (int)(t / g.ny);
+    if (is_dir(g, bits, x, y, z)) dst[nidx(g, x, y, z)] = src[nidx(g, x, y, z)];
+  }
+}
+cudaError_t vec_copy_dir(const Geom& g, const uint32_t* bits, const double* src, double* dst, cudaStream_t st) {
+  note_launch(), k_copy_dir<<<grid1((long long)g.nx * g.ny * g.nz), 256, 0, st>>>(g, bits, src, dst);
+  return cudaGetLastError();
+}
+
 // deterministic start vector of the power iteration: 1 + (i mod 7)/7 at the
 // natural node index i, zero on Dirichlet nodes
 __global__ void k_power_start(Geom g, const uint32_t* __restrict__ bits, double* __restrict__ v) {

@@ -20,6 +20,9 @@ FP64, MIXED, MIXED_BF16S = 0, 1, 2
 PC_MMG, PC_NONE, PC_JACOBI = 0, 1, 2
 GUESS_ZERO, GUESS_GIVEN, GUESS_COARSE, GUESS_WARM_COARSE = 0, 1, 2, 3
 MAX_LEVELS = 8
+KT_APPLY64, KT_SMOOTH, KT_RESTRICT, KT_PROLONG, KT_COARSE, KT_CGVEC = range(6)
+KT_NAMES = {KT_APPLY64: "apply_fp64", KT_SMOOTH: "smooth", KT_RESTRICT: "restrict", KT_PROLONG: "prolong",
+            KT_COARSE: "coarse_levels", KT_CGVEC: "cg_vector"}
 STATUS_NAMES = {0: "OK", -1: "EINVAL", -2: "ENOMEM", -3: "ECUDA", -4: "ENOTCONV",
                 -5: "EBREAKDOWN", -6: "ESINGULAR", -7: "ESTATE"}
 
@@ -27,7 +30,8 @@ EXPORTED = ["thermo_default_options", "thermo_create", "thermo_set_density", "th
             "thermo_solve", "thermo_sensitivity", "thermo_compliance", "thermo_last_error",
             "thermo_destroy", "thermo_apply", "thermo_vcycle", "thermo_load_vector",
             "thermo_hierarchy", "thermo_export_level", "thermo_filter", "thermo_oc_update",
-            "thermo_launch_count", "thermo_bench_kernel", "thermo_apply_dot"]
+            "thermo_launch_count", "thermo_bench_kernel", "thermo_apply_dot",
+          "thermo_kernel_timers", "thermo_kernel_time"]
 
 
 class thermo_options(C.Structure):
@@ -88,6 +92,8 @@ def lib():
         L.thermo_launch_count.restype = C.c_longlong
         L.thermo_bench_kernel.argtypes = [vp, i, i, dp, dp]
         L.thermo_apply_dot.argtypes = [vp, vp, vp, dp]
+        L.thermo_kernel_timers.argtypes = [vp, i]
+        L.thermo_kernel_time.argtypes = [vp, i, dp, C.POINTER(C.c_longlong), dp, dp]
         for n in EXPORTED:
             if n not in ("thermo_last_error", "thermo_destroy", "thermo_launch_count"):
                 getattr(L, n).restype = C.c_int
@@ -226,6 +232,17 @@ class Solver:
         d = C.c_double()
         self._check(lib().thermo_apply_dot(self.ctx, _ptr(p), _ptr(q), C.byref(d)))
         return q, d.value
+
+    def kernel_timers(self, enable=True):
+        """Start (zeroing the totals) or stop the per-kernel-class event timers of solve()."""
+        self._check(lib().thermo_kernel_timers(self.ctx, 1 if enable else 0))
+
+    def kernel_time(self, kclass):
+        """(ms, launches, bytes, flops) summed over the timed launches of one class."""
+        ms, b, f = C.c_double(), C.c_double(), C.c_double()
+        n = C.c_longlong()
+        self._check(lib().thermo_kernel_time(self.ctx, int(kclass), C.byref(ms), C.byref(n), C.byref(b), C.byref(f)))
+        return ms.value, n.value, b.value, f.value
 
     def vcycle(self, r):
         r = _dev(r, torch.float64)

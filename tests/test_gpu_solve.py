@@ -17,6 +17,7 @@ import torch
 
 from helpers import gpu_solver, oracle_problem, relerr, small_problem
 from oracle import fem, krylov, mmg
+import workloads as W
 
 pytestmark = pytest.mark.gpu
 
@@ -129,6 +130,24 @@ def test_guess_modes_and_given_rhs(smooth32):
     assert relerr(u3.cpu().numpy(), ud) < 1e-7
     s.close()
     s2.close()
+
+
+def test_given_rhs_with_nonzero_dirichlet_entries(smooth32):
+    """A caller's right-hand side is solved with the eliminated operator
+    A = P_F A_N P_F + P_D (Sec. 2.1 boundary data): u_D = rhs_D exactly, the
+    free part from A_FF u_F = rhs_F, whatever the Dirichlet values of the
+    context were."""
+    pr, P, ud = smooth32
+    rhs = P["f"] + np.where(P["mask"], 0.5 + W.uniform01(5, P["f"].size), 0.0)
+    ref = spla.spsolve(P["A"].tocsc(), rhs)
+    for prec in (0, 1):
+        s = gpu_solver(pr, prec=prec)
+        s.setup_precond()
+        u, info = s.solve(rhs=torch.as_tensor(rhs), tol=1e-11)
+        u = u.cpu().numpy()
+        assert np.array_equal(u[P["mask"]], rhs[P["mask"]])
+        assert relerr(u, ref) < 1e-8, (prec, info)
+        s.close()
 
 
 def test_compliance_and_sensitivity_match_oracle(smooth32):
