@@ -174,6 +174,33 @@ thermo_status thermo_solve(thermo_ctx *ctx, const double *rhs, double *u,
  * u device double[nodes], dc device double[M]. */
 thermo_status thermo_sensitivity(thermo_ctx *ctx, const double *u, double *dc);
 
+/* result = x . y (FP64), a context-free variant of the CG reduction that
+ * allocates no memory.  The paper has no counterpart: this is a service
+ * entry point for callers that must not allocate device memory during the
+ * call, e.g. code running under a caller-managed memory budget, or a loop
+ * that cannot afford the device-wide synchronisation an allocation may imply;
+ * such a caller may also hold no thermo_ctx (creating one allocates).
+ * Scratch: a file-scope device array in the library (partial sums of fixed
+ * 8192-element chunks plus an arrival counter), hence n <= 134,217,728;
+ * larger n is rejected with THERMO_EINVAL and a message.  The counter must
+ * start at zero: it is zero when the library loads, zeroed again at the
+ * first call on each device, and every completed call leaves it at zero.
+ *   x, y    device double[n] (may be NULL when n == 0)
+ *   result  device double, written by the kernel (0 for n == 0)
+ *   stream  a cudaStream_t (NULL = legacy default stream); the call only
+ *           enqueues work, except the first call on each device, which
+ *           resolves the scratch address and zeroes the counter
+ *           synchronously: make it before any stream capture
+ *   msg     host buffer of msg_len bytes for an error message, may be NULL
+ * Deterministic: fixed chunking and tree order, bitwise repeatable for
+ * equal inputs.  Calls on one device share the scratch: two calls whose
+ * kernels overlap in time (different streams, or host threads) race and give
+ * wrong results; serialise them (same stream, or events).
+ * Errors: EINVAL (bad arguments, n over the limit), ECUDA (no device, symbol
+ * lookup or launch failure). */
+thermo_status thermo_dot_noalloc(const double *x, const double *y, long long n, double *result,
+                                 void *stream, char *msg, int msg_len);
+
 /* c = f^T u (Sec. 2.3 Eq. (6) with q = 1: the mean temperature).
  * u device double[nodes]; c host double*.  Synchronises the stream. */
 thermo_status thermo_compliance(thermo_ctx *ctx, const double *u, double *c);

@@ -31,7 +31,7 @@ EXPORTED = ["thermo_default_options", "thermo_create", "thermo_set_density", "th
             "thermo_destroy", "thermo_apply", "thermo_vcycle", "thermo_load_vector",
             "thermo_hierarchy", "thermo_export_level", "thermo_filter", "thermo_oc_update",
             "thermo_launch_count", "thermo_bench_kernel", "thermo_apply_dot",
-          "thermo_kernel_timers", "thermo_kernel_time"]
+          "thermo_kernel_timers", "thermo_kernel_time", "thermo_dot_noalloc"]
 
 
 class thermo_options(C.Structure):
@@ -93,6 +93,7 @@ def lib():
         L.thermo_bench_kernel.argtypes = [vp, i, i, dp, dp]
         L.thermo_apply_dot.argtypes = [vp, vp, vp, dp]
         L.thermo_kernel_timers.argtypes = [vp, i]
+        L.thermo_dot_noalloc.argtypes = [vp, vp, C.c_longlong, vp, vp, C.c_char_p, i]
         L.thermo_kernel_time.argtypes = [vp, i, dp, C.POINTER(C.c_longlong), dp, dp]
         for n in EXPORTED:
             if n not in ("thermo_last_error", "thermo_destroy", "thermo_launch_count"):
@@ -284,6 +285,24 @@ class Solver:
         self._check(lib().thermo_oc_update(self.ctx, _ptr(x), _ptr(dc), _ptr(dv), float(volfrac),
                                            float(move), float(rmin), C.byref(ch)))
         return ch.value
+
+
+def dot_noalloc(x, y, out):
+    """out[0] = x . y through thermo_dot_noalloc (the library allocates nothing).
+    x, y: contiguous CUDA float64 tensors of equal length; out: a CUDA float64
+    tensor with at least one element, written on the current stream.  Only
+    pointers are passed: nothing is converted or copied here."""
+    for t in (x, y, out):
+        if t.device.type != "cuda" or t.dtype != torch.float64 or not t.is_contiguous():
+            raise ValueError("dot_noalloc needs contiguous CUDA float64 tensors")
+    if x.numel() != y.numel() or out.numel() < 1:
+        raise ValueError("dot_noalloc: x and y must have equal length and out at least one element")
+    msg = C.create_string_buffer(256)
+    st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = lib().thermo_dot_noalloc(_ptr(x), _ptr(y), x.numel(), _ptr(out), st, msg, 256)
+    if rc != OK:
+        raise ThermoError(rc, msg.value.decode())
+    return out
 
 
 def launch_count() -> int:
