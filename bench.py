@@ -254,7 +254,7 @@ def main():
             ts = time.perf_counter() - t0
             u, info = sv.solve(tol=args.tol)
             ks = {}
-            for k in range(11):
+            for k in range(13):
                 try:
                     ms, by = sv.bench_kernel(k, 10)
                     ks[k] = (round(ms, 4), round(by / (ms * 1e-3) / 1e9, 1) if by else None)

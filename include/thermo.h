@@ -100,6 +100,11 @@ typedef struct {
   int cheb_degree;                  /* Chebyshev: operator applications per smoothing (>= 1) */
   double cheb_ratio;                /* Chebyshev interval [lmax/ratio, 1.1 lmax] of D^-1 A */
   int power_iters;                  /* power iterations estimating lmax(D^-1 A) in set-up */
+  int outer_apply;                  /* operator of the outer CG loop: 0 auto (float-float for the
+                                       mixed forms when the grid allows it: cubic elements,
+                                       Nx a multiple of 64), 1 FP64 arithmetic, 2 float-float
+                                       (FP64-accurate sums of two floats on the FP32 pipes;
+                                       falls back to 1 where the grid does not allow it) */
 } thermo_options;
 
 typedef struct {
@@ -219,10 +224,12 @@ void thermo_destroy(thermo_ctx *ctx);
  * THERMO_MIXED_BF16S (BF16 data, FP32 math).  u, y: device double[nodes]. */
 thermo_status thermo_apply(thermo_ctx *ctx, int precision, const double *u, double *y);
 
-/* q = A p and pq = p^T A p with the fused FP64 kernel of the CG loop (the
- * operator of Sec. 2.2 Eq. (5) and the CG reduction of Sec. 4).  p, q device
- * double[nodes]; p must vanish on Gamma_D (as CG directions do); pq host.
- * Deterministic (fixed reduction order).  Synchronises the stream. */
+/* q = A p and pq = p^T A p with the fused kernel of the outer CG loop (the
+ * operator of Sec. 2.2 Eq. (5) and the CG reduction of Sec. 4): FP64
+ * arithmetic or the FP64-accurate float-float kernel, as opt.outer_apply
+ * selects.  p, q device double[nodes]; p must vanish on Gamma_D (as CG
+ * directions do); pq host.  Deterministic (fixed reduction order).
+ * Synchronises the stream. */
 thermo_status thermo_apply_dot(thermo_ctx *ctx, const double *p, double *q, double *pq);
 
 /* z = B r: one MMG V-cycle (Algorithm 1) in the context's precision.
@@ -274,11 +281,14 @@ long long thermo_launch_count(void);
 
 /* Benchmark one internal kernel: `reps` back-to-back launches on the
  * context's own buffers, timed with CUDA events on the context stream.
- *   which: 0 FP64 apply (+ fused p.Ap), 1 FP32 apply, 2 BF16 apply,
+ *   which: 0 the outer CG loop's apply (+ fused p.Ap; float-float or FP64
+ *          per opt.outer_apply), 1 FP32 apply, 2 BF16 apply,
  *          3 FP32 fine smoother sweep, 4 FP32 fused residual + restriction,
- *          5 FP32 fused prolongation + sweep, 6 level-1 block-sparse apply,
+ *          5 FP32 prolongation, 6 level-1 block-sparse apply,
  *          7 FP64 CG update, 8 one mixed V-cycle, 9 one FP64 V-cycle,
- *          10 FP64 fine smoother sweep
+ *          10 FP64 fine smoother sweep, 11 FP64-arithmetic apply + p.Ap,
+ *          12 float-float apply + p.Ap (EINVAL-like CUDA error where the
+ *          grid does not allow it)
  *   ms_per_launch (host): average duration; bytes_per_launch (host, may be
  *   NULL): algorithmic DRAM bytes of one launch (0 for whole cycles).
  * Kernels 4-6, 8, 9 need setup_precond; 2 needs a MIXED_BF16S context and 9

@@ -40,7 +40,7 @@ cudaError_t unpack_nodes(const Geom& g, const double* pad, double* nat, cudaStre
 cudaError_t mask_to_bits(const Geom& g, const uint8_t* nat, uint32_t* bits, cudaStream_t st);
 cudaError_t count_mask(const Geom& g, const uint8_t* nat, long long n, int* out, cudaStream_t st);
 cudaError_t simp_kappa(const Geom& g, const double* x, double p, double kmin, double kmax, double* k64,
-                       float* k32, bf16* k16, cudaStream_t st);
+                       float* k32, bf16* k16, float* klo, cudaStream_t st);
 cudaError_t load_vector(const Geom& g, const double* q, double* f, cudaStream_t st);
 cudaError_t dirichlet_rhs(const Geom& g, const uint32_t* bits, const double* k64, const double* f,
                           const double* TDpad, double* b, cudaStream_t st);
@@ -60,6 +60,11 @@ cudaError_t cg_pupdate(const Geom& g, const void* z, int z_kind, double* p, cons
                        cudaStream_t st);
 cudaError_t vec_to_f64(const Geom& g, const void* src, int kind, double* dst, cudaStream_t st);
 cudaError_t fine_prolong_add(const Geom& g, const double* phi, int L1, const double* ec, double* u, cudaStream_t st);
+// float-float FP64-accurate fine apply (+ fused p.q when dot != NULL); see fine_ds.cu
+bool fine_ds_supported(const Geom& g);
+unsigned fine_ds_num_ctas(const Geom& g);
+cudaError_t fine_apply_ds(const Geom& g, const uint32_t* mask, const float* khi, const float* klo, const double* u,
+                          double* y, double* partial, unsigned* counter, double* dot, cudaStream_t st);
 cudaError_t vec_mask_dir(const Geom& g, const uint32_t* bits, double* v, cudaStream_t st);
 cudaError_t vec_copy_dir(const Geom& g, const uint32_t* bits, const double* src, double* dst, cudaStream_t st);
 cudaError_t power_start(const Geom& g, const uint32_t* bits, double* v, cudaStream_t st);

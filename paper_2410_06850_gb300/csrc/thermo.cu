@@ -70,6 +70,7 @@ struct thermo_ctx {
   double* k64 = nullptr;
   float* k32 = nullptr;
   bf16* k16 = nullptr;
+  float* klo = nullptr;  // kappa - (double)k32: with k32 a float-float copy of k64
   double* xd = nullptr;     // design copy (natural)
   double *f = nullptr, *blift = nullptr, *TD = nullptr, *zero64 = nullptr;
   double *u = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *bv = nullptr, *tmp = nullptr, *z64 = nullptr;
@@ -172,6 +173,7 @@ extern "C" thermo_status thermo_default_options(const int grid[3], thermo_option
   opt->cheb_degree = 4;
   opt->cheb_ratio = 30.0;
   opt->power_iters = 15;
+  opt->outer_apply = 0;
   return THERMO_OK;
 }
 
@@ -206,6 +208,7 @@ extern "C" thermo_status thermo_create(const int grid[3], const double h[3], con
   if (grid[0] % b || grid[1] % b || grid[2] % b) return fail(ctx, THERMO_EINVAL, "grid must be a multiple of block");
   if (opt.nu_fine < 1 || opt.nu_coarse < 1 || opt.nu_fine > 64) return fail(ctx, THERMO_EINVAL, "smoothing sweeps must be in [1, 64]");
   if (opt.smoother != 0 && opt.smoother != 1) return fail(ctx, THERMO_EINVAL, "smoother must be 0 (Jacobi) or 1 (Chebyshev)");
+  if (opt.outer_apply < 0 || opt.outer_apply > 2) return fail(nullptr, THERMO_EINVAL, "outer_apply must be 0, 1 or 2");
   if (opt.smoother == 1 && (opt.cheb_degree < 1 || opt.cheb_degree > 64 || !(opt.cheb_ratio > 1.0) || opt.power_iters < 1))
     return fail(ctx, THERMO_EINVAL, "Chebyshev needs 1 <= degree <= 64, ratio > 1, power_iters >= 1");
   if (opt.nvec[0] < 1 || opt.nvec[0] > 6) return fail(ctx, THERMO_EINVAL, "nvec[0] must be in 1..6");
@@ -308,6 +311,7 @@ extern "C" thermo_status thermo_create(const int grid[3], const double h[3], con
   CK(dalloc(ctx, &ctx->k64, es));
   CK(dalloc(ctx, &ctx->k32, es));
   CK(dalloc(ctx, &ctx->k16, es));
+  CK(dalloc(ctx, &ctx->klo, es));
   CK(dalloc(ctx, &ctx->xd, ctx->nelem));
   for (double** pp : {&ctx->f, &ctx->blift, &ctx->TD, &ctx->zero64, &ctx->u, &ctx->r, &ctx->p, &ctx->q, &ctx->bv,
                       &ctx->tmp})
@@ -406,7 +410,7 @@ extern "C" thermo_status thermo_set_density(thermo_ctx* ctx, const double* x, do
   if (!(p >= 1.0) || !(kmin > 0.0) || !(kmax >= kmin) || !std::isfinite(kmax))
     return fail(ctx, THERMO_EINVAL, "need p >= 1 and 0 < kmin <= kmax");
   CK(cudaMemcpyAsync(ctx->xd, x, ctx->nelem * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
-  CK(simp_kappa(ctx->g, ctx->xd, p, kmin, kmax, ctx->k64, ctx->k32, ctx->k16, ctx->st));
+  CK(simp_kappa(ctx->g, ctx->xd, p, kmin, kmax, ctx->k64, ctx->k32, ctx->k16, ctx->klo, ctx->st));
   // lifted right-hand side b = f - A_FD T_D (b_D = T_D)
   CK(dirichlet_rhs(ctx->g, ctx->bits, ctx->k64, ctx->f, ctx->TD, ctx->blift, ctx->st));
   ctx->sp = p;
@@ -553,6 +557,21 @@ template <>
 const double* lvP<double>(Lev& l) { return l.Psi64; }
 template <>
 const float* lvP<float>(Lev& l) { return l.Psi32; }
+
+// operator of the outer CG loop: float-float (FP64-accurate on the FP32 pipes)
+// or FP64 arithmetic, per opt.outer_apply
+static bool use_ds(const thermo_ctx* ctx) {
+  if (!fine_ds_supported(ctx->g)) return false;
+  if (ctx->opt.outer_apply == 2) return true;
+  if (ctx->opt.outer_apply == 1) return false;
+  return ctx->opt.prec != THERMO_FP64;
+}
+static cudaError_t outer_apply_dot(thermo_ctx* ctx, const double* p, double* q, double* dot) {
+  const Geom& g = ctx->g;
+  if (use_ds(ctx))
+    return fine_apply_ds(g, ctx->bits, ctx->k32, ctx->klo, p, q, ctx->red.partial, ctx->red.counter, dot, ctx->st);
+  return fine_apply_f64(g, ctx->bits, ctx->k64, p, q, ctx->red.partial, ctx->red.counter, dot, ctx->st);
+}
 
 // ---- kernel-class timers: begin/end bracket one launch on the context stream
 static inline void kt_begin(thermo_ctx* ctx, int c) {
@@ -834,7 +853,7 @@ extern "C" thermo_status thermo_solve(thermo_ctx* ctx, const double* rhs, double
     const double nn = (double)ctx->nnode;
     while (true) {
       kt_begin(ctx, THERMO_KT_APPLY64);
-      CK(fine_apply_f64(g, ctx->bits, ctx->k64, ctx->p, ctx->q, ctx->red.partial, ctx->red.counter, &ctx->sc->pq, st));
+      CK(outer_apply_dot(ctx, ctx->p, ctx->q, &ctx->sc->pq));
       kt_end(ctx, THERMO_KT_APPLY64, apply_bytes, apply_flops);
       kt_begin(ctx, THERMO_KT_CGVEC);
       CK(cg_update(g, ctx->u, ctx->r, ctx->p, ctx->q, flexible ? zptr(ctx) : nullptr, zkind(ctx), rptr(ctx),
@@ -952,7 +971,7 @@ extern "C" thermo_status thermo_apply_dot(thermo_ctx* ctx, const double* p, doub
   const Geom& g = ctx->g;
   cudaStream_t st = ctx->st;
   CK(pack_nodes(g, p, ctx->tmp, st));
-  CK(fine_apply_f64(g, ctx->bits, ctx->k64, ctx->tmp, ctx->q, ctx->red.partial, ctx->red.counter, ctx->dscal, st));
+  CK(outer_apply_dot(ctx, ctx->tmp, ctx->q, ctx->dscal));
   CK(unpack_nodes(g, ctx->q, q, st));
   CK(cudaMemcpyAsync(ctx->dscal_h, ctx->dscal, sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
@@ -1134,10 +1153,17 @@ extern "C" thermo_status thermo_bench_kernel(thermo_ctx* ctx, int which, int rep
   double bytes = 0.0;
   auto run = [&]() -> cudaError_t {
     switch (which) {
-      case 0:
+      case 0:  // the outer CG loop's operator (float-float or FP64, per outer_apply)
+        bytes = n * 16 + M * 8;
+        return outer_apply_dot(ctx, ctx->p, ctx->q, &ctx->sc->pq);
+      case 11:  // FP64-arithmetic apply + dot
         bytes = n * 16 + M * 8;
         return fine_apply_f64(g, ctx->bits, ctx->k64, ctx->p, ctx->q, ctx->red.partial, ctx->red.counter,
                               &ctx->sc->pq, st);
+      case 12:  // float-float apply + dot
+        bytes = n * 16 + M * 8;
+        return fine_apply_ds(g, ctx->bits, ctx->k32, ctx->klo, ctx->p, ctx->q, ctx->red.partial, ctx->red.counter,
+                             &ctx->sc->pq, st);
       case 1:
         bytes = n * 8 + M * 4;
         return fine_apply_lp<float>(g, ctx->bits, ctx->k32, ctx->ea32, ctx->eb32, st);

@@ -161,9 +161,12 @@ cudaError_t count_mask(const Geom& g, const uint8_t* nat, long long n, int* out,
   return cudaGetLastError();
 }
 
-// Sec. 2.1 Eq. (1): kappa_e = kmin + x_e^p (kmax - kmin), kept in three precisions
+// Sec. 2.1 Eq. (1): kappa_e = kmin + x_e^p (kmax - kmin), kept in three precisions;
+// klo (optional) is the float remainder kappa - (double)k32, so that k32 + klo is a
+// float-float copy of the FP64 value (used by the float-float fine apply)
 __global__ void k_simp(Geom g, const double* __restrict__ x, double p, double kmin, double kmax,
-                       double* __restrict__ k64, float* __restrict__ k32, bf16* __restrict__ k16) {
+                       double* __restrict__ k64, float* __restrict__ k32, bf16* __restrict__ k16,
+                       float* __restrict__ klo) {
   const long long M = (long long)g.Nx * g.Ny * g.Nz;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < M; e += (long long)gridDim.x * blockDim.x) {
     const int ex = (int)(e % g.Nx);
@@ -171,14 +174,16 @@ __global__ void k_simp(Geom g, const double* __restrict__ x, double p, double km
     const int ey = (int)(t % g.Ny), ez = (int)(t / g.Ny);
     const double k = kmin + pow(x[e], p) * (kmax - kmin);
     const long long i = eidx(g, ex, ey, ez);
+    const float kh = (float)k;
     k64[i] = k;
-    k32[i] = (float)k;
-    k16[i] = __float2bfloat16_rn((float)k);
+    k32[i] = kh;
+    k16[i] = __float2bfloat16_rn(kh);
+    if (klo) klo[i] = (float)(k - (double)kh);
   }
 }
 cudaError_t simp_kappa(const Geom& g, const double* x, double p, double kmin, double kmax, double* k64, float* k32,
-                       bf16* k16, cudaStream_t st) {
-  note_launch(), k_simp<<<grid1((long long)g.Nx * g.Ny * g.Nz), 256, 0, st>>>(g, x, p, kmin, kmax, k64, k32, k16);
+                       bf16* k16, float* klo, cudaStream_t st) {
+  note_launch(), k_simp<<<grid1((long long)g.Nx * g.Ny * g.Nz), 256, 0, st>>>(g, x, p, kmin, kmax, k64, k32, k16, klo);
   return cudaGetLastError();
 }
 

@@ -186,3 +186,27 @@ def test_nonzero_dirichlet_values_layered_exact():
     lower = exact < 2 * t  # the conductive half carries values of order t = 1e-6
     np.testing.assert_allclose(uu[lower], exact[lower], rtol=1e-4, atol=1e-13)
     s.close()
+
+
+def test_float_float_outer_operator_solve():
+    """The mixed solve with the float-float outer operator (outer_apply = 2)
+    at contrast 1e6 meets the tolerance on the oracle's assembled operator
+    (true residual ||b - A u|| <= 1.5 tol ||b_F||, Dirichlet values exact),
+    agrees with the FP64-arithmetic operator's solution to 1e-8, and takes
+    its iteration count (+-2).  (A direct solve is too slow at 64^3.)"""
+    pr = small_problem(64, kind="chan", kmin=1e-6)
+    P = oracle_problem(pr)
+    b, A, free = P["b"], P["A"], ~P["mask"]
+    bF = np.linalg.norm(b[free])
+    res, us = {}, {}
+    for oa in (1, 2):
+        s = gpu_solver(pr, prec=1, outer_apply=oa)
+        s.setup_precond()
+        u, info = s.solve(tol=1e-10)
+        u = u.cpu().numpy()
+        assert np.linalg.norm(b - A @ u) <= 1.5e-10 * bF, (oa, info)
+        assert np.array_equal(u[P["mask"]], b[P["mask"]])
+        res[oa], us[oa] = info["iters"], u
+        s.close()
+    assert relerr(us[2], us[1]) < 1e-8
+    assert abs(res[2] - res[1]) <= 2, res
