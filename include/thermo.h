@@ -105,6 +105,10 @@ typedef struct {
                                        Nx a multiple of 64), 1 FP64 arithmetic, 2 float-float
                                        (FP64-accurate sums of two floats on the FP32 pipes;
                                        falls back to 1 where the grid does not allow it) */
+  int nu_growth;                    /* coarse sweeps on level l: nu_coarse * nu_growth^(l-1),
+                                       capped at 64 (1: the same on every coarse level) */
+  int w_from;                       /* 0: V-cycle; k > 0: levels >= k make two coarse
+                                       corrections per visit (W-cycle below level k) */
 } thermo_options;
 
 typedef struct {

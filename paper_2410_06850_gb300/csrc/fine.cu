@@ -576,6 +576,7 @@ cudaError_t fine_apply_f64(const Geom& g, const uint32_t* mask, const double* ka
 template <class S>
 cudaError_t fine_apply_lp(const Geom& g, const uint32_t* mask, const S* kap, const S* u, S* y, cudaStream_t st,
                           bool mask_input) {
+  if (!mask_input && fine2_supported(g)) return fine2_apply<S>(g, mask, kap, u, y, st);
   auto a = fargs<S, S>(g, mask, kap);
   a.v = u;
   a.out = y;
@@ -599,10 +600,23 @@ template cudaError_t fine_apply_lp<bf16>(const Geom&, const uint32_t*, const bf1
     default: return cudaErrorInvalidValue;                       \
   }
 
+// FP32/BF16 sweeps on grids the two-nodes-per-lane engine covers (fine2.cu)
+template <class S, class To>
+static cudaError_t fine2_smooth_dispatch(const Geom& g, const uint32_t* mask, const S* kap, const S* r, const S* e,
+                                         const S* w, To* out, float cA, float cB, cudaStream_t st) {
+  if constexpr (sizeof(S) == 8) {
+    return cudaErrorInvalidValue;
+  } else {
+    return fine2_smooth<S, To>(g, mask, kap, r, e, w, out, cA, cB, st);
+  }
+}
+
 // One sweep e' = e + cA (e - w) + cB D^-1 (r - A e); e == nullptr: e' = cB D^-1 r.
 template <class S, class To>
 cudaError_t fine_smooth(const Geom& g, const uint32_t* mask, const S* kap, const S* r, const S* e, const S* w,
                         To* out, typename Cv<S>::C cA, typename Cv<S>::C cB, cudaStream_t st) {
+  if (sizeof(S) < 8 && fine2_supported(g))
+    return fine2_smooth_dispatch(g, mask, kap, r, e, w, out, (float)cA, (float)cB, st);
   auto a = fargs<S, To>(g, mask, kap);
   a.r = r;
   a.v = e;

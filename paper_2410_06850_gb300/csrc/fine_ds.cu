@@ -23,10 +23,14 @@
 // over ZC planes; one elected thread stages each plane of p (FP64), of kappa
 // (hi and lo floats) and of the Dirichlet bits with TMA tensor copies into an
 // mbarrier ring; all threads split the landed FP64 plane into hi/lo float
-// planes (integer arithmetic, no FP64 pipe) before the plane is used; a ninth
-// warp evaluates the closing column and row of the last tiles.  FP64 work per
-// node: one add to assemble q and one fused multiply-add for p.q.
+// planes (integer arithmetic, no FP64 pipe) before the plane is used.  The
+// closing column (x = Nx) and row (y = Ny), 0.8% of the nodes at 256^3, are
+// evaluated first by a small grid-stride kernel (ds_edge) whose block partials
+// of p.q open the reduction buffer.  FP64 work per node: one add to assemble
+// q and one fused multiply-add for p.q.
 #include <cuda.h>
+
+#include <algorithm>
 
 #include "common.cuh"
 #include "kernels.h"
@@ -37,7 +41,7 @@ namespace thermo {
 namespace {
 
 constexpr int DTY = 8;               // rows per tile (max), one warp each
-constexpr int DNT = 32 * (DTY + 1);  // + the closing column / row warp
+constexpr int DNT = 32 * DTY;        // the closing column / row go to ds_edge
 constexpr int DTX = 64;              // nodes per tile row (two per lane)
 constexpr int DSX = 4;               // staged rows start at x0 - DSX (16-byte aligned)
 constexpr int DW = 72;               // staged row width (x0 - 4 .. x0 + 67)
@@ -58,10 +62,11 @@ struct DsArgs {
   double* out;      // q = A p (padded)
   const uint32_t* mask;
   float c3h, c3l;   // -h/12 as a float-float pair
-  double* partial;  // dot partials, one per CTA
+  double* partial;  // dot partials: [0, nedge) from ds_edge, then one per CTA
   unsigned* counter;
   double* dot;
   int* err;
+  int nedge;        // partials written by ds_edge before this kernel
 };
 struct alignas(64) DsMaps {
   CUtensorMap v, kh, kl, m;
@@ -140,8 +145,95 @@ __device__ __forceinline__ double f2d(float f) {
   return __longlong_as_double((long long)d);
 }
 
+// ---- scalar float-float helpers (edge kernel)
+struct D1 {
+  float h, l;
+};
+__device__ __forceinline__ D1 d1_split(double x) {
+  D1 r;
+  split_d(x, r.h, r.l);
+  return r;
+}
+__device__ __forceinline__ D1 d1_sub(const D1& a, const D1& b) {
+  const float s = __fsub_rn(a.h, b.h);
+  const float bb = __fsub_rn(s, a.h);
+  const float e = __fsub_rn(__fsub_rn(a.h, __fsub_rn(s, bb)), __fadd_rn(b.h, bb));
+  return D1{s, __fadd_rn(e, __fsub_rn(a.l, b.l))};
+}
+__device__ __forceinline__ void d1_fma_acc(D1& acc, const D1& w, const D1& d) {
+  const float ph = __fmul_rn(w.h, d.h);
+  const float pe = __fmaf_rn(w.h, d.h, -ph);
+  const float cr = __fmaf_rn(w.h, d.l, __fmul_rn(w.l, d.h));
+  const float s = __fadd_rn(acc.h, ph);
+  const float bb = __fsub_rn(s, acc.h);
+  const float e = __fadd_rn(__fsub_rn(acc.h, __fsub_rn(s, bb)), __fsub_rn(ph, bb));
+  acc.h = s;
+  acc.l = __fadd_rn(acc.l, __fadd_rn(e, __fadd_rn(pe, cr)));
+}
+
+// closing column x = Nx (all y, z) and closing row y = Ny (x < Nx, all z):
+// per node, the sum over its 8 elements of kappa_e times the differences to
+// the element's three face-diagonal nodes and its body-diagonal node (the
+// same operator as the tile kernel, grouped by element); the zero padding of
+// the node and element arrays supplies every off-domain neighbour.
 template <bool DOT>
-__global__ void __launch_bounds__(DNT, 1) ds_apply(const __grid_constant__ DsArgs a, const __grid_constant__ DsMaps tm) {
+__global__ void __launch_bounds__(256) ds_edge(const Geom g, const double* __restrict__ v, const float* __restrict__ khi,
+                                               const float* __restrict__ klo, const uint32_t* __restrict__ mask,
+                                               double* __restrict__ out, float c3h, float c3l,
+                                               double* __restrict__ partial) {
+  __shared__ double sh[256];
+  const long long ncol = (long long)(g.Ny + 1) * (g.Nz + 1);  // x = Nx
+  const long long nrow = (long long)g.Nx * (g.Nz + 1);        // y = Ny, x < Nx
+  double dacc = 0.0;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < ncol + nrow;
+       i += (long long)gridDim.x * blockDim.x) {
+    int x, y, z;
+    if (i < ncol) {
+      x = g.Nx;
+      y = (int)(i % (g.Ny + 1));
+      z = (int)(i / (g.Ny + 1));
+    } else {
+      const long long j = i - ncol;
+      x = (int)(j % g.Nx);
+      y = g.Ny;
+      z = (int)(j / g.Nx);
+    }
+    const double pd = v[nidx(g, x, y, z)];
+    const D1 pc = d1_split(pd);
+    D1 acc{0.f, 0.f};
+#pragma unroll
+    for (int sz = -1; sz <= 1; sz += 2)
+#pragma unroll
+      for (int sy = -1; sy <= 1; sy += 2)
+#pragma unroll
+        for (int sx = -1; sx <= 1; sx += 2) {
+          const long long e = eidx(g, sx < 0 ? x - 1 : x, sy < 0 ? y - 1 : y, sz < 0 ? z - 1 : z);
+          const D1 k{khi[e], klo[e]};
+          d1_fma_acc(acc, k, d1_sub(d1_split(v[nidx(g, x + sx, y + sy, z)]), pc));
+          d1_fma_acc(acc, k, d1_sub(d1_split(v[nidx(g, x + sx, y, z + sz)]), pc));
+          d1_fma_acc(acc, k, d1_sub(d1_split(v[nidx(g, x, y + sy, z + sz)]), pc));
+          d1_fma_acc(acc, k, d1_sub(d1_split(v[nidx(g, x + sx, y + sy, z + sz)]), pc));
+        }
+    const float yh = __fmul_rn(acc.h, c3h);
+    const float ye = __fmaf_rn(acc.h, c3h, -yh);
+    const float yl = __fadd_rn(ye, __fmaf_rn(acc.h, c3l, __fmul_rn(acc.l, c3h)));
+    const double q = is_dir(g, mask, x, y, z) ? 0.0 : f2d(yh) + f2d(yl);
+    out[nidx(g, x, y, z)] = q;
+    if (DOT) dacc = fma(pd, q, dacc);
+  }
+  if (DOT) {
+    sh[threadIdx.x] = dacc;
+    __syncthreads();
+    for (int s2 = 128; s2 > 0; s2 >>= 1) {
+      if ((int)threadIdx.x < s2) sh[threadIdx.x] += sh[threadIdx.x + s2];
+      __syncthreads();
+    }
+    if (threadIdx.x == 0) partial[blockIdx.x] = sh[0];
+  }
+}
+
+template <bool DOT>
+__global__ void __launch_bounds__(DNT, 2) ds_apply(const __grid_constant__ DsArgs a, const __grid_constant__ DsMaps tm) {
   const Geom& g = a.g;
   extern __shared__ __align__(128) unsigned char smem_dyn[];
   unsigned char* smem_raw = smem_dyn + ((128u - (smem_u32(smem_dyn) & 127u)) & 127u);
@@ -149,11 +241,10 @@ __global__ void __launch_bounds__(DNT, 1) ds_apply(const __grid_constant__ DsArg
   unsigned char* stages = smem_raw + 128;
   unsigned char* pairs = stages + DNS * STB;  // 3 slots x (hi plane, lo plane)
   __shared__ int stage_bad;
-  __shared__ double dsh[DTY + 1];
+  __shared__ double dsh[DTY];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int TY = g.TY;
   const int x0 = blockIdx.x * DTX, y0 = blockIdx.y * TY;
-  const bool lastx = (x0 + DTX == g.Nx), lasty = (y0 + TY == g.Ny);
   const int zs = blockIdx.z * g.ZC;
   const int ze = (zs + g.ZC == g.Nz) ? g.Nz : zs + g.ZC - 1;
   const int mx = (x0 >> 5) & ~3;
@@ -215,9 +306,8 @@ __global__ void __launch_bounds__(DNT, 1) ds_apply(const __grid_constant__ DsArg
   const float2 c3h = F2(a.c3h, a.c3h), c3l = F2(a.c3l, a.c3l);
   double dacc = 0.0;
 
-  // node pair (x0 + c, x0 + c + 1) on tile row r (0..TY) of node plane t; writes the
-  // first node only if single (closing column)
-  auto pair = [&](int t, int r, int c, bool single) {
+  // node pair (x0 + c, x0 + c + 1) on tile row r of node plane t
+  auto pair = [&](int t, int r, int c) {
     const int sc = c + DSX;  // staged column of node x0 + c
     // conductivity pairs k[a][b][s]: element plane t-1+a, element row y-1+b (staged row r+b),
     // side s = 0: elements (c-1, c), s = 1: elements (c, c+1)
@@ -282,13 +372,8 @@ __global__ void __launch_bounds__(DNT, 1) ds_apply(const __grid_constant__ DsArg
     double q1 = ((mw >> ((xx + 1) & 31)) & 1u) ? 0.0 : f2d(yh.y) + f2d(yl.y);
     const long long n = nidx(g, xx, yy, t);
     const double* pv = sV(t) + (r + 1) * DW + sc;  // FP64 p of the pair (for the dot)
-    if (single) {
-      a.out[n] = q0;
-      if (DOT) dacc = fma(pv[0], q0, dacc);
-    } else {
-      *reinterpret_cast<double2*>(a.out + n) = make_double2(q0, q1);
-      if (DOT) dacc = fma(pv[1], q1, fma(pv[0], q0, dacc));
-    }
+    *reinterpret_cast<double2*>(a.out + n) = make_double2(q0, q1);
+    if (DOT) dacc = fma(pv[1], q1, fma(pv[0], q0, dacc));
   };
 
   const int nsplit = (TY + 3) * DW;
@@ -312,12 +397,7 @@ __global__ void __launch_bounds__(DNT, 1) ds_apply(const __grid_constant__ DsArg
     }
     __syncthreads();
     if (t < zs) continue;
-    if (w < TY) {
-      pair(t, w, 2 * lane, false);
-    } else if (w == DTY) {
-      if (lastx && (lane < TY || (lasty && lane == TY))) pair(t, lane, DTX, true);  // closing column
-      if (lasty) pair(t, TY, 2 * lane, false);                                    // closing row
-    }
+    if (w < TY) pair(t, w, 2 * lane);
   }
 
   if (DOT) {
@@ -330,22 +410,23 @@ __global__ void __launch_bounds__(DNT, 1) ds_apply(const __grid_constant__ DsArg
     const unsigned bid = blockIdx.x + gridDim.x * (blockIdx.y + gridDim.y * blockIdx.z);
     if (tid == 0) {
       double s = 0.0;
-      for (int i = 0; i < DTY + 1; ++i) s += dsh[i];
-      a.partial[bid] = s;
+      for (int i = 0; i < DTY; ++i) s += dsh[i];
+      a.partial[a.nedge + bid] = s;
       __threadfence();
       last = (atomicAdd(a.counter, 1u) == nblk - 1);
     }
     __syncthreads();
     if (last) {
       __threadfence();
+      const unsigned ntot = nblk + (unsigned)a.nedge;  // the edge kernel's partials come first
       double v = 0.0;
-      for (unsigned i = tid; i < nblk; i += DNT) v += __ldcg(a.partial + i);
+      for (unsigned i = tid; i < ntot; i += DNT) v += __ldcg(a.partial + i);
       for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
       if (lane == 0) dsh[w] = v;
       __syncthreads();
       if (tid == 0) {
         double s = 0.0;
-        for (int i = 0; i < DTY + 1; ++i) s += dsh[i];
+        for (int i = 0; i < DTY; ++i) s += dsh[i];
         *a.dot = s;
         *a.counter = 0u;
       }
@@ -391,10 +472,15 @@ cudaError_t fine_apply_ds(const Geom& g, const uint32_t* mask, const float* khi,
       cudaSuccess)
     return e;
   const dim3 grid(g.Nx / DTX, g.Ny / g.TY, g.Nz / g.ZC);
+  const long long nedge_nodes = (long long)(g.Ny + 1) * (g.Nz + 1) + (long long)g.Nx * (g.Nz + 1);
+  const int eb = (int)std::min<long long>((nedge_nodes + 255) / 256, 512);
+  a.nedge = dot ? eb : 0;
   if (dot) {
+    note_launch(), ds_edge<true><<<eb, 256, 0, st>>>(g, u, khi, klo, mask, y, a.c3h, a.c3l, partial);
     cudaFuncSetAttribute(ds_apply<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
     note_launch(), ds_apply<true><<<grid, DNT, SMEM, st>>>(a, tm);
   } else {
+    note_launch(), ds_edge<false><<<eb, 256, 0, st>>>(g, u, khi, klo, mask, y, a.c3h, a.c3l, nullptr);
     cudaFuncSetAttribute(ds_apply<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
     note_launch(), ds_apply<false><<<grid, DNT, SMEM, st>>>(a, tm);
   }

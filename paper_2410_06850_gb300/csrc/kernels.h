@@ -60,6 +60,14 @@ cudaError_t cg_pupdate(const Geom& g, const void* z, int z_kind, double* p, cons
                        cudaStream_t st);
 cudaError_t vec_to_f64(const Geom& g, const void* src, int kind, double* dst, cudaStream_t st);
 cudaError_t fine_prolong_add(const Geom& g, const double* phi, int L1, const double* ec, double* u, cudaStream_t st);
+// two-nodes-per-lane FP32-compute fine sweeps / applies (fine2.cu): cubic
+// elements, Nx a multiple of 64
+bool fine2_supported(const Geom& g);
+template <class S, class To>
+cudaError_t fine2_smooth(const Geom& g, const uint32_t* mask, const S* kap, const S* r, const S* e, const S* w, To* out,
+                         float cA, float cB, cudaStream_t st);
+template <class S>
+cudaError_t fine2_apply(const Geom& g, const uint32_t* mask, const S* kap, const S* u, S* y, cudaStream_t st);
 // float-float FP64-accurate fine apply (+ fused p.q when dot != NULL); see fine_ds.cu
 bool fine_ds_supported(const Geom& g);
 unsigned fine_ds_num_ctas(const Geom& g);

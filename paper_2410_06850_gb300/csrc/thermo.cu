@@ -174,6 +174,8 @@ extern "C" thermo_status thermo_default_options(const int grid[3], thermo_option
   opt->cheb_ratio = 30.0;
   opt->power_iters = 15;
   opt->outer_apply = 0;
+  opt->nu_growth = 1;
+  opt->w_from = 0;
   return THERMO_OK;
 }
 
@@ -208,7 +210,9 @@ extern "C" thermo_status thermo_create(const int grid[3], const double h[3], con
   if (grid[0] % b || grid[1] % b || grid[2] % b) return fail(ctx, THERMO_EINVAL, "grid must be a multiple of block");
   if (opt.nu_fine < 1 || opt.nu_coarse < 1 || opt.nu_fine > 64) return fail(ctx, THERMO_EINVAL, "smoothing sweeps must be in [1, 64]");
   if (opt.smoother != 0 && opt.smoother != 1) return fail(ctx, THERMO_EINVAL, "smoother must be 0 (Jacobi) or 1 (Chebyshev)");
-  if (opt.outer_apply < 0 || opt.outer_apply > 2) return fail(nullptr, THERMO_EINVAL, "outer_apply must be 0, 1 or 2");
+  if (opt.nu_growth < 1 || opt.nu_growth > 8) return fail(ctx, THERMO_EINVAL, "nu_growth must be in 1..8");
+  if (opt.w_from < 0) return fail(ctx, THERMO_EINVAL, "w_from must be >= 0");
+  if (opt.outer_apply < 0 || opt.outer_apply > 2) return fail(ctx, THERMO_EINVAL, "outer_apply must be 0, 1 or 2");
   if (opt.smoother == 1 && (opt.cheb_degree < 1 || opt.cheb_degree > 64 || !(opt.cheb_ratio > 1.0) || opt.power_iters < 1))
     return fail(ctx, THERMO_EINVAL, "Chebyshev needs 1 <= degree <= 64, ratio > 1, power_iters >= 1");
   if (opt.nvec[0] < 1 || opt.nvec[0] > 6) return fail(ctx, THERMO_EINVAL, "nvec[0] must be in 1..6");
@@ -616,7 +620,10 @@ static cudaError_t coarse_cycle(thermo_ctx* ctx, int l) {
   Lev& lv = ctx->lev[l];
   cudaError_t e;
   if (l == ctx->nlev) return dense_gemv<T>(ctx->ncoarse, ctx->Ainv, lvr<T>(lv), lve<T>(lv), st);
-  const int nu = ctx->opt.nu_coarse;
+  // sweeps on this level: nu_coarse, multiplied by nu_growth per level below level 1
+  int nu = ctx->opt.nu_coarse;
+  for (int k = 1; k < l && nu < 64; ++k) nu *= ctx->opt.nu_growth;
+  if (nu > 64) nu = 64;
   T* E = lve<T>(lv);
   T* Tt = lvt<T>(lv);
   if ((e = coarse_smooth0<T>(lv.cl, lvD<T>(lv), lvr<T>(lv), E, st)) != cudaSuccess) return e;
@@ -625,10 +632,15 @@ static cudaError_t coarse_cycle(thermo_ctx* ctx, int l) {
     std::swap(E, Tt);
   }
   Lev& nx = ctx->lev[l + 1];
-  if ((e = coarse_residual<T>(lv.cl, lvT<T>(lv), lvr<T>(lv), E, lvs<T>(lv), st)) != cudaSuccess) return e;
-  if ((e = coarse_restrict<T>(lv.cl, nx.cl, lvP<T>(nx), lvs<T>(lv), lvr<T>(nx), st)) != cudaSuccess) return e;
-  if ((e = coarse_cycle<T>(ctx, l + 1)) != cudaSuccess) return e;
-  if ((e = coarse_prolong<T>(lv.cl, nx.cl, lvP<T>(nx), lve<T>(nx), E, st)) != cudaSuccess) return e;
+  // coarse corrections: two (W-cycle) on levels >= w_from, unless the next level is
+  // the exact coarsest solve (a second Galerkin correction would be zero)
+  const int reps = (ctx->opt.w_from > 0 && l >= ctx->opt.w_from && l + 1 < ctx->nlev) ? 2 : 1;
+  for (int c = 0; c < reps; ++c) {
+    if ((e = coarse_residual<T>(lv.cl, lvT<T>(lv), lvr<T>(lv), E, lvs<T>(lv), st)) != cudaSuccess) return e;
+    if ((e = coarse_restrict<T>(lv.cl, nx.cl, lvP<T>(nx), lvs<T>(lv), lvr<T>(nx), st)) != cudaSuccess) return e;
+    if ((e = coarse_cycle<T>(ctx, l + 1)) != cudaSuccess) return e;
+    if ((e = coarse_prolong<T>(lv.cl, nx.cl, lvP<T>(nx), lve<T>(nx), E, st)) != cudaSuccess) return e;
+  }
   for (int s = 0; s < nu; ++s) {
     if ((e = coarse_smooth<T>(lv.cl, lvT<T>(lv), lvD<T>(lv), lvr<T>(lv), E, Tt, st)) != cudaSuccess) return e;
     std::swap(E, Tt);
@@ -947,16 +959,22 @@ extern "C" thermo_status thermo_apply(thermo_ctx* ctx, int precision, const doub
   CK(pack_nodes(g, u, ctx->tmp, st));
   if (precision == THERMO_FP64) {
     CK(fine_apply_f64(g, ctx->bits, ctx->k64, ctx->tmp, ctx->q, nullptr, nullptr, nullptr, st, true));
-  } else if (precision == THERMO_MIXED) {
-    CK(vec_copy_cvt(g, ctx->tmp, ctx->ea32, 1, st));
-    CK(fine_apply_lp<float>(g, ctx->bits, ctx->k32, ctx->ea32, ctx->eb32, st, true));
-    CK(vec_to_f64(g, ctx->eb32, 1, ctx->q, st));
-  } else if (precision == THERMO_MIXED_BF16S) {
-    bf16 *a16 = ctx->ea16, *b16 = ctx->eb16;
-    if (!a16) return fail(ctx, THERMO_EINVAL, "BF16 buffers exist only for a MIXED_BF16S context");
-    CK(vec_copy_cvt(g, ctx->tmp, a16, 2, st));
-    CK(fine_apply_lp<bf16>(g, ctx->bits, ctx->k16, a16, b16, st, true));
-    CK(vec_to_f64(g, b16, 2, ctx->q, st));
+  } else if (precision == THERMO_MIXED || precision == THERMO_MIXED_BF16S) {
+    // the V-cycle's kernel: input zero on Gamma_D, rows there 0; identity rows restored below
+    CK(vec_mask_dir(g, ctx->bits, ctx->tmp, st));
+    if (precision == THERMO_MIXED) {
+      CK(vec_copy_cvt(g, ctx->tmp, ctx->ea32, 1, st));
+      CK(fine_apply_lp<float>(g, ctx->bits, ctx->k32, ctx->ea32, ctx->eb32, st, false));
+      CK(vec_to_f64(g, ctx->eb32, 1, ctx->q, st));
+    } else {
+      bf16 *a16 = ctx->ea16, *b16 = ctx->eb16;
+      if (!a16) return fail(ctx, THERMO_EINVAL, "BF16 buffers exist only for a MIXED_BF16S context");
+      CK(vec_copy_cvt(g, ctx->tmp, a16, 2, st));
+      CK(fine_apply_lp<bf16>(g, ctx->bits, ctx->k16, a16, b16, st, false));
+      CK(vec_to_f64(g, b16, 2, ctx->q, st));
+    }
+    CK(pack_nodes(g, u, ctx->tmp, st));
+    CK(vec_copy_dir(g, ctx->bits, ctx->tmp, ctx->q, st));
   } else {
     return fail(ctx, THERMO_EINVAL, "unknown precision %d", precision);
   }

@@ -40,7 +40,8 @@ class thermo_options(C.Structure):
                 ("omega", C.c_double), ("prec", C.c_int), ("pc", C.c_int), ("guess", C.c_int),
                 ("max_iter", C.c_int), ("flexible", C.c_int), ("check_every", C.c_int),
                 ("smoother", C.c_int), ("cheb_degree", C.c_int), ("cheb_ratio", C.c_double),
-                ("power_iters", C.c_int), ("outer_apply", C.c_int)]
+                ("power_iters", C.c_int), ("outer_apply", C.c_int),
+                ("nu_growth", C.c_int), ("w_from", C.c_int)]
 
 
 class thermo_solve_info(C.Structure):

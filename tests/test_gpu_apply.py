@@ -39,9 +39,15 @@ def test_apply_fp64_matches_oracle(case):
     s.close()
 
 
+LP_CASES = [dict(N=32), dict(N=64), dict(N=0, grid=(128, 64, 40), h=(1 / 128,) * 3)]
+
+
+@pytest.mark.parametrize("case", LP_CASES, ids=["32", "64", "box128x64x40"])
 @pytest.mark.parametrize("prec,tol", [(1, 2e-6), (2, 3e-2)])
-def test_apply_low_precision_normwise(prec, tol):
-    pr = small_problem(32, kind="rand", kmin=1e-3)
+def test_apply_low_precision_normwise(prec, tol, case):
+    """FP32 and BF16-storage applies (32^3: one node per lane; 64^3 and the box:
+    two nodes per lane with packed f32x2 plus the closing column/row kernel)."""
+    pr = small_problem(case["N"], kind="rand", kmin=1e-3, grid=case.get("grid"), h=case.get("h"))
     P = oracle_problem(pr)
     s = gpu_solver(pr, prec=prec)
     n = P["A"].shape[0]
@@ -51,6 +57,7 @@ def test_apply_low_precision_normwise(prec, tol):
     scale = np.abs(P["A"]).dot(np.abs(u))
     err = np.abs(y - ref) / np.maximum(scale, 1e-300)
     assert err.max() < tol, err.max()
+    assert np.array_equal(y[P["mask"]], u[P["mask"]])  # identity rows
     s.close()
 
 

@@ -54,6 +54,30 @@ def test_vcycle_fp64_matches_oracle(smooth32):
     s.close()
 
 
+@pytest.mark.parametrize("case", [dict(N=64), dict(N=0, grid=(128, 64, 40), h=(1 / 128,) * 3)],
+                         ids=["64", "box128x64x40"])
+@pytest.mark.parametrize("prec,tol", [(1, 2e-5), (2, 5e-2)])
+def test_vcycle_low_precision_matches_oracle(case, prec, tol):
+    """The FP32 V-cycle (and the BF16-storage smoother variant) against the
+    oracle's FP64 V-cycle (Algorithm 1 with the same Chebyshev smoother and
+    hierarchy) on grids where the fine sweeps run two nodes per lane."""
+    pr = small_problem(case["N"], kind="smooth", grid=case.get("grid"), h=case.get("h"))
+    P = oracle_problem(pr)
+    s = gpu_solver(pr, prec=prec)
+    s.setup_precond()
+    # the library's default hierarchy for these grids: 64^3 -> L (4, 8, 17); 128x64x40 -> (4, 17)
+    opts = (mmg.default_options(case["N"]) if case["N"] else
+            mmg.MMGOptions(block=4, nvec=(4, 17), group=(2,), smoother="chebyshev"))
+    H = mmg.MMG(P, opts)
+    assert [lv["nvec"] for lv in s.hierarchy()] == list(opts.nvec)
+    n = P["A"].shape[0]
+    r = np.random.default_rng(4).standard_normal(n)
+    r[P["mask"]] = 0.0
+    z = s.vcycle(torch.as_tensor(r)).cpu().numpy()
+    assert relerr(z, H(r)) < tol, relerr(z, H(r))
+    s.close()
+
+
 @pytest.mark.parametrize("prec", [0, 1, 2])
 def test_solve_matches_exact_solution(smooth32, prec):
     pr, P, ud = smooth32
