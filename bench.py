@@ -184,6 +184,8 @@ def main():
                     help="only build the workload and launch thermo_bench_kernel(K) three times (for ncu)")
     ap.add_argument("--profile-solve", action="store_true",
                     help="only set up and run one mixed solve inside an NVTX range 'solve' (for ncu)")
+    ap.add_argument("--profile-setup", action="store_true",
+                    help="only run one warm-up set-up, then one set-up inside an NVTX range 'setup' (for ncu)")
     ap.add_argument("--prec", type=int, default=1, help="precision of the profiling modes")
     ap.add_argument("--kernels-only", action="store_true", help="only time the kernels and one solve per form")
     args = ap.parse_args()
@@ -264,6 +266,21 @@ def main():
                          "rel": info["rel_res_true"], "kernels_ms_GBps": ks}
             sv.close()
         print(json.dumps(res))
+        return 0
+
+    if args.profile_setup:
+        s = make(args.prec)
+        s.set_density(x_d, pr["p"], pr["kmin"], pr["kmax"])
+        s.setup_precond()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("setup")
+        t0 = time.perf_counter()
+        s.set_density(x_d, pr["p"], pr["kmin"], pr["kmax"])
+        s.setup_precond()
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print(json.dumps({"setup_s": time.perf_counter() - t0}))
+        s.close()
         return 0
 
     if args.profile_kernel is not None or args.profile_solve:

@@ -93,7 +93,10 @@ typedef struct {
   thermo_pc pc;
   int guess;                        /* a thermo_guess value */
   int max_iter;                     /* default 10000 */
-  int flexible;                     /* -1 auto (flexible iff prec != FP64), 0, 1 */
+  int flexible;                     /* -1 auto (1 iff prec != FP64); 0 standard PCG;
+                                       1 flexible CG, new direction A-orthogonalised
+                                       against the last one (robust to the FP32 cycle);
+                                       2 flexible CG with the Polak-Ribiere beta */
   int check_every;                  /* host convergence check every k iterations (>= 1) */
   int smoother;                     /* fine smoother: 0 damped Jacobi (nu_fine sweeps, omega),
                                        1 Chebyshev-accelerated Jacobi (default) */
@@ -109,6 +112,10 @@ typedef struct {
                                        capped at 64 (1: the same on every coarse level) */
   int w_from;                       /* 0: V-cycle; k > 0: levels >= k make two coarse
                                        corrections per visit (W-cycle below level k) */
+  double restart_decades;           /* > 0: restart the recurrence from the true FP64
+                                       residual each time the recursive residual has
+                                       dropped by this many decades (iterative refinement
+                                       around the low-precision cycle); 0: never */
 } thermo_options;
 
 typedef struct {
@@ -124,7 +131,7 @@ typedef struct {
 /* Fill *opt with the defaults for an Nx x Ny x Nz grid: b = 4, L_1 = 4, then
  * groups of 2^3 cells down to a 4^3-cell coarsest level with L = 17 (the
  * second level keeps 8 vectors when there are more than two coarse levels),
- * Chebyshev fine smoother of degree 4 on [lmax/30, 1.1 lmax] (15 power
+ * Chebyshev fine smoother of degree 5 on [lmax/30, 1.1 lmax] (15 power
  * iterations), nu_fine = 2 / omega = 2/3 for the Jacobi alternative,
  * nu_coarse = 1, MIXED, MMG, coarse guess, max_iter = 10000, flexible auto,
  * check_every = 1.  Returns EINVAL if the
@@ -278,6 +285,11 @@ thermo_status thermo_filter(thermo_ctx *ctx, const double *in, double *out,
 thermo_status thermo_oc_update(thermo_ctx *ctx, double *x, const double *dc,
                                const double *dv, double volfrac, double move,
                                double rmin, double *change);
+
+/* Relative recursive residuals ||r_k|| / ||b_F|| of the last thermo_solve, one
+ * per convergence check (every opt.check_every iterations); copies at most
+ * max of them to out (host, may be NULL) and returns how many exist. */
+int thermo_residual_history(const thermo_ctx *ctx, double *out, int max);
 
 /* Number of kernel launches this library has issued in the process (host
  * counter; for launch accounting in benchmarks). */

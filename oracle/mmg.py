@@ -54,7 +54,7 @@ class MMGOptions:
     nu_coarse: int = 1
     omega: float = 2.0 / 3.0
     smoother: str = "jacobi"            # fine smoother: "jacobi" or "chebyshev"
-    cheb_degree: int = 4                # Chebyshev: matrix-vector products per smoothing
+    cheb_degree: int = 5                # Chebyshev: matrix-vector products per smoothing
     cheb_ratio: float = 30.0            # interval [lmax / ratio, 1.1 lmax] of D^-1 A
     power_iters: int = 15               # power iterations for lmax(D^-1 A)
 

@@ -96,6 +96,70 @@ __global__ void k_csmooth(CLevel lv, const T* __restrict__ tiles, const T* __res
   }
 }
 
+// Levels with many vectors per cell (L >= 12): one CTA per cell, one thread per
+// (neighbour tile n, row i) forming the partial row sum of that tile, then the
+// rows summed over the 27 neighbours in fixed order (deterministic).
+//   MODE 0: out = A x;  MODE 1: out = r - A x;  MODE 2: out = x + Dinv (r - A x)
+template <class T, int MODE>
+__global__ void k_ccell(CLevel lv, const T* __restrict__ tiles, const T* __restrict__ Dinv, const T* __restrict__ r,
+                        const T* __restrict__ x, T* __restrict__ out) {
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  const int L = lv.L;
+  T* part = reinterpret_cast<T*>(sm_raw);  // [27][L]
+  T* res = part + 27 * L;                  // [L]
+  const long long c = blockIdx.x;
+  const int cx = (int)(c % lv.mx);
+  const long long tt = c / lv.mx;
+  const int cy = (int)(tt % lv.my), cz = (int)(tt / lv.my);
+  for (int idx = threadIdx.x; idx < 27 * L; idx += blockDim.x) {
+    const int n = idx / L, i = idx - n * L;
+    const int nx = cx + n % 3 - 1, ny = cy + (n / 3) % 3 - 1, nz = cz + n / 9 - 1;
+    T s = T(0);
+    if (nx >= 0 && ny >= 0 && nz >= 0 && nx < lv.mx && ny < lv.my && nz < lv.mz) {
+      const long long nc = nx + (long long)lv.mx * (ny + (long long)lv.my * nz);
+      const T* row = tiles + ((c * 27 + n) * L + i) * (long long)L;
+      const T* xv = x + nc * L;
+      T s2 = T(0);
+      int j = 0;
+      for (; j + 1 < L; j += 2) {
+        s = fma(row[j], xv[j], s);
+        s2 = fma(row[j + 1], xv[j + 1], s2);
+      }
+      if (j < L) s = fma(row[j], xv[j], s);
+      s += s2;
+    }
+    part[n * L + i] = s;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < L; i += blockDim.x) {
+    T s = T(0);
+    for (int n = 0; n < 27; ++n) s += part[n * L + i];
+    if (MODE == 0)
+      out[c * L + i] = s;
+    else if (MODE == 1)
+      out[c * L + i] = r[c * L + i] - s;
+    else
+      res[i] = r[c * L + i] - s;
+  }
+  if (MODE == 2) {
+    __syncthreads();
+    for (int i = threadIdx.x; i < L; i += blockDim.x) {
+      const T* D = Dinv + (c * L + i) * (long long)L;
+      T s = T(0);
+      for (int j = 0; j < L; ++j) s = fma(D[j], res[j], s);
+      out[c * L + i] = x[c * L + i] + s;
+    }
+  }
+}
+template <class T, int MODE>
+static void launch_ccell(const CLevel& lv, const T* tiles, const T* Dinv, const T* r, const T* x, T* out,
+                         cudaStream_t st) {
+  const int nt = ((27 * lv.L + 31) / 32) * 32;
+  const size_t sm = (size_t)28 * lv.L * sizeof(T);
+  note_launch(), k_ccell<T, MODE><<<(unsigned)lv.ncell, nt > 1024 ? 1024 : nt, sm, st>>>(lv, tiles, Dinv, r, x, out);
+}
+constexpr int CCELL_MIN_L = 12;
+
 // rc[G][k] = sum_{c in G} sum_i Psi[G][lc*Lf + i][k] res[c][i]
 template <class T>
 __global__ void k_crestrict(CLevel f, CLevel cs, const T* __restrict__ Psi, const T* __restrict__ res,
@@ -179,12 +243,20 @@ static int cgrid(long long n, int nt = 256) {
 
 template <class T>
 cudaError_t coarse_apply(const CLevel& lv, const T* tiles, const T* x, T* y, cudaStream_t st) {
+  if (lv.L >= CCELL_MIN_L) {
+    launch_ccell<T, 0>(lv, tiles, nullptr, nullptr, x, y, st);
+    return cudaGetLastError();
+  }
   note_launch();
   LT_DISPATCH(lv.L, (k_capply<T, LT><<<cgrid(lv.ncell * lv.L), 256, 0, st>>>(lv, tiles, x, y)));
   return cudaGetLastError();
 }
 template <class T>
 cudaError_t coarse_residual(const CLevel& lv, const T* tiles, const T* r, const T* e, T* res, cudaStream_t st) {
+  if (lv.L >= CCELL_MIN_L) {
+    launch_ccell<T, 1>(lv, tiles, nullptr, r, e, res, st);
+    return cudaGetLastError();
+  }
   note_launch();
   LT_DISPATCH(lv.L, (k_cresidual<T, LT><<<cgrid(lv.ncell * lv.L), 256, 0, st>>>(lv, tiles, r, e, res)));
   return cudaGetLastError();
@@ -197,6 +269,10 @@ cudaError_t coarse_smooth0(const CLevel& lv, const T* Dinv, const T* r, T* e, cu
 template <class T>
 cudaError_t coarse_smooth(const CLevel& lv, const T* tiles, const T* Dinv, const T* r, const T* e, T* out,
                           cudaStream_t st) {
+  if (lv.L >= CCELL_MIN_L) {
+    launch_ccell<T, 2>(lv, tiles, Dinv, r, e, out, st);
+    return cudaGetLastError();
+  }
   const int cpc = lv.L >= 128 ? 1 : 128 / lv.L;
   const long long nb = (lv.ncell + cpc - 1) / cpc;
   const int nt = ((cpc * lv.L + 31) / 32) * 32;

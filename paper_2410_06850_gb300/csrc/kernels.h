@@ -54,8 +54,8 @@ cudaError_t vec_dot_free(const Geom& g, const uint32_t* bits, const double* a, c
 cudaError_t vec_copy_cvt(const Geom& g, const double* src, void* dst, int dst_kind, cudaStream_t st);  // 0 f64,1 f32,2 bf16
 cudaError_t cg_update(const Geom& g, double* u, double* r, const double* p, const double* q, const void* z_old,
                       int z_kind, void* r_lp, int r_lp_kind, CgScalars* sc, const Reducer& red, cudaStream_t st);
-cudaError_t cg_beta_dot(const Geom& g, const double* r, const void* z, int z_kind, int flexible, CgScalars* sc,
-                        const Reducer& red, cudaStream_t st);
+cudaError_t cg_beta_dot(const Geom& g, const double* r, const void* z, int zk, const double* q, int flexible,
+                        CgScalars* sc, const Reducer& red, cudaStream_t st);
 cudaError_t cg_pupdate(const Geom& g, const void* z, int z_kind, double* p, const CgScalars* sc, int first,
                        cudaStream_t st);
 cudaError_t vec_to_f64(const Geom& g, const void* src, int kind, double* dst, cudaStream_t st);

@@ -57,6 +57,7 @@ struct KTimer {
 
 struct thermo_ctx {
   std::string err;
+  std::vector<double> hist;  // relative recursive residual at each check of the last solve
   bool kt_on = false;
   KTimer kt[THERMO_KT_COUNT];
   cudaStream_t st = nullptr;
@@ -170,12 +171,13 @@ extern "C" thermo_status thermo_default_options(const int grid[3], thermo_option
   opt->flexible = -1;
   opt->check_every = 1;
   opt->smoother = 1;
-  opt->cheb_degree = 4;
+  opt->cheb_degree = 5;
   opt->cheb_ratio = 30.0;
   opt->power_iters = 15;
   opt->outer_apply = 0;
   opt->nu_growth = 1;
   opt->w_from = 0;
+  opt->restart_decades = 0;
   return THERMO_OK;
 }
 
@@ -210,8 +212,10 @@ extern "C" thermo_status thermo_create(const int grid[3], const double h[3], con
   if (grid[0] % b || grid[1] % b || grid[2] % b) return fail(ctx, THERMO_EINVAL, "grid must be a multiple of block");
   if (opt.nu_fine < 1 || opt.nu_coarse < 1 || opt.nu_fine > 64) return fail(ctx, THERMO_EINVAL, "smoothing sweeps must be in [1, 64]");
   if (opt.smoother != 0 && opt.smoother != 1) return fail(ctx, THERMO_EINVAL, "smoother must be 0 (Jacobi) or 1 (Chebyshev)");
+  if (opt.flexible < -1 || opt.flexible > 2) return fail(ctx, THERMO_EINVAL, "flexible must be -1, 0, 1 or 2");
   if (opt.nu_growth < 1 || opt.nu_growth > 8) return fail(ctx, THERMO_EINVAL, "nu_growth must be in 1..8");
   if (opt.w_from < 0) return fail(ctx, THERMO_EINVAL, "w_from must be >= 0");
+  if (!(opt.restart_decades >= 0.0)) return fail(ctx, THERMO_EINVAL, "restart_decades must be >= 0");
   if (opt.outer_apply < 0 || opt.outer_apply > 2) return fail(ctx, THERMO_EINVAL, "outer_apply must be 0, 1 or 2");
   if (opt.smoother == 1 && (opt.cheb_degree < 1 || opt.cheb_degree > 64 || !(opt.cheb_ratio > 1.0) || opt.power_iters < 1))
     return fail(ctx, THERMO_EINVAL, "Chebyshev needs 1 <= degree <= 64, ratio > 1, power_iters >= 1");
@@ -834,13 +838,14 @@ extern "C" thermo_status thermo_solve(thermo_ctx* ctx, const double* rhs, double
   if (s != THERMO_OK) return s;
   const double bnorm = sqrt(ctx->sc_h->bb);
   double rn = sqrt(ctx->sc_h->rr);
+  ctx->hist.clear();
   if (!std::isfinite(bnorm)) return fail(ctx, THERMO_EINVAL, "right-hand side is not finite");
   if (!std::isfinite(rn)) {
     inf.status = THERMO_EBREAKDOWN;
     if (info) *info = inf;
     return fail(ctx, THERMO_EBREAKDOWN, "initial residual is not finite (check the density)");
   }
-  int it = 0, restarts = 0;
+  int it = 0, restarts = 0, refinements = 0;
   thermo_status result = THERMO_OK;
   auto start_cycle = [&](void) -> thermo_status {
     // r (FP64) -> cycle storage, z = B r, rz = r.z, p = z
@@ -863,14 +868,18 @@ extern "C" thermo_status thermo_solve(thermo_ctx* ctx, const double* rhs, double
     const double apply_bytes = ctx->kt_on ? fine_bytes(g, 16.0, 8.0) : 0.0;
     const double apply_flops = 2.0 * (g.cube ? 21.0 : 27.0) * (double)ctx->nnode;
     const double nn = (double)ctx->nnode;
+    // low-precision cycles limit how far one recurrence can reduce the residual:
+    // restart from the true residual every restart_decades decades
+    double anchor = rn;
+    const double restart_factor = o.restart_decades > 0 ? pow(10.0, -o.restart_decades) : 0.0;
     while (true) {
       kt_begin(ctx, THERMO_KT_APPLY64);
       CK(outer_apply_dot(ctx, ctx->p, ctx->q, &ctx->sc->pq));
       kt_end(ctx, THERMO_KT_APPLY64, apply_bytes, apply_flops);
       kt_begin(ctx, THERMO_KT_CGVEC);
-      CK(cg_update(g, ctx->u, ctx->r, ctx->p, ctx->q, flexible ? zptr(ctx) : nullptr, zkind(ctx), rptr(ctx),
+      CK(cg_update(g, ctx->u, ctx->r, ctx->p, ctx->q, flexible == 2 ? zptr(ctx) : nullptr, zkind(ctx), rptr(ctx),
                    rkind(ctx), ctx->sc, ctx->red, st));
-      kt_end(ctx, THERMO_KT_CGVEC, nn * (4 * 8.0 + 2 * 8.0 + rs + (flexible ? zs : 0.0)));
+      kt_end(ctx, THERMO_KT_CGVEC, nn * (4 * 8.0 + 2 * 8.0 + rs + (flexible == 2 ? zs : 0.0)));
       ++it;
       if (it % check == 0 || it >= o.max_iter) {
         s = read_scalars(ctx);
@@ -880,6 +889,7 @@ extern "C" thermo_status thermo_solve(thermo_ctx* ctx, const double* rhs, double
           break;
         }
         rn = sqrt(ctx->sc_h->rr);
+        ctx->hist.push_back(bnorm > 0 ? rn / bnorm : 0.0);
         if (rn <= tol * bnorm) {
           s = true_residual(ctx, b);
           if (s != THERMO_OK) return s;
@@ -899,11 +909,23 @@ extern "C" thermo_status thermo_solve(thermo_ctx* ctx, const double* rhs, double
           result = fail(ctx, THERMO_ENOTCONV, "no convergence in %d iterations", it);
           break;
         }
+        if (o.restart_decades > 0 && rn <= anchor * restart_factor) {
+          // refinement step: true FP64 residual, fresh recurrence from z = B r
+          s = true_residual(ctx, b);
+          if (s != THERMO_OK) return s;
+          s = read_scalars(ctx);
+          if (s != THERMO_OK) return s;
+          anchor = sqrt(ctx->sc_h->rr);
+          ++refinements;
+          s = start_cycle();
+          if (s != THERMO_OK) return s;
+          continue;
+        }
       }
       CK(apply_precond(ctx));
       kt_begin(ctx, THERMO_KT_CGVEC);
-      CK(cg_beta_dot(g, ctx->r, zptr(ctx), zkind(ctx), flexible, ctx->sc, ctx->red, st));
-      kt_end(ctx, THERMO_KT_CGVEC, nn * (8.0 + zs));
+      CK(cg_beta_dot(g, ctx->r, zptr(ctx), zkind(ctx), ctx->q, flexible, ctx->sc, ctx->red, st));
+      kt_end(ctx, THERMO_KT_CGVEC, nn * (8.0 + zs + (flexible == 1 ? 8.0 : 0.0)));
       kt_begin(ctx, THERMO_KT_CGVEC);
       CK(cg_pupdate(g, zptr(ctx), zkind(ctx), ctx->p, ctx->sc, 0, st));
       kt_end(ctx, THERMO_KT_CGVEC, nn * (zs + 16.0));
@@ -923,7 +945,7 @@ extern "C" thermo_status thermo_solve(thermo_ctx* ctx, const double* rhs, double
   kt_fold(ctx);
   if (fine_stage_errors(true)) result = fail(ctx, THERMO_ECUDA, "a fine-grid kernel timed out waiting for its TMA stage");
   inf.iters = it;
-  inf.restarts = restarts;
+  inf.restarts = restarts + refinements;
   inf.t_solve_ms = now_ms() - t0;
   inf.status = result;
   if (info) *info = inf;
@@ -1121,6 +1143,14 @@ extern "C" thermo_status thermo_oc_update(thermo_ctx* ctx, double* x, const doub
 }
 
 extern "C" long long thermo_launch_count(void) { return thermo::launch_count(); }
+
+extern "C" int thermo_residual_history(const thermo_ctx* ctx, double* out, int max) {
+  if (!ctx) return 0;
+  const int n = (int)ctx->hist.size();
+  if (out)
+    for (int i = 0; i < n && i < max; ++i) out[i] = ctx->hist[i];
+  return n;
+}
 
 extern "C" thermo_status thermo_kernel_timers(thermo_ctx* ctx, int enable) {
   if (!ctx) return THERMO_EINVAL;

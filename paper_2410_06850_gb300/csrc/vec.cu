@@ -390,20 +390,35 @@ cudaError_t cg_update(const Geom& g, double* u, double* r, const double* p, cons
   return cg_update_t<double>(g, u, r, p, q, (const double*)z_old, r_lp, rk, sc, red, st);
 }
 
-// rzn = r.z;  beta = (rzn - rzo)/rz (flexible) or rzn/rz;  rz = rzn
+// rzn = r.z; beta for p' = z + beta p:
+//   flexible 0: rzn / rz (standard PCG)
+//   flexible 1: -(z.q) / (p.q), q = A p of the previous direction (flexible CG with explicit
+//               A-orthogonalisation against the last direction, Notay's truncated form)
+//   flexible 2: (rzn - r.z_old) / rz (Polak-Ribiere)
+//   rz = rzn
 template <class Tz>
 __global__ void __launch_bounds__(VNT) k_beta(Geom g, Rows R, const double* __restrict__ r, const Tz* __restrict__ z,
-                                              int flexible, CgScalars* sc, Reducer red) {
-  double v[1] = {0.0}, res[1];
+                                              const double* __restrict__ q, int flexible, CgScalars* sc, Reducer red) {
+  double v[2] = {0.0, 0.0}, res[2];
   for (long long it = blockIdx.x * (long long)VNT + threadIdx.x; it < R.items; it += (long long)gridDim.x * VNT) {
     const long long i = item_index(g, it, R.ppr);
     double2 rr = ld2<double>(r + i), zz = ld2<Tz>(z + i);
     v[0] += rr.x * zz.x + rr.y * zz.y;
+    if (flexible == 1) {
+      const double2 qq = ld2<double>(q + i);
+      v[1] += zz.x * qq.x + zz.y * qq.y;
+    }
   }
-  if (reduce_k<1>(v, red, res) && threadIdx.x == 0) {
+  if (reduce_k<2>(v, red, res) && threadIdx.x == 0) {
     const double rzn = res[0];
     const double rz = sc->rz;
-    double beta = flexible ? (rzn - sc->rzo) / rz : rzn / rz;
+    double beta;
+    if (flexible == 1)
+      beta = -res[1] / sc->pq;
+    else if (flexible == 2)
+      beta = (rzn - sc->rzo) / rz;
+    else
+      beta = rzn / rz;
     if (!isfinite(beta)) {
       beta = 0.0;
       sc->flag = 1;
@@ -413,16 +428,16 @@ __global__ void __launch_bounds__(VNT) k_beta(Geom g, Rows R, const double* __re
     sc->rz = rzn;
   }
 }
-cudaError_t cg_beta_dot(const Geom& g, const double* r, const void* z, int zk, int flexible, CgScalars* sc,
-                        const Reducer& red, cudaStream_t st) {
+cudaError_t cg_beta_dot(const Geom& g, const double* r, const void* z, int zk, const double* q, int flexible,
+                        CgScalars* sc, const Reducer& red, cudaStream_t st) {
   Rows R = rows_of(g);
   const int nb = vec_blocks(R.items);
   if (zk == 1)
-    note_launch(), k_beta<float><<<nb, VNT, 0, st>>>(g, R, r, (const float*)z, flexible, sc, red);
+    note_launch(), k_beta<float><<<nb, VNT, 0, st>>>(g, R, r, (const float*)z, q, flexible, sc, red);
   else if (zk == 2)
-    note_launch(), k_beta<bf16><<<nb, VNT, 0, st>>>(g, R, r, (const bf16*)z, flexible, sc, red);
+    note_launch(), k_beta<bf16><<<nb, VNT, 0, st>>>(g, R, r, (const bf16*)z, q, flexible, sc, red);
   else
-    note_launch(), k_beta<double><<<nb, VNT, 0, st>>>(g, R, r, (const double*)z, flexible, sc, red);
+    note_launch(), k_beta<double><<<nb, VNT, 0, st>>>(g, R, r, (const double*)z, q, flexible, sc, red);
   return cudaGetLastError();
 }
 

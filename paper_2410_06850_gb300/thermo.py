@@ -31,7 +31,7 @@ EXPORTED = ["thermo_default_options", "thermo_create", "thermo_set_density", "th
             "thermo_destroy", "thermo_apply", "thermo_vcycle", "thermo_load_vector",
             "thermo_hierarchy", "thermo_export_level", "thermo_filter", "thermo_oc_update",
             "thermo_launch_count", "thermo_bench_kernel", "thermo_apply_dot",
-          "thermo_kernel_timers", "thermo_kernel_time", "thermo_dot_noalloc"]
+          "thermo_kernel_timers", "thermo_kernel_time", "thermo_dot_noalloc", "thermo_residual_history"]
 
 
 class thermo_options(C.Structure):
@@ -41,7 +41,7 @@ class thermo_options(C.Structure):
                 ("max_iter", C.c_int), ("flexible", C.c_int), ("check_every", C.c_int),
                 ("smoother", C.c_int), ("cheb_degree", C.c_int), ("cheb_ratio", C.c_double),
                 ("power_iters", C.c_int), ("outer_apply", C.c_int),
-                ("nu_growth", C.c_int), ("w_from", C.c_int)]
+                ("nu_growth", C.c_int), ("w_from", C.c_int), ("restart_decades", C.c_double)]
 
 
 class thermo_solve_info(C.Structure):
@@ -95,6 +95,8 @@ def lib():
         L.thermo_apply_dot.argtypes = [vp, vp, vp, dp]
         L.thermo_kernel_timers.argtypes = [vp, i]
         L.thermo_dot_noalloc.argtypes = [vp, vp, C.c_longlong, vp, vp, C.c_char_p, i]
+        L.thermo_residual_history.argtypes = [vp, C.POINTER(C.c_double), i]
+        L.thermo_residual_history.restype = C.c_int
         L.thermo_kernel_time.argtypes = [vp, i, dp, C.POINTER(C.c_longlong), dp, dp]
         for n in EXPORTED:
             if n not in ("thermo_last_error", "thermo_destroy", "thermo_launch_count"):
@@ -234,6 +236,13 @@ class Solver:
         d = C.c_double()
         self._check(lib().thermo_apply_dot(self.ctx, _ptr(p), _ptr(q), C.byref(d)))
         return q, d.value
+
+    def residual_history(self):
+        """Relative recursive residuals of the last solve, one per convergence check."""
+        n = lib().thermo_residual_history(self.ctx, None, 0)
+        buf = (C.c_double * max(n, 1))()
+        lib().thermo_residual_history(self.ctx, buf, n)
+        return list(buf[:n])
 
     def kernel_timers(self, enable=True):
         """Start (zeroing the totals) or stop the per-kernel-class event timers of solve()."""
