@@ -109,9 +109,11 @@ typedef struct {
                                        (FP64-accurate sums of two floats on the FP32 pipes;
                                        falls back to 1 where the grid does not allow it) */
   int nu_growth;                    /* coarse sweeps on level l: nu_coarse * nu_growth^(l-1),
-                                       capped at 64 (1: the same on every coarse level) */
+                                       capped at 64 (1: the same on every coarse level;
+                                       default 2) */
   int w_from;                       /* 0: V-cycle; k > 0: levels >= k make two coarse
-                                       corrections per visit (W-cycle below level k) */
+                                       corrections per visit (W-cycle below level k), except
+                                       just above the direct coarsest solve (default 3) */
   double restart_decades;           /* > 0: restart the recurrence from the true FP64
                                        residual each time the recursive residual has
                                        dropped by this many decades (iterative refinement

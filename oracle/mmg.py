@@ -22,6 +22,10 @@ Follows Sec. 3 of the paper step by step:
 * Galerkin coarse operators A_c = R_c A R_c^T, A_cc = R_cc A_c R_cc^T (Sec. 3).
 * Smoothed V-cycle, Algorithm 1 (generalised to any number of levels, with
   the coarsest "correction" read as a solve with A_cc, i.e. A_cc^{-1} r_cc).
+  Coarse levels: nu_coarse sweeps on level 1, doubled per level below it, and
+  two coarse corrections per visit from level 3 on (a W-cycle: the deep levels
+  stand in for the paper's direct coarse-coarse solve, so they are solved more
+  accurately than one V-cycle would).
   Fine smoother: nu damped-Jacobi sweeps, or (default) Chebyshev-accelerated
   Jacobi of degree m on [lmax/30, 1.1 lmax] of D^-1 A -- the paper smooths
   with block-Jacobi inside PETSc's Krylov smoothers (Sec. 4), whose
@@ -52,6 +56,8 @@ class MMGOptions:
     group: tuple = (2,)                 # g_2, g_3, ... (one per level >= 2)
     nu_fine: int = 2                    # damped-Jacobi sweeps (smoother = "jacobi")
     nu_coarse: int = 1
+    nu_growth: int = 2                  # coarse sweeps on level l: nu_coarse * nu_growth^(l-1), at most 64
+    w_from: int = 3                     # levels >= w_from make two coarse corrections (0: V-cycle)
     omega: float = 2.0 / 3.0
     smoother: str = "jacobi"            # fine smoother: "jacobi" or "chebyshev"
     cheb_degree: int = 5                # Chebyshev: matrix-vector products per smoothing
@@ -354,18 +360,23 @@ class MMG:
         e = np.zeros_like(r)
         if l == 0 and self.opts.smoother == "chebyshev":
             return self._chebyshev(r, e)
-        nu = self.opts.nu_fine if l == 0 else self.opts.nu_coarse
-        for _ in range(nu):
+        for _ in range(self._sweeps(l)):
             e = self._smooth(l, r, e)
         return e
 
     def _postsmooth(self, l, r, e):
         if l == 0 and self.opts.smoother == "chebyshev":
             return self._chebyshev(r, e)
-        nu = self.opts.nu_fine if l == 0 else self.opts.nu_coarse
-        for _ in range(nu):
+        for _ in range(self._sweeps(l)):
             e = self._smooth(l, r, e)
         return e
+
+    def _sweeps(self, l):
+        """Smoothing sweeps on level l: nu_fine on the fine grid; nu_coarse on level 1,
+        multiplied by nu_growth per level below it (at most 64)."""
+        if l == 0:
+            return self.opts.nu_fine
+        return min(64, self.opts.nu_coarse * self.opts.nu_growth ** (l - 1))
 
     def vcycle(self, r, l=0):
         """Algorithm 1 on grids l, l+1, ..., coarsest (recursive)."""
@@ -375,9 +386,14 @@ class MMG:
         A = self._A(l)
         e = self._presmooth(l, r)                 # pre-smoothing (from e = 0)
         P = self.levels[l].P
-        rc = P.T @ (r - A @ e)                    # restriction of the residual
-        ec = self.vcycle(rc, l + 1)
-        e = e + P @ ec                            # prolongation
+        # one coarse correction (V-cycle); two on coarse levels >= w_from (W-cycle) unless
+        # the next level is the direct solve, where a second Galerkin correction is zero
+        w = self.opts.w_from
+        reps = 2 if (l >= 1 and w > 0 and l >= w and l + 1 < nlev) else 1
+        for _ in range(reps):
+            rc = P.T @ (r - A @ e)                # restriction of the residual
+            ec = self.vcycle(rc, l + 1)
+            e = e + P @ ec                        # prolongation
         e = self._postsmooth(l, r, e)             # post-smoothing (S^{-T} = S^{-1})
         return e
 

@@ -175,8 +175,8 @@ extern "C" thermo_status thermo_default_options(const int grid[3], thermo_option
   opt->cheb_ratio = 30.0;
   opt->power_iters = 15;
   opt->outer_apply = 0;
-  opt->nu_growth = 1;
-  opt->w_from = 0;
+  opt->nu_growth = 2;
+  opt->w_from = 3;
   opt->restart_decades = 0;
   return THERMO_OK;
 }

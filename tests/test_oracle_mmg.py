@@ -157,11 +157,14 @@ def _dense_vcycle_matrix(H, P):
         A = mats[l]
         if l == len(mats) - 1:
             return np.linalg.inv(A)
-        nu = o.nu_fine if l == 0 else o.nu_coarse
+        nu = o.nu_fine if l == 0 else min(64, o.nu_coarse * o.nu_growth ** (l - 1))
         I = np.eye(A.shape[0])
         S = I - smoother_inv(l) @ A
         Sn = np.linalg.matrix_power(S, nu)
-        E = Sn @ (I - Ps[l] @ B(l + 1) @ Ps[l].T @ A) @ Sn
+        # coarse corrections per visit: two (W-cycle) on levels >= w_from above the second-coarsest
+        reps = 2 if (l >= 1 and o.w_from > 0 and l >= o.w_from and l + 2 < len(mats)) else 1
+        C = np.linalg.matrix_power(I - Ps[l] @ B(l + 1) @ Ps[l].T @ A, reps)
+        E = Sn @ C @ Sn
         return (I - E) @ np.linalg.inv(A)
 
     return B(0)
@@ -178,6 +181,35 @@ def test_vcycle_equals_closed_product_form():
         ej = np.zeros(n)
         ej[j] = 1.0
         np.testing.assert_allclose(H(ej), Bd[:, j], rtol=1e-9, atol=1e-12 * np.abs(Bd).max())
+
+
+def test_wcycle_with_growing_sweeps_equals_closed_product_form():
+    """Three coarse levels, sweeps doubling per level and two coarse
+    corrections per visit on level 1: the recursive cycle equals the dense
+    product form E_l = S^nu_l (I - P B_(l+1) P^T A)^2 S^nu_l, and stays
+    symmetric positive definite."""
+    P = _prob(N=8, seed=23)
+    o = mmg.MMGOptions(block=2, nvec=(4, 6, 6), group=(2, 2), nu_growth=2, w_from=1)
+    H = mmg.MMG(P, o)
+    assert len(H.levels) == 3
+    Bd = _dense_vcycle_matrix(H, P)
+    n = P["A"].shape[0]
+    for j in [0, 9, 200, n - 1]:
+        ej = np.zeros(n)
+        ej[j] = 1.0
+        np.testing.assert_allclose(H(ej), Bd[:, j], rtol=1e-9, atol=1e-12 * np.abs(Bd).max())
+    x = _free_random(P, 3)
+    y = _free_random(P, 4)
+    assert abs(H(x) @ y - x @ H(y)) <= 1e-12 * np.linalg.norm(H(x)) * np.linalg.norm(y)
+    assert x @ H(x) > 0
+    # the W-cycle is a better solver than the V-cycle on the same hierarchy
+    ov = mmg.MMGOptions(block=2, nvec=(4, 6, 6), group=(2, 2), nu_growth=1, w_from=0)
+    Bv = _dense_vcycle_matrix(mmg.MMG(P, ov), P)
+    A = P["A"].toarray()
+    free = ~P["mask"]
+    I = np.eye(n)
+    rho = lambda B: np.abs(np.linalg.eigvals((I - B @ A)[np.ix_(free, free)])).max()
+    assert rho(Bd) < rho(Bv)
 
 
 def test_vcycle_symmetric_positive_definite():
