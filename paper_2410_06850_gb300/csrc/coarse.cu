@@ -96,39 +96,58 @@ __global__ void k_csmooth(CLevel lv, const T* __restrict__ tiles, const T* __res
   }
 }
 
-// Levels with many vectors per cell (L >= 12): one CTA per cell, one thread per
-// (neighbour tile n, row i) forming the partial row sum of that tile, then the
-// rows summed over the 27 neighbours in fixed order (deterministic).
+// Levels with many vectors per cell (L >= 12): one CTA per cell.  The cell's
+// 27 tiles (contiguous, 27 L^2 values) are staged into shared memory with
+// coalesced loads by all threads, the 27 neighbour vectors gathered beside
+// them; thread (n, i) forms the partial row sum of tile n, then the rows are
+// summed over the 27 neighbours in fixed order (deterministic).
 //   MODE 0: out = A x;  MODE 1: out = r - A x;  MODE 2: out = x + Dinv (r - A x)
 template <class T, int MODE>
 __global__ void k_ccell(CLevel lv, const T* __restrict__ tiles, const T* __restrict__ Dinv, const T* __restrict__ r,
                         const T* __restrict__ x, T* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int L = lv.L;
-  T* part = reinterpret_cast<T*>(sm_raw);  // [27][L]
-  T* res = part + 27 * L;                  // [L]
+  const int LL = L * L;
+  T* ts = reinterpret_cast<T*>(sm_raw);  // [27][L][L]
+  T* xs = ts + 27 * LL;                  // [27][L] (zero outside the grid)
+  T* part = xs + 27 * L;                 // [27][L]
+  T* res = part + 27 * L;                // [L]
   const long long c = blockIdx.x;
   const int cx = (int)(c % lv.mx);
   const long long tt = c / lv.mx;
   const int cy = (int)(tt % lv.my), cz = (int)(tt / lv.my);
-  for (int idx = threadIdx.x; idx < 27 * L; idx += blockDim.x) {
-    const int n = idx / L, i = idx - n * L;
+  const T* tg = tiles + c * 27 * (long long)LL;
+  // asynchronous element copies (all in flight at once), completed before the barrier
+  for (int k = threadIdx.x; k < 27 * LL; k += blockDim.x) {
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(ts + k);
+    if (sizeof(T) == 8)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(tg + k) : "memory");
+    else
+      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(tg + k) : "memory");
+  }
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+  for (int k = threadIdx.x; k < 27 * L; k += blockDim.x) {
+    const int n = k / L, j = k - n * L;
     const int nx = cx + n % 3 - 1, ny = cy + (n / 3) % 3 - 1, nz = cz + n / 9 - 1;
-    T s = T(0);
-    if (nx >= 0 && ny >= 0 && nz >= 0 && nx < lv.mx && ny < lv.my && nz < lv.mz) {
-      const long long nc = nx + (long long)lv.mx * (ny + (long long)lv.my * nz);
-      const T* row = tiles + ((c * 27 + n) * L + i) * (long long)L;
-      const T* xv = x + nc * L;
-      T s2 = T(0);
-      int j = 0;
-      for (; j + 1 < L; j += 2) {
-        s = fma(row[j], xv[j], s);
-        s2 = fma(row[j + 1], xv[j + 1], s2);
-      }
-      if (j < L) s = fma(row[j], xv[j], s);
-      s += s2;
+    T v = T(0);
+    if (nx >= 0 && ny >= 0 && nz >= 0 && nx < lv.mx && ny < lv.my && nz < lv.mz)
+      v = x[(nx + (long long)lv.mx * (ny + (long long)lv.my * nz)) * L + j];
+    xs[k] = v;
+  }
+  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 27 * L; idx += blockDim.x) {
+    const int n = idx / L;
+    const T* row = ts + (long long)idx * L;  // tile n, row i
+    const T* xv = xs + n * L;
+    T s = T(0), s2 = T(0);
+    int j = 0;
+    for (; j + 1 < L; j += 2) {
+      s = fma(row[j], xv[j], s);
+      s2 = fma(row[j + 1], xv[j + 1], s2);
     }
-    part[n * L + i] = s;
+    if (j < L) s = fma(row[j], xv[j], s);
+    part[idx] = s + s2;
   }
   __syncthreads();
   for (int i = threadIdx.x; i < L; i += blockDim.x) {
@@ -155,7 +174,8 @@ template <class T, int MODE>
 static void launch_ccell(const CLevel& lv, const T* tiles, const T* Dinv, const T* r, const T* x, T* out,
                          cudaStream_t st) {
   const int nt = ((27 * lv.L + 31) / 32) * 32;
-  const size_t sm = (size_t)28 * lv.L * sizeof(T);
+  const size_t sm = ((size_t)27 * lv.L * lv.L + (size_t)55 * lv.L) * sizeof(T);
+  if (sm > 48 * 1024) cudaFuncSetAttribute(k_ccell<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   note_launch(), k_ccell<T, MODE><<<(unsigned)lv.ncell, nt > 1024 ? 1024 : nt, sm, st>>>(lv, tiles, Dinv, r, x, out);
 }
 constexpr int CCELL_MIN_L = 12;
