@@ -36,8 +36,10 @@ WORKLOAD = "chan256_1e6"
 
 FP64_NOMINAL_GFLOPS = 1250.0
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the current kernels at this
-# workload (profiles/ summaries); None where no capture of the current kernel exists
-TRAFFIC = {}
+# workload (profiles/ summaries); None where no capture of the current kernel exists.
+# smooth: the three-term sweep with a staged previous iterate (7 of the 10 sweeps of a cycle);
+# apply_fp64: the float-float outer operator + p.Ap
+TRAFFIC = {"smooth": 315.894272e6 + 56.016896e6, "apply_fp64": 309.905920e6 + 109.324800e6}
 
 
 def _peaks():
@@ -178,7 +180,7 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-iters", type=int, default=137,
+    ap.add_argument("--ref-iters", type=int, default=86,
                     help="iterations of the FP64 solve at 256^3 used to scale the oracle sample")
     ap.add_argument("--profile-kernel", type=int, default=None,
                     help="only build the workload and launch thermo_bench_kernel(K) three times (for ncu)")
@@ -303,7 +305,13 @@ def main():
         return 0
 
     # ---- mixed form (headline)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
     s = make(thermo.MIXED)
+    s.set_density(x_d, pr["p"], pr["kmin"], pr["kmax"])
+    s.setup_precond()
+    torch.cuda.synchronize()
+    footprint_gb = (free0 - torch.cuda.mem_get_info()[0]) / 1e9
     u = torch.zeros(nnode, dtype=torch.float64, device="cuda")
     for _ in range(args.warmup):
         u, dc, info, tm = step(s, u)
@@ -408,6 +416,7 @@ def main():
            "config": {"workload": f"{args.workload}: 256^3 Q1 elements (16,974,593 nodes), channel-tree density "
                                   "V=0.2, p=3, kmin=1e-6, kmax=1, q=1, T=0 on 0.2x0.2 patch of z=0",
                       "tol": args.tol, "hierarchy": s.hierarchy(), "l2": "inputs larger than L2 (no flush)",
+                      "hbm_footprint_gb": footprint_gb,
                       "parallelism": f"replicas x{world}"},
            "iters": iters, "rel_res_true": infos[-1]["rel_res_true"], "setup_s": setup_s,
            "sensitivity_s": sens_s, "dof_per_s_apply": dof_apply, "variants": variants, "kernels": kern,
