@@ -171,6 +171,48 @@ def run_reference(args, rank, world):
     return 0
 
 
+def run_topopt(args, pr, mask_d, q_d):
+    """SIMP / optimality-criteria loop on the benchmark geometry: density filter
+    radius 1.5 elements, volume fraction 0.3, from uniform x = 0.3; every solve
+    starts from the previous solution corrected by the interpolated coarse
+    solution (warm coarse guess)."""
+    import torch
+    from paper_2410_06850_gb300 import Solver, thermo
+    grid = pr["grid"]
+    M = grid[0] * grid[1] * grid[2]
+    nnode = (grid[0] + 1) * (grid[1] + 1) * (grid[2] + 1)
+    p, kmin, kmax, rmin, vf = 3.0, 1e-3, 1.0, 1.5, 0.3
+    s = Solver(grid, pr["h"], mask_d, q_d, prec=thermo.MIXED, guess=3)
+    x = torch.full((M,), vf, dtype=torch.float64, device="cuda")
+    dv = s.filter(torch.ones(M, dtype=torch.float64, device="cuda"), rmin, transpose=True)
+    u = torch.zeros(nnode, dtype=torch.float64, device="cuda")
+    hist = []
+    torch.cuda.synchronize()
+    t_all = time.perf_counter()
+    for it in range(args.topopt):
+        t0 = time.perf_counter()
+        xp = s.filter(x, rmin)
+        s.set_density(xp, p, kmin, kmax)
+        s.setup_precond()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        u, info = s.solve(u=u, tol=args.tol)
+        torch.cuda.synchronize()
+        t2 = time.perf_counter()
+        c = s.compliance(u)
+        dc = s.filter(s.sensitivity(u), rmin, transpose=True)
+        change = s.oc_update(x, dc, dv, vf, 0.2, rmin)
+        torch.cuda.synchronize()
+        hist.append({"it": it, "compliance": c, "iters": info["iters"], "setup_s": t1 - t0, "solve_s": t2 - t1,
+                     "step_s": time.perf_counter() - t0, "change": change, "volume": float(xp.mean())})
+    total = time.perf_counter() - t_all
+    s.close()
+    print(json.dumps({"mode": "topopt", "workload": args.workload, "design_iterations": args.topopt,
+                      "total_s": total, "filter_rmin": rmin, "volfrac": vf, "kmin": kmin,
+                      "history": hist}))
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -189,6 +231,10 @@ def main():
     ap.add_argument("--profile-setup", action="store_true",
                     help="only run one warm-up set-up, then one set-up inside an NVTX range 'setup' (for ncu)")
     ap.add_argument("--prec", type=int, default=1, help="precision of the profiling modes")
+    ap.add_argument("--no-contrasts", action="store_true", help="skip the contrast 1e3 / 1e9 solves")
+    ap.add_argument("--topopt", type=int, default=0,
+                    help="run N SIMP/OC design iterations at the workload's size (density filter 1.5, V = 0.3, "
+                         "warm-started coarse guesses) and print one JSON line")
     ap.add_argument("--kernels-only", action="store_true", help="only time the kernels and one solve per form")
     args = ap.parse_args()
 
@@ -269,6 +315,9 @@ def main():
             sv.close()
         print(json.dumps(res))
         return 0
+
+    if args.topopt:
+        return run_topopt(args, pr, mask_d, q_d)
 
     if args.profile_setup:
         s = make(args.prec)
@@ -391,6 +440,32 @@ def main():
                 kern[kn] = {"ms": ms, "bytes": by, "GBps": (by / (ms * 1e-3) / 1e9) if by else None}
         sv.close()
 
+    # ---- contrast sweep: the same geometry at kmin = 1e-3 and 1e-9 (mixed form vs the FP64 form)
+    contrasts = {}
+    if not args.no_contrasts and args.workload == WORKLOAD:
+        for nm in ("chan256_1e3", "chan256_1e9"):
+            pc_ = make_inputs(nm)
+            xc = torch.as_tensor(pc_["x"]).cuda()
+            res = {}
+            for tag, prec in (("mixed", thermo.MIXED), ("fp64_form", thermo.FP64)):
+                sv = Solver(grid, pc_["h"], mask_d, q_d, prec=prec)
+                sv.set_density(xc, pc_["p"], pc_["kmin"], pc_["kmax"])
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                sv.setup_precond()
+                torch.cuda.synchronize()
+                ts = time.perf_counter() - t0
+                uc, ic = sv.solve(tol=args.tol)
+                uc, ic = sv.solve(tol=args.tol)
+                res[tag] = (uc, ic, ts)
+                sv.close()
+            um, im, tsm = res["mixed"]
+            uf, if_, tsf = res["fp64_form"]
+            contrasts[nm] = {"kmin": pc_["kmin"], "mixed_solve_s": im["t_solve_ms"] / 1e3, "mixed_iters": im["iters"],
+                             "mixed_rel_res_true": im["rel_res_true"], "setup_s": tsm,
+                             "fp64_form_solve_s": if_["t_solve_ms"] / 1e3, "fp64_form_iters": if_["iters"],
+                             "rel_diff_mixed_vs_fp64_form": float(torch.linalg.norm(um - uf) / torch.linalg.norm(uf))}
+
     # roofline of the dominant kernel class of the timed solves (largest summed event time)
     dom = max((k for k in klass if k != "coarse_levels"), key=lambda k: klass[k]["ms_total"])
     dk = klass[dom]
@@ -420,7 +495,7 @@ def main():
                       "parallelism": f"replicas x{world}"},
            "iters": iters, "rel_res_true": infos[-1]["rel_res_true"], "setup_s": setup_s,
            "sensitivity_s": sens_s, "dof_per_s_apply": dof_apply, "variants": variants, "kernels": kern,
-           "roofline": roof, "gpu_launches": launches, "kernel_classes": klass,
+           "roofline": roof, "gpu_launches": launches, "kernel_classes": klass, "contrasts": contrasts,
            "e2e": {"value": e2e_s, "unit": "s", "h2d_bytes_per_step": int(b_h.numel() * 8),
                    "d2h_bytes_per_step": int(u_h.numel() * 8), "iters": e2e_iters,
                    "what": "H2D right-hand side (pinned) + thermo_solve + D2H solution"},

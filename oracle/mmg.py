@@ -45,6 +45,8 @@ from __future__ import annotations
 from dataclasses import dataclass, field
 
 import numpy as np
+
+import workloads as W
 import scipy.linalg as sla
 import scipy.sparse as sp
 
@@ -101,9 +103,16 @@ class Level:
     eigvals: list = field(default_factory=list)
 
 
+POWER_SEED = 101
+
+
 def power_start(n):
-    """Deterministic start vector of the power iteration: 1 + (i mod 7)/7."""
-    return 1.0 + (np.arange(n) % 7) / 7.0
+    """Seeded start vector of the power iteration: u_i - 1/2 with u the SplitMix64
+    uniforms of stream POWER_SEED at the natural node index (the shared input
+    generator).  A random start has weight on the top of the spectrum of D^-1 A;
+    a smooth or periodic one does not on uniform media, where 15 iterations then
+    underestimate lmax by 12-17% and the Chebyshev smoother amplifies the top modes."""
+    return W.uniform01(POWER_SEED, n) - 0.5
 
 
 def lmax_estimate(A, D, free, iters):

@@ -234,3 +234,51 @@ def test_float_float_outer_operator_solve():
         s.close()
     assert relerr(us[2], us[1]) < 1e-8
     assert abs(res[2] - res[1]) <= 2, res
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-4), (1, 2e-5)])
+def test_wcycle_with_growing_sweeps_matches_oracle(prec, tol):
+    """The cycle options of the deep levels (R17), active at 64^3 when the W-cycle
+    starts at level 1: sweeps 1 / 2 on levels 1 / 2, two coarse corrections per
+    level-1 visit; the GPU cycle (FP64 form, and FP32 with the two-nodes-per-lane
+    engine) against the oracle's cycle with the same options."""
+    pr = small_problem(64, kind="smooth")
+    P = oracle_problem(pr)
+    s = gpu_solver(pr, prec=prec, w_from=1, nu_growth=2)
+    s.setup_precond()
+    o = mmg.default_options(64)
+    o.w_from, o.nu_growth = 1, 2
+    H = mmg.MMG(P, o)
+    n = P["A"].shape[0]
+    r = np.random.default_rng(6).standard_normal(n)
+    r[P["mask"]] = 0.0
+    z = s.vcycle(torch.as_tensor(r)).cpu().numpy()
+    assert relerr(z, H(r)) < tol, relerr(z, H(r))
+    s.close()
+
+
+@pytest.fixture(scope="module")
+def uniform64():
+    pr = small_problem(64, kind="rand", kmin=1e-3)
+    pr["x"] = np.full(64 ** 3, 0.3)
+    P = oracle_problem(pr)
+    H = mmg.MMG(P)
+    _, info = krylov.pcg(P["A"], P["b"], precond=H, u0=H.coarse_guess(P["b"]), tol=1e-8)
+    return pr, P, info["iters"]
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_uniform_density_converges_like_the_oracle(uniform64, prec):
+    """A uniform design (the first iterate of any SIMP loop): the Chebyshev
+    interval must cover the dense top of the spectrum of D^-1 A.  Both forms
+    converge, the FP64 form in the oracle's iteration count (+-2)."""
+    pr, P, it_oracle = uniform64
+    s = gpu_solver(pr, prec=prec)
+    s.setup_precond()
+    u, info = s.solve(tol=1e-8)
+    assert info["iters"] <= 40, info
+    if prec == 0:
+        assert abs(info["iters"] - it_oracle) <= 2, (info["iters"], it_oracle)
+    res = np.linalg.norm(P["b"] - P["A"] @ u.cpu().numpy()) / np.linalg.norm(P["b"][~P["mask"]])
+    assert res <= 1.5e-8
+    s.close()

@@ -273,6 +273,39 @@ def test_lmax_estimate_below_and_close_to_true():
     assert est >= 0.85 * lam_true
 
 
+@pytest.mark.parametrize("N", [16, 32])
+def test_lmax_estimate_covers_the_spectrum_on_uniform_media(N):
+    """Uniform conductivity: the top of the spectrum of D^-1 A is a dense cluster
+    at 3/2 (cubic Q1: the mode alternating along one axis).  From the seeded
+    start vector, 15 power iterations come within 7% of it, so the Chebyshev
+    interval's upper end 1.1 lmax covers the spectrum."""
+    import scipy.sparse as sp
+    grid = (N, N, N)
+    P = fem.build_problem(grid, (1.0 / N,) * 3, np.full(N ** 3, 0.3), 3.0, 1e-3, 1.0,
+                          W.dirichlet_patch_mask(grid), W.uniform_source(grid))
+    A = P["A"].tocsr()
+    D = A.diagonal()
+    free = (~P["mask"]).astype(float)
+    Dm = sp.diags(1 / np.sqrt(D))
+    lam_true = spla.eigsh(Dm @ A @ Dm, k=1, which="LA", return_eigenvectors=False)[0]
+    assert abs(lam_true - 1.5) < 1e-3
+    est = mmg.lmax_estimate(A, D, free, 15)
+    assert 0.93 * lam_true <= est <= lam_true * (1 + 1e-12)
+    assert 1.1 * est >= lam_true
+
+
+def test_mmg_pcg_converges_on_uniform_media():
+    """Regression: on a uniform density the multigrid-preconditioned CG converges
+    as fast as on a random one (an underestimated lmax made it stall)."""
+    N = 32
+    grid = (N, N, N)
+    P = fem.build_problem(grid, (1.0 / N,) * 3, np.full(N ** 3, 0.3), 3.0, 1e-3, 1.0,
+                          W.dirichlet_patch_mask(grid), W.uniform_source(grid))
+    H = mmg.MMG(P)
+    _, info = krylov.pcg(P["A"], P["b"], precond=H, u0=H.coarse_guess(P["b"]), tol=1e-8, maxit=200)
+    assert info["converged"] and info["iters"] <= 30, info["iters"]
+
+
 @pytest.mark.parametrize("m", [2, 3, 4])
 def test_chebyshev_smoother_is_scaled_chebyshev_polynomial(m):
     """The smoother's error propagation (r = A e*, start e = 0, error e* - e)
