@@ -431,6 +431,14 @@ extern "C" thermo_status thermo_set_density(thermo_ctx* ctx, const double* x, do
 
 // ---------------------------------------------------------------------------
 // preconditioner set-up (Sec. 3)
+// operator of the outer CG loop: float-float (FP64-accurate on the FP32 pipes)
+// or FP64 arithmetic, per opt.outer_apply
+static bool use_ds(const thermo_ctx* ctx) {
+  if (!fine_ds_supported(ctx->g)) return false;
+  if (ctx->opt.outer_apply == 2) return true;
+  if (ctx->opt.outer_apply == 1) return false;
+  return ctx->opt.prec != THERMO_FP64;
+}
 extern "C" thermo_status thermo_setup_precond(thermo_ctx* ctx) {
   if (!ctx) return THERMO_EINVAL;
   if (!ctx->have_density) return fail(ctx, THERMO_ESTATE, "setup_precond before set_density");
@@ -448,7 +456,8 @@ extern "C" thermo_status thermo_setup_precond(thermo_ctx* ctx) {
     // fine smoother coefficients
     const thermo_options& o = ctx->opt;
     if (o.smoother == 1) {
-      // lmax(D^-1 A) by power iteration from a fixed start vector (FP64)
+      // lmax(D^-1 A) by power iteration from the seeded start vector (FP64 vectors; the
+      // operator in FP64 arithmetic for the FP64 form, else the FP64-accurate float-float apply)
       CK(power_start(g, ctx->bits, ctx->p, st));
       CK(vec_dot(g, ctx->p, ctx->p, 0, ctx->red, ctx->dscal, st));
       CK(cudaMemcpyAsync(ctx->dscal_h, ctx->dscal, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -456,7 +465,10 @@ extern "C" thermo_status thermo_setup_precond(thermo_ctx* ctx) {
       CK(vec_scale(g, 1.0 / sqrt(ctx->dscal_h[0]), ctx->p, st));
       double lam = 0.0;
       for (int it = 0; it < o.power_iters; ++it) {
-        CK(fine_apply_f64(g, ctx->bits, ctx->k64, ctx->p, ctx->q, nullptr, nullptr, nullptr, st));
+        if (use_ds(ctx))
+          CK(fine_apply_ds(g, ctx->bits, ctx->k32, ctx->klo, ctx->p, ctx->q, nullptr, nullptr, nullptr, st));
+        else
+          CK(fine_apply_f64(g, ctx->bits, ctx->k64, ctx->p, ctx->q, nullptr, nullptr, nullptr, st));
         CK((fine_smooth<double, double>(g, ctx->bits, ctx->k64, ctx->q, nullptr, nullptr, ctx->p, 0.0, 1.0, st)));
         CK(vec_dot(g, ctx->p, ctx->p, 0, ctx->red, ctx->dscal, st));
         CK(cudaMemcpyAsync(ctx->dscal_h, ctx->dscal, sizeof(double), cudaMemcpyDeviceToHost, st));
@@ -566,14 +578,6 @@ const double* lvP<double>(Lev& l) { return l.Psi64; }
 template <>
 const float* lvP<float>(Lev& l) { return l.Psi32; }
 
-// operator of the outer CG loop: float-float (FP64-accurate on the FP32 pipes)
-// or FP64 arithmetic, per opt.outer_apply
-static bool use_ds(const thermo_ctx* ctx) {
-  if (!fine_ds_supported(ctx->g)) return false;
-  if (ctx->opt.outer_apply == 2) return true;
-  if (ctx->opt.outer_apply == 1) return false;
-  return ctx->opt.prec != THERMO_FP64;
-}
 static cudaError_t outer_apply_dot(thermo_ctx* ctx, const double* p, double* q, double* dot) {
   const Geom& g = ctx->g;
   if (use_ds(ctx))
