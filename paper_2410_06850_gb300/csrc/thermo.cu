@@ -1039,6 +1039,8 @@ extern "C" thermo_status thermo_vcycle(thermo_ctx* ctx, const double* r, double*
   } else {
     CK(unpack_nodes(g, ctx->z64, z, st));
   }
+  CK(cudaStreamSynchronize(st));
+  if (fine_stage_errors(true)) return fail(ctx, THERMO_ECUDA, "a fine-grid kernel timed out waiting for its TMA stage");
   return THERMO_OK;
 }
 
