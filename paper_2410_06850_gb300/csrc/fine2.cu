@@ -5,7 +5,8 @@
 // and the low-precision operator apply, for FP32 or BF16 storage with FP32
 // arithmetic on cubic elements.  A CTA owns 64 x TY nodes: one row per warp,
 // two neighbouring nodes per lane evaluated with packed f32x2 instructions,
-// marching over ZC planes.  One elected thread stages each plane of the
+// marching over one of NZ2 ragged z chunks (chosen so that the CTAs fill
+// whole waves of the GPU).  One elected thread stages each plane of the
 // iterate (with halo), of kappa, of the Dirichlet bits and of the centre
 // arrays r and e_prev with TMA tensor copies into an mbarrier ring (waits
 // bounded, failures flagged).  A ninth warp evaluates, from the same stages,
@@ -115,8 +116,8 @@ __global__ void __launch_bounds__(QNT, 3) q_tile(const __grid_constant__ QArgs<S
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int TY = g.TY;
   const int x0 = blockIdx.x * QTX, y0 = blockIdx.y * TY;
-  const int zs = blockIdx.z * g.ZC;
-  const int ze = (zs + g.ZC == g.Nz) ? g.Nz : zs + g.ZC - 1;
+  int zs, ze;
+  zchunk(g, g.NZ2, blockIdx.z, zs, ze);
   const int mx = (x0 >> 5) & ~3;
   const unsigned bytesV = (unsigned)((TY + 3) * W * sizeof(S)), bytesK = (unsigned)((TY + 2) * W * sizeof(S));
   const unsigned bytesM = (unsigned)((TY + 1) * QMW * 4), bytesR = (unsigned)((TY + 1) * QRW * sizeof(S));
@@ -176,23 +177,47 @@ __global__ void __launch_bounds__(QNT, 3) q_tile(const __grid_constant__ QArgs<S
   const float2 c0 = Q2(a.c0, a.c0), c3 = Q2(a.c3, a.c3);
   const bool lastx = x0 + QTX == g.Nx, lasty = y0 + TY == g.Ny;
 
+  // Values carried in registers from node plane t-1 to t (a warp marches in z
+  // over the same row): the element plane t-1 conductivities (kappa at x-1,
+  // x, x+1 of element rows y-1, y) and the iterate on node plane t (x-1 .. x+2
+  // of rows y-1, y, y+1), so that each step reads one new plane of each from
+  // shared memory instead of two of kappa and three of the iterate.
+  float ck[2][3], cv[3][4];
+  bool carried = false;
+
   // update of the two nodes (x0 + c, x0 + c + 1) of tile row r (0..TY) in node plane t
   auto pair_row = [&](int t, int r, int c) {
     const int sc = c + SX;
-    // conductivities k[a][b][s]: element plane t-1+a, element row y-1+b, side s
-    // (0: elements (x-1, x) of the two nodes, 1: elements (x, x+1))
-    float2 k[2][2][2];
+    // conductivities kf[a][b][.]: element plane t-1+a, element row y-1+b, x-1 / x / x+1
+    float kf[2][2][3];
 #pragma unroll
     for (int aa = 0; aa < 2; ++aa) {
+      if (aa == 0 && carried) {
+#pragma unroll
+        for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+          for (int q = 0; q < 3; ++q) kf[0][bb][q] = ck[bb][q];
+        continue;
+      }
       const S* kp = sK(t + aa);
 #pragma unroll
       for (int bb = 0; bb < 2; ++bb) {
         const int o = (r + bb) * W + sc;
         const float2 k01 = ld2<S>(kp + o);
-        k[aa][bb][0] = Q2(ldf<S>(kp + o - 1), k01.x);
-        k[aa][bb][1] = k01;
+        kf[aa][bb][0] = ldf<S>(kp + o - 1);
+        kf[aa][bb][1] = k01.x;
+        kf[aa][bb][2] = k01.y;
       }
     }
+    // k[a][b][s]: side s (0: elements (x-1, x) of the two nodes, 1: elements (x, x+1))
+    float2 k[2][2][2];
+#pragma unroll
+    for (int aa = 0; aa < 2; ++aa)
+#pragma unroll
+      for (int bb = 0; bb < 2; ++bb) {
+        k[aa][bb][0] = Q2(kf[aa][bb][0], kf[aa][bb][1]);
+        k[aa][bb][1] = Q2(kf[aa][bb][1], kf[aa][bb][2]);
+      }
     float2 zp[2][2], yp[2][2], xp[2][2];
 #pragma unroll
     for (int i = 0; i < 2; ++i)
@@ -205,20 +230,41 @@ __global__ void __launch_bounds__(QNT, 3) q_tile(const __grid_constant__ QArgs<S
     const float2 K8 = qadd(qadd(zp[0][0], zp[0][1]), qadd(zp[1][0], zp[1][1]));
     float2 Av = Q2(0.f, 0.f), ctr = Q2(0.f, 0.f);
     if (HV) {
-      float2 s = Q2(0.f, 0.f);
+      // vf[dz][dy][.]: iterate at x-1, x, x+1, x+2 of node plane t+dz, row y+dy
+      float vf[3][3][4];
 #pragma unroll
       for (int dz = -1; dz <= 1; ++dz) {
+        if (dz == 0 && carried) {
+#pragma unroll
+          for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+            for (int q = 0; q < 4; ++q) vf[1][dy][q] = cv[dy][q];
+          continue;
+        }
         const S* vp = sV(t + dz);
 #pragma unroll
         for (int dy = -1; dy <= 1; ++dy) {
           const int o = (r + 1 + dy) * W + sc;
           const float2 v01 = ld2<S>(vp + o);
+          vf[dz + 1][dy + 1][0] = ldf<S>(vp + o - 1);
+          vf[dz + 1][dy + 1][1] = v01.x;
+          vf[dz + 1][dy + 1][2] = v01.y;
+          vf[dz + 1][dy + 1][3] = ldf<S>(vp + o + 2);
+        }
+      }
+      float2 s = Q2(0.f, 0.f);
+#pragma unroll
+      for (int dz = -1; dz <= 1; ++dz) {
+#pragma unroll
+        for (int dy = -1; dy <= 1; ++dy) {
+          const float* vv = vf[dz + 1][dy + 1];
+          const float2 v01 = Q2(vv[1], vv[2]);
           if (dz == 0 && dy == 0) {
             ctr = v01;
             continue;
           }
-          const float2 vl = Q2(ldf<S>(vp + o - 1), v01.x);  // x - 1
-          const float2 vr = Q2(v01.y, ldf<S>(vp + o + 2));  // x + 1
+          const float2 vl = Q2(vv[0], vv[1]);  // x - 1
+          const float2 vr = Q2(vv[2], vv[3]);  // x + 1
           const int ia = dz < 0 ? 0 : 1, ib = dy < 0 ? 0 : 1;
           if (dz == 0) {  // xy face diagonals
             s = qfma(zp[ib][0], vl, s);
@@ -234,7 +280,16 @@ __global__ void __launch_bounds__(QNT, 3) q_tile(const __grid_constant__ QArgs<S
         }
       }
       Av = qfma(qmul(c0, K8), ctr, qmul(c3, s));
+#pragma unroll
+      for (int dy = 0; dy < 3; ++dy)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) cv[dy][q] = vf[2][dy][q];
     }
+#pragma unroll
+    for (int bb = 0; bb < 2; ++bb)
+#pragma unroll
+      for (int q = 0; q < 3; ++q) ck[bb][q] = kf[1][bb][q];
+    carried = true;
     float2 e;
     if (!SM) {
       e = Av;
@@ -350,7 +405,7 @@ cudaError_t q_launch(const QArgs<S, To>& a, cudaStream_t st) {
     return e;
   auto k = q_tile<S, To, OP, VAR>;
   cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LY::SMEM);
-  const dim3 grid(g.Nx / QTX, g.Ny / g.TY, g.Nz / g.ZC);
+  const dim3 grid(g.Nx / QTX, g.Ny / g.TY, g.NZ2);
   note_launch(), k<<<grid, QNT, LY::SMEM, st>>>(a, tm);
   return cudaGetLastError();
 }
@@ -371,6 +426,17 @@ QArgs<S, To> qargs(const Geom& g, const uint32_t* mask, const S* kap) {
 }  // namespace
 
 bool fine2_supported(const Geom& g) { return g.cube && g.Nx % QTX == 0 && g.TY <= QTY; }
+
+int fine2_tiles_xy(const Geom& g) { return (g.Nx / QTX) * (g.Ny / g.TY); }
+
+int fine2_ctas_per_sm() {
+  typedef QLay<float, true, true> LY;
+  auto k = q_tile<float, float, 1, 7>;
+  int n = 0;
+  cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)LY::SMEM);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k, QNT, LY::SMEM) != cudaSuccess) n = 0;
+  return n;
+}
 
 template <class S, class To>
 cudaError_t fine2_smooth(const Geom& g, const uint32_t* mask, const S* kap, const S* r, const S* e, const S* w, To* out,

@@ -20,7 +20,7 @@
 // elements have kappa = 0.  The result is as accurate as the FP64 sum form.
 //
 // Engine: a CTA owns 64 x TY nodes (two per lane, one row per warp) and marches
-// over ZC planes; one elected thread stages each plane of p (FP64), of kappa
+// over one of NZD ragged z chunks; one elected thread stages each plane of p (FP64), of kappa
 // (hi and lo floats) and of the Dirichlet bits with TMA tensor copies into an
 // mbarrier ring; all threads split the landed FP64 plane into hi/lo float
 // planes (integer arithmetic, no FP64 pipe) before the plane is used.  The
@@ -245,8 +245,8 @@ __global__ void __launch_bounds__(DNT, 2) ds_apply(const __grid_constant__ DsArg
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int TY = g.TY;
   const int x0 = blockIdx.x * DTX, y0 = blockIdx.y * TY;
-  const int zs = blockIdx.z * g.ZC;
-  const int ze = (zs + g.ZC == g.Nz) ? g.Nz : zs + g.ZC - 1;
+  int zs, ze;
+  zchunk(g, g.NZD, blockIdx.z, zs, ze);
   const int mx = (x0 >> 5) & ~3;
   const unsigned bytesV = (unsigned)((TY + 3) * DW * 8), bytesK = (unsigned)((TY + 2) * DW * 4);
   const unsigned bytesM = (unsigned)((TY + 1) * DMW * 4);
@@ -438,7 +438,16 @@ __global__ void __launch_bounds__(DNT, 2) ds_apply(const __grid_constant__ DsArg
 
 bool fine_ds_supported(const Geom& g) { return g.cube && g.Nx % DTX == 0 && g.TY <= DTY; }
 
-unsigned fine_ds_num_ctas(const Geom& g) { return (unsigned)(g.Nx / DTX) * (g.Ny / g.TY) * (g.Nz / g.ZC); }
+unsigned fine_ds_num_ctas(const Geom& g) { return (unsigned)(g.Nx / DTX) * (g.Ny / g.TY) * g.NZD; }
+
+int fine_ds_tiles_xy(const Geom& g) { return (g.Nx / DTX) * (g.Ny / g.TY); }
+
+int fine_ds_ctas_per_sm() {
+  int n = 0;
+  cudaFuncSetAttribute(ds_apply<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SMEM);
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, ds_apply<true>, DNT, SMEM) != cudaSuccess) n = 0;
+  return n;
+}
 
 cudaError_t fine_apply_ds(const Geom& g, const uint32_t* mask, const float* khi, const float* klo, const double* u,
                           double* y, double* partial, unsigned* counter, double* dot, cudaStream_t st) {
@@ -471,7 +480,7 @@ cudaError_t fine_apply_ds(const Geom& g, const uint32_t* mask, const float* khi,
   if ((e = get_map(&tm.m, mask, CU_TENSOR_MAP_DATA_TYPE_UINT32, 4, g.mwr, g.RYn, g.nz + 2, DMW, g.TY + 1)) !=
       cudaSuccess)
     return e;
-  const dim3 grid(g.Nx / DTX, g.Ny / g.TY, g.Nz / g.ZC);
+  const dim3 grid(g.Nx / DTX, g.Ny / g.TY, g.NZD);
   const long long nedge_nodes = (long long)(g.Ny + 1) * (g.Nz + 1) + (long long)g.Nx * (g.Nz + 1);
   const int eb = (int)std::min<long long>((nedge_nodes + 255) / 256, 512);
   a.nedge = dot ? eb : 0;

@@ -63,6 +63,8 @@ cudaError_t fine_prolong_add(const Geom& g, const double* phi, int L1, const dou
 // two-nodes-per-lane FP32-compute fine sweeps / applies (fine2.cu): cubic
 // elements, Nx a multiple of 64
 bool fine2_supported(const Geom& g);
+int fine2_tiles_xy(const Geom& g);  // CTAs per z chunk
+int fine2_ctas_per_sm();            // resident CTAs per SM of the FP32 sweep
 template <class S, class To>
 cudaError_t fine2_smooth(const Geom& g, const uint32_t* mask, const S* kap, const S* r, const S* e, const S* w, To* out,
                          float cA, float cB, cudaStream_t st);
@@ -71,6 +73,8 @@ cudaError_t fine2_apply(const Geom& g, const uint32_t* mask, const S* kap, const
 // float-float FP64-accurate fine apply (+ fused p.q when dot != NULL); see fine_ds.cu
 bool fine_ds_supported(const Geom& g);
 unsigned fine_ds_num_ctas(const Geom& g);
+int fine_ds_tiles_xy(const Geom& g);
+int fine_ds_ctas_per_sm();
 cudaError_t fine_apply_ds(const Geom& g, const uint32_t* mask, const float* khi, const float* klo, const double* u,
                           double* y, double* partial, unsigned* counter, double* dot, cudaStream_t st);
 cudaError_t vec_mask_dir(const Geom& g, const uint32_t* bits, double* v, cudaStream_t st);

@@ -136,6 +136,27 @@ static cudaError_t dalloc(thermo_ctx* ctx, T** p, size_t n) {
   return e;
 }
 
+// Number of ragged z chunks for a fine engine whose CTAs each own one of `tiles`
+// xy tiles and one chunk: the CTAs should fill whole waves of `slots` resident
+// CTAs (a last, partly filled wave runs at a fraction of the bandwidth), while
+// each chunk re-reads about one halo plane.  Chunks have at least 6 planes.
+static int balanced_zchunks(long long tiles, long long slots, int Nz) {
+  int best = 1;
+  double best_score = -1.0;
+  if (tiles < 1 || slots < 1) return Nz / 8 > 0 ? Nz / 8 : 1;
+  for (int n = 1; n <= Nz / 6 || n == 1; ++n) {
+    const double waves = (double)(tiles * n) / (double)slots;
+    const double fill = waves / std::ceil(waves);
+    const double len = (double)Nz / n;
+    const double score = fill * len / (len + 1.0);
+    if (score > best_score + 1e-12) {
+      best_score = score;
+      best = n;
+    }
+  }
+  return best;
+}
+
 static double now_ms() {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
@@ -278,6 +299,15 @@ extern "C" thermo_status thermo_create(const int grid[3], const double h[3], con
     }
   }
   if (!g.TX || !g.TY || !g.ZC) return fail(ctx, THERMO_EINVAL, "unsupported grid / block combination");
+  g.NZ2 = g.NZD = g.Nz / g.ZC;
+  {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 0;
+    if (sms > 0 && fine2_supported(g)) g.NZ2 = balanced_zchunks(fine2_tiles_xy(g), (long long)sms * fine2_ctas_per_sm(), g.Nz);
+    if (sms > 0 && fine_ds_supported(g))
+      g.NZD = balanced_zchunks(fine_ds_tiles_xy(g), (long long)sms * fine_ds_ctas_per_sm(), g.Nz);
+  }
   ctx->L1 = opt.nvec[0];
   ctx->nnode = (long long)g.nx * g.ny * g.nz;
   ctx->nelem = (long long)g.Nx * g.Ny * g.Nz;
@@ -373,7 +403,8 @@ extern "C" thermo_status thermo_create(const int grid[3], const double h[3], con
   CK(dalloc(ctx, &ctx->dscal, 16));
   CK(dalloc(ctx, &ctx->status_dev, 4));
   {
-    const unsigned nf = fine_num_ctas(g);
+    unsigned nf = fine_num_ctas(g);
+    if (fine_ds_supported(g) && fine_ds_num_ctas(g) + 512 > nf) nf = fine_ds_num_ctas(g) + 512;
     const long long np = (long long)(nf > 8192 ? nf : 8192) * 2;
     CK(dalloc(ctx, &ctx->red.partial, np));
     CK(dalloc(ctx, &ctx->red.counter, 4));
