@@ -39,7 +39,7 @@ FP64_NOMINAL_GFLOPS = 1250.0
 # workload (profiles/ summaries); None where no capture of the current kernel exists.
 # smooth: the three-term sweep with a staged previous iterate (7 of the 10 sweeps of a cycle);
 # apply_fp64: the float-float outer operator + p.Ap
-TRAFFIC = {"smooth": 315.894272e6 + 56.016896e6, "apply_fp64": 309.905920e6 + 109.324800e6}
+TRAFFIC = {"smooth": 315.739648e6 + 55.940096e6, "apply_fp64": None}
 
 
 def _peaks():

@@ -36,7 +36,7 @@ constexpr int QTY = 8;               // rows per tile (max), one warp each
 constexpr int QNT = 32 * (QTY + 1);  // + one warp for the closing column / row
 constexpr int QTX = 64;        // nodes per tile row (two per lane)
 constexpr int QMW = 8;         // staged mask words per row
-constexpr int QNS = 6;         // TMA ring stages (3 resident + 3 in flight)
+constexpr int QNS = 6;         // TMA ring stages (4 resident + 2 in flight)
 constexpr int QRW = 72;        // staged centre row width: x0 .. x0 + 71 (closing column included)
 
 template <class S>
@@ -171,8 +171,9 @@ __global__ void __launch_bounds__(QNT, 3) q_tile(const __grid_constant__ QArgs<S
     mbar_fence_init();
   }
   __syncthreads();
+  static_assert(QNS == 6, "the two-plane step keeps four groups resident and two in flight");
   if (tid == 0)
-    for (int q = zs - 1; q < zs - 1 + (QNS - 3); ++q) issue(q);
+    for (int q = zs - 1; q <= zs + 2; ++q) issue(q);
 
   const float2 c0 = Q2(a.c0, a.c0), c3 = Q2(a.c3, a.c3);
   const bool lastx = x0 + QTX == g.Nx, lasty = y0 + TY == g.Ny;
@@ -351,19 +352,33 @@ __global__ void __launch_bounds__(QNT, 3) q_tile(const __grid_constant__ QArgs<S
     Cv<To>::st(a.out + nidx(g, xx, yy, t), e);
   };
 
-  for (int t = zs - 2; t <= ze; ++t) {
-    wait_group(t + 1);
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-      issue(t + QNS - 2);
-    }
-    if (t < zs) continue;
+  auto plane = [&](int t) {
     if (w < TY) {
       pair_row(t, w, 2 * lane);
     } else if (w == QTY) {  // extra warp: closing column (lanes = rows) and closing row
       if (lastx && (lane < TY || (lasty && lane == TY))) col_node(t, lane);
       if (lasty) pair_row(t, TY, 2 * lane);
+    }
+  };
+  // Two node planes per CTA barrier: a step reads groups t-1 .. t+2 and, once
+  // every warp has left the previous step (which read t-3 .. t), refills the
+  // two stages that step released with groups t+3 and t+4.
+  for (int t = zs; t <= ze; t += 2) {
+    if (t == zs) {
+      wait_group(zs - 1);
+      wait_group(zs);
+    }
+    wait_group(t + 1);
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+      issue(t + 3);
+      issue(t + 4);
+    }
+    plane(t);
+    if (t + 1 <= ze) {
+      wait_group(t + 2);
+      plane(t + 1);
     }
   }
 }
