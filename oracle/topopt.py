@@ -9,8 +9,11 @@ are the textbook SIMP harness used to drive repeated solves:
 * OC: x_new = clip(x * (-dc / (lambda dv))^eta, x - move, x + move) within
   [0, 1]; lambda by bisection so that the filtered volume fraction hits V*.
 
-Parity unpinned beyond the linear-algebra identities checked in tests
-(filter rows sum to one, transpose identity, volume hit by the bisection).
+Pinned by tests/test_oracle_topopt.py: the filter against a brute-force
+loop over element pairs on tiny grids (plus row sums, identity at radius
+<= 1, transpose); the OC step against its closed form on uniform
+sensitivities, its box and move limits, the volume it reaches and the
+optimality form shared by all unclipped elements.
 """
 from __future__ import annotations
 
