@@ -11,7 +11,7 @@ CG), and the adjoint sensitivity.  `value` is the mean solve time in seconds
 (the headline metric); set-up, iterations, the FP64 form and the BF16
 smoother variant, per-kernel timings and the roofline of the dominant kernel
 are reported beside it.  Inputs are resident in HBM; the working set
-(~3 GB per context) is far larger than L2, so no flush is needed.
+(~7 GB per context) is far larger than L2, so no flush is needed.
 
 --impl reference times the FP64 CPU oracle (test infrastructure) on a
 bounded sample of the same workload family and scales it to the metric.
@@ -148,6 +148,25 @@ def cpu_baseline(iters256, name="chan64"):
             "oracle": o}
 
 
+def rank_barrier(dist, cuda=True):
+    """Barrier over the replica ranks, then a device synchronisation."""
+    if dist is not None:
+        dist.barrier()
+    if cuda:
+        import torch
+        torch.cuda.synchronize()
+
+
+def max_over_ranks(v, dist, device="cuda"):
+    """The largest of the ranks' values: the job's time is its slowest replica's."""
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return 0
@@ -282,16 +301,10 @@ def main():
         return u, dc, info, dict(setup=t1 - t0, solve=t2 - t1, sens=t3 - t2, step=t3 - t0)
 
     def barrier():
-        if dist is not None:
-            dist.barrier()
-        torch.cuda.synchronize()
+        rank_barrier(dist)
 
     def maxr(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return max_over_ranks(v, dist)
 
     if args.kernels_only:
         res = {}
