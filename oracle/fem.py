@@ -129,6 +129,46 @@ def build_problem(grid, h, x, p, kmin, kmax, mask, source, values=None):
                 mass=lumped_kappa_mass(grid, h, kappa))
 
 
+def operator_rows(grid, h, kappa, mask, u, rows, absolute=False, chunk=1 << 21) -> np.ndarray:
+    """(A u)_i on the listed nodes i for the Dirichlet-eliminated operator
+    A = P_F A_N P_F + P_D of Sec. 2.2 Eq. (5) with the Gamma_D data of Sec. 2.1,
+    evaluated row by row from the element matrices, without assembling A: a
+    free row sums kappa_e K0[a, b] u_b over the (up to) eight elements e that
+    contain node i (as their local node a) and over their free nodes b; a
+    Dirichlet row returns u_i.  absolute=True evaluates (|A| |u|)_i, the scale
+    of a row's rounding error.  Serves spot checks of outputs too large for
+    the assembled matrix.
+    """
+    Nx, Ny, Nz = grid
+    nx, ny = Nx + 1, Ny + 1
+    K0 = element_matrix(h)
+    if absolute:
+        K0 = np.abs(K0)
+    kappa = np.asarray(kappa, dtype=np.float64)
+    mask = np.asarray(mask).astype(bool)
+    u = np.asarray(u, dtype=np.float64)
+    if absolute:
+        u = np.abs(u)
+    rows = np.asarray(rows, dtype=np.int64).reshape(-1)
+    out = np.empty(rows.size)
+    for c0 in range(0, rows.size, chunk):
+        r = rows[c0:c0 + chunk]
+        ix, iy, iz = r % nx, (r // nx) % ny, r // (nx * ny)
+        y = np.zeros(r.size)
+        for a in range(8):
+            ax, ay, az = a & 1, (a >> 1) & 1, (a >> 2) & 1
+            ex, ey, ez = ix - ax, iy - ay, iz - az
+            ok = (ex >= 0) & (ey >= 0) & (ez >= 0) & (ex < Nx) & (ey < Ny) & (ez < Nz)
+            ke = np.where(ok, kappa[np.where(ok, ex + Nx * (ey + Ny * ez), 0)], 0.0)
+            for b in range(8):
+                bx, by, bz = b & 1, (b >> 1) & 1, (b >> 2) & 1
+                nb = np.where(ok, (ex + bx) + nx * ((ey + by) + ny * (ez + bz)), 0)
+                ub = np.where(mask[nb], 0.0, u[nb])
+                y += ke * (K0[a, b] * ub)
+        out[c0:c0 + r.size] = np.where(mask[r], u[r], y)
+    return out
+
+
 def compliance(f, u) -> float:
     """c = f^T u; for q = 1 on the unit cube this equals int u_h dV, the mean
     temperature of Sec. 2.3 Eq. (6) (sum_i phi_i = 1)."""
