@@ -484,7 +484,7 @@ def main():
     dk = klass[dom]
     if dom == "apply_fp64":
         # FP64 ALU bound: algorithmic flops (2 per stored-matrix nonzero of the row) against the
-        # nominal FP64 rate (no measured FP64 peak exists for this machine)
+        # nominal FP64 rate (no measured FP64 peak is available)
         ach = dk["flops_per_launch"] / (dk["ms_per_launch"] * 1e-3) / 1e9
         roof = {"kernel": "fine FP64 Q1 apply + fused p.Ap (CG loop)", "bound": "alu", "achieved": ach,
                 "peak": FP64_NOMINAL_GFLOPS, "unit": "GFLOP/s", "frac": ach / FP64_NOMINAL_GFLOPS,

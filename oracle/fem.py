@@ -7,7 +7,7 @@ scipy sparse matrices.
 Paper anchors
   * SIMP conductivity, Sec. 2.1 Eq. (1):  kappa = kL + x^p (kH - kL).
   * Linear system A t = f, Sec. 2.2 Eq. (5).  The paper discretises with TPFA
-    finite volumes; this build uses trilinear nodal elements on the same
+    finite volumes; this oracle uses trilinear nodal elements on the same
     structured grid (one unknown per grid node), which keeps the system SPD
     with the same SIMP law and the same Dirichlet/Neumann boundary data.
   * Objective and adjoint, Sec. 2.3 Eqs. (6)-(7): for the compliance
