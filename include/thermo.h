@@ -247,7 +247,10 @@ thermo_status thermo_apply_dot(thermo_ctx *ctx, const double *p, double *q, doub
 
 /* z = B r: one MMG V-cycle (Algorithm 1) in the context's precision.
  * r, z: device double[nodes]; entries of r on Gamma_D are ignored (treated as
- * zero) and z vanishes there.  Requires setup_precond. */
+ * zero) and z vanishes there.  Requires setup_precond (THERMO_ESTATE
+ * otherwise).  Synchronises the stream; THERMO_ECUDA if a fine-grid kernel gave
+ * up waiting for one of its staged planes (bounded wait; the context stays
+ * usable). */
 thermo_status thermo_vcycle(thermo_ctx *ctx, const double *r, double *z);
 
 /* The assembled load vector f (device double[nodes]). */
