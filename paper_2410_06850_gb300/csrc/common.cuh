@@ -16,6 +16,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "zchunks.h"
+
 namespace thermo {
 
 typedef __nv_bfloat16 bf16;
@@ -40,13 +42,6 @@ struct Geom {
   int TX, TY, ZC;           // tile width / height, z planes per CTA chunk
   int NZ2, NZD;             // z chunks (ragged) of the two-nodes-per-lane and float-float engines
 };
-
-// z chunk k of n (ragged, lengths differ by at most one plane): node planes zs..ze;
-// the last chunk also takes the closing plane Nz
-__host__ __device__ __forceinline__ void zchunk(const Geom& g, int n, int k, int& zs, int& ze) {
-  zs = (int)(((long long)k * g.Nz) / n);
-  ze = (k == n - 1) ? g.Nz : (int)(((long long)(k + 1) * g.Nz) / n) - 1;
-}
 
 __host__ __device__ __forceinline__ long long nidx(const Geom& g, int x, int y, int z) {
   return g.base + ((long long)(z + 1) * g.RYn + (y + 1)) * g.P + x;

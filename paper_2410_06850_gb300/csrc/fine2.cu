@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(QNT, 3) q_tile(const __grid_constant__ QArgs<S
   const int TY = g.TY;
   const int x0 = blockIdx.x * QTX, y0 = blockIdx.y * TY;
   int zs, ze;
-  zchunk(g, g.NZ2, blockIdx.z, zs, ze);
+  zchunk(g.Nz, g.NZ2, blockIdx.z, zs, ze);
   const int mx = (x0 >> 5) & ~3;
   const unsigned bytesV = (unsigned)((TY + 3) * W * sizeof(S)), bytesK = (unsigned)((TY + 2) * W * sizeof(S));
   const unsigned bytesM = (unsigned)((TY + 1) * QMW * 4), bytesR = (unsigned)((TY + 1) * QRW * sizeof(S));

@@ -246,7 +246,7 @@ __global__ void __launch_bounds__(DNT, 2) ds_apply(const __grid_constant__ DsArg
   const int TY = g.TY;
   const int x0 = blockIdx.x * DTX, y0 = blockIdx.y * TY;
   int zs, ze;
-  zchunk(g, g.NZD, blockIdx.z, zs, ze);
+  zchunk(g.Nz, g.NZD, blockIdx.z, zs, ze);
   const int mx = (x0 >> 5) & ~3;
   const unsigned bytesV = (unsigned)((TY + 3) * DW * 8), bytesK = (unsigned)((TY + 2) * DW * 4);
   const unsigned bytesM = (unsigned)((TY + 1) * DMW * 4);

@@ -136,27 +136,6 @@ static cudaError_t dalloc(thermo_ctx* ctx, T** p, size_t n) {
   return e;
 }
 
-// Number of ragged z chunks for a fine engine whose CTAs each own one of `tiles`
-// xy tiles and one chunk: the CTAs should fill whole waves of `slots` resident
-// CTAs (a last, partly filled wave runs at a fraction of the bandwidth), while
-// each chunk re-reads about one halo plane.  Chunks have at least 6 planes.
-static int balanced_zchunks(long long tiles, long long slots, int Nz) {
-  int best = 1;
-  double best_score = -1.0;
-  if (tiles < 1 || slots < 1) return Nz / 8 > 0 ? Nz / 8 : 1;
-  for (int n = 1; n <= Nz / 6 || n == 1; ++n) {
-    const double waves = (double)(tiles * n) / (double)slots;
-    const double fill = waves / std::ceil(waves);
-    const double len = (double)Nz / n;
-    const double score = fill * len / (len + 1.0);
-    if (score > best_score + 1e-12) {
-      best_score = score;
-      best = n;
-    }
-  }
-  return best;
-}
-
 static double now_ms() {
   return std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now().time_since_epoch()).count();
 }
