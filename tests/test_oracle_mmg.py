@@ -11,7 +11,9 @@ the method's definition and by linear algebra:
 * the algorithmic V-cycle (Algorithm 1) equals its closed product form built
   here from dense matrices, is symmetric and positive definite;
 * the coarse initial guess is Galerkin-orthogonal: P^T (b - A u0) = 0;
-* MMG-PCG reproduces a direct solve.
+* MMG-PCG reproduces a direct solve;
+* the l1-block-Jacobi smoother: D_l1 - A is SPSD, so the spectrum of
+  D_l1^-1 A lies in (0, 1].
 """
 import numpy as np
 import pytest
@@ -366,3 +368,30 @@ def test_vcycle_closed_form_with_chebyshev():
         ej = np.zeros(A.shape[0])
         ej[j] = 1.0
         np.testing.assert_allclose(H(ej)[free], B[free, j], rtol=1e-9, atol=1e-12 * np.abs(B).max())
+
+
+def test_l1_block_jacobi_is_convergent_without_damping():
+    """The l1-block-Jacobi smoother of the coarse levels (Baker, Falgout, Kolev
+    and Yang, 2011): D_l1 = A_cc + diag(sum of the off-cell |a_ij|) makes
+    D_l1 - A symmetric positive semidefinite (a symmetric diagonally dominant
+    matrix with a nonnegative diagonal), so the spectrum of D_l1^-1 A lies in
+    (0, 1] and one undamped sweep reduces the error in the A-norm.  With no
+    off-cell couplings (one cell) D_l1 = A and the sweep is exact."""
+    P = _prob(N=16, density="chan", kmin=1e-6)
+    H = mmg.MMG(P, mmg.MMGOptions(block=4, nvec=(4, 17), group=(2,), smoother="chebyshev"))
+    lev = H.levels[0]
+    A = lev.A.toarray()
+    L = lev.L
+    D = np.zeros_like(A)
+    for c, Dinv in enumerate(lev.smoother):
+        s = slice(c * L, (c + 1) * L)
+        D[s, s] = np.linalg.inv(Dinv)
+    act = np.flatnonzero(lev.active)
+    A, D = A[np.ix_(act, act)], D[np.ix_(act, act)]
+    assert np.abs(D - D.T).max() <= 1e-12 * np.abs(D).max()
+    assert np.linalg.eigvalsh(D - A).min() >= -1e-12 * np.abs(A).max()
+    ev = np.linalg.eigvals(np.linalg.solve(D, A)).real
+    assert ev.min() > 0.0 and ev.max() <= 1.0 + 1e-10
+    # a single cell: the l1 block is the whole operator
+    one = mmg.l1_block_inverses(lev.A[:L, :L], (1, 1, 1), L)[0]
+    np.testing.assert_allclose(one @ lev.A[:L, :L].toarray(), np.eye(L), atol=1e-10)
