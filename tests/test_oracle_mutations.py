@@ -1,0 +1,117 @@
+"""The oracle's pins catch plausible mistakes.  Each case plants one mistake in
+the oracle on the CPU (a dropped term, a wrong sign, a wrong exponent or index,
+a missing normalisation or elimination), re-runs the pins that guard that
+function, and requires that at least one of them fails.  The oracle itself is
+restored after each case (pytest monkeypatch).
+"""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+import test_oracle_fem as F
+import test_oracle_mmg as G
+import test_oracle_topopt as T
+from oracle import fem, mmg, topopt
+
+_K1 = np.array([[1.0, -1.0], [-1.0, 1.0]])
+_M1 = np.array([[1.0 / 3.0, 1.0 / 6.0], [1.0 / 6.0, 1.0 / 3.0]])
+_orig = {"element_matrix": fem.element_matrix, "simp_kappa": fem.simp_kappa, "load_vector": fem.load_vector,
+         "sensitivity": fem.sensitivity, "filter_matrix": topopt.filter_matrix}
+
+
+def k_dropped_term(h):
+    hx, hy, hz = (float(v) for v in h)
+    return (hy * hz / hx) * np.kron(_M1, np.kron(_M1, _K1)) + (hx * hz / hy) * np.kron(_M1, np.kron(_K1, _M1))
+
+
+def k_axes_swapped(h):
+    # the x and z factors exchanged (local index read as az + 2ay + 4ax)
+    hx, hy, hz = (float(v) for v in h)
+    K = (hy * hz / hx) * np.kron(_K1, np.kron(_M1, _M1))
+    K += (hx * hz / hy) * np.kron(_M1, np.kron(_K1, _M1))
+    K += (hx * hy / hz) * np.kron(_M1, np.kron(_M1, _K1))
+    return K
+
+
+def kappa_wrong_exponent(x, p, kmin, kmax):
+    return _orig["simp_kappa"](x, p - 1.0, kmin, kmax)
+
+
+def load_double_weight(grid, h, source):
+    return 2.0 * _orig["load_vector"](grid, h, source)
+
+
+def sensitivity_wrong_sign(grid, h, x, p, kmin, kmax, u):
+    return -_orig["sensitivity"](grid, h, x, p, kmin, kmax, u)
+
+
+def sensitivity_wrong_power(grid, h, x, p, kmin, kmax, u):
+    x = np.asarray(x, float)
+    return -p * x ** p * (kmax - kmin) * fem.element_energy(grid, h, u)
+
+
+def dirichlet_rows_only(A_neu, f, mask, values=None):
+    # identity rows on Gamma_D but the Dirichlet columns kept in the free rows
+    mask = np.asarray(mask).astype(bool)
+    free = (~mask).astype(np.float64)
+    A = (sp.diags(free) @ A_neu + sp.diags(mask.astype(np.float64))).tocsr()
+    return A, free * f
+
+
+def filter_unnormalised(N, rmin):
+    H = _orig["filter_matrix"](N, rmin)
+    H = H.tocoo()
+    # rows scaled by their neighbour counts: they no longer sum to one
+    w = np.zeros(N ** 3)
+    np.add.at(w, H.row, H.data > 0)
+    return sp.csr_matrix((H.data * w[H.row], (H.row, H.col)), shape=H.shape)
+
+
+def l1_without_abs(A, shape, L):
+    A = A.tocsr()
+    ncell = shape[0] * shape[1] * shape[2]
+    rows = np.asarray(A.sum(axis=1)).ravel()
+    out = []
+    for c in range(ncell):
+        d = np.arange(c * L, (c + 1) * L)
+        D = A[d][:, d].toarray()
+        inside = np.asarray(A[d][:, d].sum(axis=1)).ravel()
+        out.append(np.linalg.inv(D + np.diag(rows[d] - inside)))
+    return out
+
+
+CASES = {
+    "element matrix drops a term": (fem, "element_matrix", k_dropped_term,
+                                    [lambda: F.test_element_matrix_matches_gauss_quadrature((0.3, 0.5, 0.7)),
+                                     F.test_element_matrix_cube_closed_form]),
+    "element matrix axes swapped": (fem, "element_matrix", k_axes_swapped,
+                                    [lambda: F.test_element_matrix_matches_gauss_quadrature((0.3, 0.5, 0.7))]),
+    "SIMP exponent p - 1": (fem, "simp_kappa", kappa_wrong_exponent,
+                            [F.test_sensitivity_euler_identity, F.test_sensitivity_central_finite_differences]),
+    "load vector weight": (fem, "load_vector", load_double_weight,
+                           [F.test_load_vector_integrates_source, F.test_compliance_energy_identity_and_mean_temperature]),
+    "sensitivity sign": (fem, "sensitivity", sensitivity_wrong_sign,
+                         [F.test_sensitivity_euler_identity, F.test_sensitivity_central_finite_differences]),
+    "sensitivity power p": (fem, "sensitivity", sensitivity_wrong_power,
+                            [F.test_sensitivity_euler_identity, F.test_sensitivity_central_finite_differences]),
+    "Dirichlet columns kept": (fem, "dirichlet_system", dirichlet_rows_only,
+                               [F.test_operator_symmetric_spd_zero_rowsums_mmatrix]),
+    "filter rows not normalised": (topopt, "filter_matrix", filter_unnormalised,
+                                   [lambda: T.test_filter_matches_brute_force(3, 1.5),
+                                    T.test_filter_rows_sum_to_one_and_transpose]),
+    "l1 smoother without |a_ij|": (mmg, "l1_block_inverses", l1_without_abs,
+                                   [G.test_l1_block_jacobi_is_convergent_without_damping]),
+}
+
+
+@pytest.mark.parametrize("name", list(CASES))
+def test_pins_catch_a_planted_mistake(monkeypatch, name):
+    mod, attr, bad, pins = CASES[name]
+    monkeypatch.setattr(mod, attr, bad)
+    caught = 0
+    for pin in pins:
+        try:
+            pin()
+        except (AssertionError, np.linalg.LinAlgError):
+            caught += 1
+    assert caught >= 1, f"no pin caught: {name}"
