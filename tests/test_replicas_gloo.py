@@ -1,7 +1,8 @@
 """Replica runs (one independent problem per rank, no collective on the data
 path): the bench's timing aggregation over two gloo ranks on the CPU (every
-rank learns the slowest replica's time after the barrier), and the reference
-arm's rank handling (rank 0 alone works and prints; the others exit 0)."""
+rank learns the slowest replica's time after the barrier), the reference
+arm's rank handling (rank 0 alone works and prints; the others exit 0), and
+the keys of the reference arm's JSON line."""
 import argparse
 import socket
 
@@ -43,3 +44,20 @@ def test_reference_arm_runs_on_rank_zero_only(capsys):
     args = argparse.Namespace(steps=1, warmup=0, gpus=2, ref_iters=86)
     assert bench.run_reference(args, 1, 2) == 0
     assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_json_line(capsys):
+    """The reference arm's one JSON line (the oracle timed on the host cores) has
+    the keys the benchmark contract names, the main arm's metric and unit, and
+    an e2e object with no host-device traffic."""
+    import json
+    args = argparse.Namespace(steps=1, warmup=0, gpus=1, ref_iters=86)
+    assert bench.run_reference(args, 0, 1) == 0
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+              "scaling", "vs_baseline", "dtype", "data", "config", "impl", "cpu_baseline", "e2e"):
+        assert k in line, k
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC and line["unit"] == "s"
+    assert line["higher_is_better"] is False and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["value"] == line["value"]
+    assert line["e2e"] == {"value": line["value"], "unit": "s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}
