@@ -140,7 +140,9 @@ typedef struct {
  * grid is not a multiple of 4 in each axis. */
 thermo_status thermo_default_options(const int grid[3], thermo_options *opt);
 
-/* Create a solver context.
+/* Create a solver context for the steady heat problem of Sec. 2.1 (Dirichlet
+ * data on Gamma_D, adiabatic elsewhere, element heat source) discretised as the
+ * linear system of Sec. 2.2 Eq. (5).
  *   grid[3]          host: Nx, Ny, Nz (each a multiple of opt->block and
  *                    Nx/b etc. a multiple of the product of the group sizes)
  *   h[3]             host: element edge lengths (> 0)
@@ -173,7 +175,10 @@ thermo_status thermo_set_density(thermo_ctx *ctx, const double *x, double p,
  * that the context is ready. */
 thermo_status thermo_setup_precond(thermo_ctx *ctx);
 
-/* Solve A u = b to ||b - A u||_2 <= tol ||b_F||_2, where b_F is b on the free
+/* Solve the system of Sec. 2.2 Eq. (5) with CG preconditioned by the cycle of
+ * Sec. 3 Algorithm 1 (the state solve LS1 of Sec. 4), started from the
+ * interpolated coarse solution (opt.guess).
+ * Solve A u = b to ||b - A u||_2 <= tol ||b_F||_2, where b_F is b on the free
  * (non-Dirichlet) nodes; the Dirichlet rows are identities satisfied exactly
  * by every iterate.  Checked on the recursive residual, confirmed on the true
  * FP64 residual at exit.
@@ -223,15 +228,17 @@ thermo_status thermo_dot_noalloc(const double *x, const double *y, long long n, 
  * u device double[nodes]; c host double*.  Synchronises the stream. */
 thermo_status thermo_compliance(thermo_ctx *ctx, const double *u, double *c);
 
-/* Last error message of this context (never NULL). */
+/* Last error message of this context (never NULL).  Context management: no
+ * counterpart in the paper. */
 const char *thermo_last_error(const thermo_ctx *ctx);
 
-/* Release every device and host resource of the context (NULL is a no-op). */
+/* Release every device and host resource of the context (NULL is a no-op).
+ * Context management: no counterpart in the paper. */
 void thermo_destroy(thermo_ctx *ctx);
 
 /* ---- Inspection and building blocks (tests, benchmarks, the SIMP harness) */
 
-/* y = A u with the Dirichlet-eliminated operator (identity rows on Gamma_D,
+/* y = A u with the Dirichlet-eliminated operator of Sec. 2.2 Eq. (5) (identity rows on Gamma_D,
  * no coupling to Gamma_D columns), in the given arithmetic:
  * THERMO_FP64 (FP64), THERMO_MIXED (FP32 data and math) or
  * THERMO_MIXED_BF16S (BF16 data, FP32 math).  u, y: device double[nodes]. */
@@ -253,16 +260,20 @@ thermo_status thermo_apply_dot(thermo_ctx *ctx, const double *p, double *q, doub
  * usable). */
 thermo_status thermo_vcycle(thermo_ctx *ctx, const double *r, double *z);
 
-/* The assembled load vector f (device double[nodes]). */
+/* The assembled load vector f, the right-hand side of Sec. 2.2 Eq. (5) before
+ * the Dirichlet lifting (device double[nodes]). */
 thermo_status thermo_load_vector(thermo_ctx *ctx, double *f);
 
-/* Hierarchy description (host outputs, any may be NULL):
+/* The coarse spaces of Sec. 3 (Eq. (8) on level 1, Eq. (9) above), one entry
+ * per coarse level.  Hierarchy description (host outputs, any may be NULL):
  * nlevels (coarse levels), cells[l*3+k] cells per axis of level l+1,
  * nvec[l], ndof[l] = cells * nvec. */
 thermo_status thermo_hierarchy(const thermo_ctx *ctx, int *nlevels, int *cells,
                                int *nvec, long long *ndof);
 
-/* Copy level data out (device double outputs, FP64 masters):
+/* Copy level data of Sec. 3 out (bases of Eq. (8) / Eq. (9), Galerkin
+ * operators, local eigenvalues, the coarsest inverse of Algorithm 1's direct
+ * solve) (device double outputs, FP64 masters):
  *   what = 0: basis of level `level` — level 1: Phi as double[nodes][L_1]
  *             (natural node order); level l >= 2: Psi as
  *             double[cells_l][g^3 L_{l-1}][L_l] (rows in the group's local
@@ -283,7 +294,8 @@ thermo_status thermo_export_level(thermo_ctx *ctx, int level, int what,
 thermo_status thermo_filter(thermo_ctx *ctx, const double *in, double *out,
                             double rmin, int transpose);
 
-/* Optimality-criteria update with bisection on the multiplier so that the
+/* Optimality-criteria update (textbook SIMP harness; the paper's Sec. 2.3
+ * uses MMA) with bisection on the multiplier so that the
  * filtered volume fraction hits volfrac: x (device double[M], in/out),
  * dc, dv device double[M].  change (host, may be NULL) receives
  * max |x_new - x_old|. */
@@ -291,16 +303,19 @@ thermo_status thermo_oc_update(thermo_ctx *ctx, double *x, const double *dc,
                                const double *dv, double volfrac, double move,
                                double rmin, double *change);
 
-/* Relative recursive residuals ||r_k|| / ||b_F|| of the last thermo_solve, one
+/* Convergence history of the CG iteration of Sec. 4.
+ * Relative recursive residuals ||r_k|| / ||b_F|| of the last thermo_solve, one
  * per convergence check (every opt.check_every iterations); copies at most
  * max of them to out (host, may be NULL) and returns how many exist. */
 int thermo_residual_history(const thermo_ctx *ctx, double *out, int max);
 
 /* Number of kernel launches this library has issued in the process (host
- * counter; for launch accounting in benchmarks). */
+ * counter; for launch accounting in benchmarks; measurement support, no
+ * counterpart in the paper). */
 long long thermo_launch_count(void);
 
-/* Benchmark one internal kernel: `reps` back-to-back launches on the
+/* Measurement support (no counterpart in the paper).
+ * Benchmark one internal kernel: `reps` back-to-back launches on the
  * context's own buffers, timed with CUDA events on the context stream.
  *   which: 0 the outer CG loop's apply (+ fused p.Ap; float-float or FP64
  *          per opt.outer_apply), 1 FP32 apply, 2 BF16 apply,
@@ -330,8 +345,8 @@ thermo_status thermo_bench_kernel(thermo_ctx *ctx, int which, int reps, double *
  *   THERMO_KT_COARSE   everything below the fine grid in one V-cycle
  *   THERMO_KT_CGVEC    CG vector kernels (update, beta, direction, conversion)
  * bytes/flops are the algorithmic DRAM bytes and floating-point operations of
- * the timed launches (see the kernel descriptions in the design notes):
- * compulsory traffic of each array once, 0 where not defined (coarse). */
+ * the timed launches: compulsory traffic of each array once, 0 where not
+ * defined (coarse). */
 enum {
   THERMO_KT_APPLY64 = 0,
   THERMO_KT_SMOOTH = 1,
