@@ -5,6 +5,7 @@
 
 #include "common.cuh"
 #include "kernels.h"
+#include "splitmix.h"
 
 namespace thermo {
 
@@ -692,18 +693,10 @@ cudaError_t vec_copy_dir(const Geom& g, const uint32_t* bits, const double* src,
 }
 
 // seeded start vector of the power iteration: u_i - 1/2 at the natural node index i,
-// u_i the SplitMix64 uniform of stream POWER_SEED (state (seed 2^32 + i + 1) times the
-// golden gamma, then the standard finaliser; 53 bits), zero on Dirichlet nodes.  A
-// random start has weight on the top of the spectrum of D^-1 A, which a smooth or
-// periodic start lacks on uniform media.
+// u_i the SplitMix64 uniform of stream POWER_SEED (splitmix.h; 53 bits), zero on
+// Dirichlet nodes.  A random start has weight on the top of the spectrum of D^-1 A,
+// which a smooth or periodic start lacks on uniform media.
 constexpr unsigned long long POWER_SEED = 101ull;
-__device__ __forceinline__ double splitmix_u01(unsigned long long seed, unsigned long long i) {
-  unsigned long long z = (seed * (1ull << 32) + i + 1ull) * 0x9E3779B97F4A7C15ull;
-  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-  z = z ^ (z >> 31);
-  return (double)(z >> 11) * (1.0 / 9007199254740992.0);
-}
 __global__ void k_power_start(Geom g, const uint32_t* __restrict__ bits, double* __restrict__ v) {
   const long long n = (long long)g.nx * g.ny * g.nz;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
