@@ -16,6 +16,7 @@
 #include "../../include/thermo.h"
 #include "common.cuh"
 #include "kernels.h"
+#include "chebyshev.h"
 
 using namespace thermo;
 
@@ -489,18 +490,8 @@ extern "C" thermo_status thermo_setup_precond(thermo_ctx* ctx) {
       }
       ctx->lmax = lam;
       // Chebyshev on [lmax/ratio, 1.1 lmax]: three-term recurrence coefficients
-      const double lo = lam / o.cheb_ratio, hi = 1.1 * lam;
-      const double theta = 0.5 * (hi + lo), delta = 0.5 * (hi - lo), sigma = theta / delta;
-      double rho = 1.0 / sigma;
       ctx->nsweep = o.cheb_degree;
-      ctx->sa[0] = 0.0;
-      ctx->sb[0] = 1.0 / theta;
-      for (int k = 1; k < o.cheb_degree; ++k) {
-        const double rn = 1.0 / (2.0 * sigma - rho);
-        ctx->sa[k] = rn * rho;
-        ctx->sb[k] = 2.0 * rn / delta;
-        rho = rn;
-      }
+      chebyshev_coefficients(lam, o.cheb_ratio, o.cheb_degree, ctx->sa, ctx->sb);
       CK(cudaMemsetAsync(ctx->p, 0, g.nsize * sizeof(double), st));
       CK(cudaMemsetAsync(ctx->q, 0, g.nsize * sizeof(double), st));
     } else {
