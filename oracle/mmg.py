@@ -254,14 +254,22 @@ def coarse_level_basis(prob, Pcomp, fine_cell, prev_shape, prev_L, prev_active,
     rows, cols, vals = [], [], []
     active = np.zeros(ngrp * L, dtype=bool)
     eigs = []
+    # members of every group in increasing index order (a stable sort by group id
+    # lists the same indices as a scan for each id, in one pass)
+    cell_order = np.argsort(cell_group, kind="stable")
+    cell_start = np.concatenate([[0], np.cumsum(np.bincount(cell_group, minlength=ngrp))])
+    fine_order = np.argsort(fine_group, kind="stable")
+    n_dir = int(np.sum(fine_group < 0))
+    fine_start = n_dir + np.concatenate([[0], np.cumsum(np.bincount(fine_group[fine_group >= 0],
+                                                                     minlength=ngrp))])
     for G in range(ngrp):
-        cells = np.flatnonzero(cell_group == G)
+        cells = cell_order[cell_start[G]:cell_start[G + 1]]
         # local order: lx + g*ly + g^2*lz  (cells are already x-fastest sorted)
         key = (cx[cells] % g) + g * ((cy[cells] % g) + g * (cz[cells] % g))
         cells = cells[np.argsort(key)]
         dofs = (cells[:, None] * prev_L + np.arange(prev_L)[None, :]).reshape(-1)
         act = prev_active[dofs]
-        fine = np.flatnonzero(fine_group == G)
+        fine = fine_order[fine_start[G]:fine_start[G + 1]]
         PG = Pc[:, dofs].tocsr()[fine].toarray()     # composite basis on G
         AGG = A[fine][:, fine]
         NG = AGG - sp.diags(np.asarray(AGG.sum(axis=1)).ravel())  # Neumann form internal to G
@@ -301,10 +309,26 @@ def l1_block_inverses(A, shape, L):
     return out
 
 
-class MMG:
-    """The full hierarchy for one problem; ``apply(r)`` is one V-cycle."""
+def _given_level(P, shape, L):
+    """A level whose basis is given (not computed from Eq. (8) / Eq. (9)):
+    a dof is active when its basis column is nonzero."""
+    P = sp.csr_matrix(P)
+    act = np.asarray(abs(P).sum(axis=0)).ravel() > 0
+    return P, act, [], shape
 
-    def __init__(self, prob, opts: MMGOptions | None = None):
+
+class MMG:
+    """The full hierarchy for one problem; ``apply(r)`` is one V-cycle.
+
+    ``bases`` (optional): prolongations to use instead of the local spectral
+    bases -- ``bases[0]`` the level-1 Phi (n0 x n1, columns cell * L_1 + j),
+    ``bases[l]`` the Psi of level l + 1 (n_l x n_{l+1}, columns group * L + j)
+    -- for the same cells and vector counts as the options.  Everything that
+    follows the bases (Galerkin operators, smoothers, the cycle of Algorithm 1,
+    the coarse guess) is computed as usual.  This lets a test evaluate the
+    cycle's arithmetic on another implementation's bases."""
+
+    def __init__(self, prob, opts: MMGOptions | None = None, bases=None):
         N = prob["grid"][0]
         self.opts = opts or default_options(N)
         self.prob = prob
@@ -312,7 +336,12 @@ class MMG:
         self.A0 = A
         self.D0 = A.diagonal().copy()
         o = self.opts
-        P1, act, eig, fine_cell, shape = level1_basis(prob, o)
+        if bases is None:
+            P1, act, eig, fine_cell, shape = level1_basis(prob, o)
+        else:
+            _, shape = node_blocks(prob["grid"], o.block, prob["mask"])
+            P1, act, eig, shape = _given_level(bases[0], shape, o.nvec[0])
+            fine_cell = None
         if o.smoother == "chebyshev":
             free = (~prob["mask"]).astype(float)
             self.lmax = lmax_estimate(A, self.D0, free, o.power_iters)
@@ -322,8 +351,12 @@ class MMG:
         Pcomp = P1
         for li, (g, L) in enumerate(zip(o.group, o.nvec[1:])):
             prev = self.levels[-1]
-            Psi, act, eig, fine_cell, shape = coarse_level_basis(
-                prob, Pcomp, fine_cell, prev.shape, prev.L, prev.active, g, L)
+            if bases is None:
+                Psi, act, eig, fine_cell, shape = coarse_level_basis(
+                    prob, Pcomp, fine_cell, prev.shape, prev.L, prev.active, g, L)
+            else:
+                shape = tuple(m // g for m in prev.shape)
+                Psi, act, eig, shape = _given_level(bases[li + 1], shape, L)
             lev = Level(shape=shape, L=L, P=Psi, active=act, eigvals=eig)
             lev.A = _galerkin(prev.A, Psi, act)
             self.levels.append(lev)

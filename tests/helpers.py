@@ -47,3 +47,40 @@ def relerr(a, b):
     a = np.asarray(a, float)
     b = np.asarray(b, float)
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def library_bases(s, pr):
+    """The library's coarse spaces as sparse prolongations in the oracle's
+    numbering (for oracle.mmg.MMG(..., bases=...)): level 1 Phi (n0 x n1,
+    column block * L_1 + j, natural node rows, Dirichlet rows empty) and, per
+    level l >= 2, Psi (n_{l-1} x n_l, rows previous-level cell * L_{l-1} + j,
+    columns group * L_l + k), rebuilt from thermo_export_level's layouts."""
+    import scipy.sparse as sp
+    from oracle import mmg
+    h = s.hierarchy()
+    n0 = s.nnode
+    L1 = h[0]["nvec"]
+    phi = s.export_level(1, 0, n0 * L1).cpu().numpy().reshape(n0, L1)
+    blk, _ = mmg.node_blocks(pr["grid"], 4, pr["mask"])
+    rows = np.repeat(np.flatnonzero(blk >= 0), L1)
+    free = blk >= 0
+    cols = (blk[free][:, None] * L1 + np.arange(L1)[None, :]).reshape(-1)
+    vals = phi[free].reshape(-1)
+    out = [sp.csr_matrix((vals, (rows, cols)), shape=(n0, h[0]["ndof"]))]
+    for l in range(1, len(h)):
+        mx, my, mz = h[l - 1]["cells"]
+        sx, sy, sz = h[l]["cells"]
+        g = mx // sx
+        Lp, L = h[l - 1]["nvec"], h[l]["nvec"]
+        ncell = sx * sy * sz
+        psi = s.export_level(l + 1, 0, ncell * g ** 3 * Lp * L).cpu().numpy().reshape(ncell, g ** 3 * Lp, L)
+        G = np.arange(ncell)
+        Gx, Gy, Gz = G % sx, (G // sx) % sy, G // (sx * sy)
+        loc = np.arange(g ** 3)
+        lx, ly, lz = loc % g, (loc // g) % g, loc // (g * g)
+        cell = (Gx[:, None] * g + lx[None, :]) + mx * ((Gy[:, None] * g + ly[None, :]) + my * (Gz[:, None] * g + lz[None, :]))
+        prow = (cell[:, :, None] * Lp + np.arange(Lp)[None, None, :]).reshape(ncell, g ** 3 * Lp)
+        r = np.repeat(prow[:, :, None], L, axis=2).reshape(-1)
+        c = np.broadcast_to((G[:, None] * L + np.arange(L)[None, :])[:, None, :], psi.shape).reshape(-1)
+        out.append(sp.csr_matrix((psi.reshape(-1), (r, c)), shape=(mx * my * mz * Lp, ncell * L)))
+    return out

@@ -395,3 +395,22 @@ def test_l1_block_jacobi_is_convergent_without_damping():
     # a single cell: the l1 block is the whole operator
     one = mmg.l1_block_inverses(lev.A[:L, :L], (1, 1, 1), L)[0]
     np.testing.assert_allclose(one @ lev.A[:L, :L].toarray(), np.eye(L), atol=1e-10)
+
+
+def test_given_bases_reproduce_the_computed_hierarchy():
+    """MMG(..., bases=the oracle's own prolongations) is the same preconditioner:
+    identical Galerkin operators, cycle and coarse guess (the hook that lets a
+    test evaluate the cycle on the library's exported bases)."""
+    import workloads as W
+    pr = W.problem("chan32")
+    P = fem.build_problem(pr["grid"], pr["h"], pr["x"], pr["p"], pr["kmin"], pr["kmax"], pr["mask"],
+                          pr["source"])
+    H = mmg.MMG(P)
+    G = mmg.MMG(P, bases=[lev.P for lev in H.levels])
+    for a, b in zip(H.levels, G.levels):
+        assert (a.A != b.A).nnz == 0
+        assert np.array_equal(a.active, b.active)
+    r = np.random.default_rng(5).standard_normal(P["A"].shape[0])
+    r[P["mask"]] = 0.0
+    assert np.array_equal(H(r), G(r))
+    assert np.array_equal(H.coarse_guess(P["b"]), G.coarse_guess(P["b"]))

@@ -230,6 +230,7 @@ def problem(name: str) -> dict:
     * ``cube32``: 32^3, Gaussian-smoothed threshold density (sigma 2, V=0.3,
       seed 1), p=3, kmin=1e-3, kmax=1.
     * ``chan128``: 128^3, channel tree (V=0.2, seed 2), kmin=1e-6.
+    * ``chan128_1e3|1e6|1e9``: the chan128 design at contrast 1e3 / 1e6 / 1e9.
     * ``chan256_1e3|1e6|1e9``: 256^3, channel tree (V=0.2, seed 3).
     * ``smoothNN``: NN^3 continuous density in [0.05, 1] (seed 7), kmin=1e-3.
     * ``chanNN``: NN^3 channel tree (V=0.2, seed 3), kmin=1e-6.
@@ -244,6 +245,10 @@ def problem(name: str) -> dict:
         kmin = float(name.split("_")[1])
         kmin = 1.0 / kmin
         x = channel_tree_density(256, 3, 0.2)
+    elif name.startswith("chan128_"):
+        N = 128
+        kmin = 1.0 / float(name.split("_")[1])
+        x = channel_tree_density(128, 2, 0.2)
     elif name.startswith("smooth"):
         N = int(name[len("smooth"):])
         x, kmin = smooth_random_density(N, 7), 1e-3
