@@ -23,9 +23,11 @@
  *     the layout above, unless a parameter says "host".  The library copies
  *     into its own padded device layout and owns every internal buffer.
  *   - All device work is enqueued on the CUDA stream given to thermo_create.
- *     Calls return after enqueueing, except thermo_setup_precond and
- *     thermo_solve, which synchronise the stream (status words, convergence
- *     checks) and thermo_compliance (returns a host scalar).
+ *     Calls return after enqueueing, except those that launch TMA-staged
+ *     fine-grid kernels (setup_precond, solve, vcycle, apply, apply_dot,
+ *     bench_kernel), which synchronise the stream to read the context's
+ *     stage time-out word (and, for solve, once per convergence check), and
+ *     thermo_compliance (returns a host scalar).
  *   - Every call returns a thermo_status; none aborts, asserts or traps.  On
  *     failure the context stays valid and thermo_last_error() describes it.
  *   - Call order: create -> set_density -> setup_precond -> solve (any number
@@ -228,6 +230,38 @@ thermo_status thermo_dot_noalloc(const double *x, const double *y, long long n, 
  * u device double[nodes]; c host double*.  Synchronises the stream. */
 thermo_status thermo_compliance(thermo_ctx *ctx, const double *u, double *c);
 
+/* Ainv = A^-1 for a dense symmetric positive definite A with the library's
+ * blocked FP64 Cholesky factorisation and explicit inverse: the routine of
+ * the direct coarsest-level solve of Sec. 3 Algorithm 1 (A_cc^-1; the paper's
+ * Sec. 4 uses a sparse LU), exposed on caller-supplied matrices so that it
+ * can be checked on its own.  Context-free.
+ *   n       order, 1 <= n <= 20000
+ *   A       device double[n][n], row-major; symmetrised as (A + A^T)/2, not modified
+ *   Ainv    device double[n][n], row-major, written (symmetric)
+ *   stream  a cudaStream_t (NULL = legacy default stream); synchronised
+ *   pivot   host int or NULL: on THERMO_ESINGULAR the 0-based row of the
+ *           first non-positive (or non-finite) pivot
+ *   msg     host buffer of msg_len bytes for an error message, may be NULL
+ * Allocates and frees its scratch (about 2 n^2 doubles) on the current device.
+ * Errors: EINVAL (arguments), ENOMEM, ECUDA, ESINGULAR (A not positive
+ * definite; Ainv then holds no useful values). */
+thermo_status thermo_dense_spd_inverse(int n, const double *A, double *Ainv, void *stream, int *pivot,
+                                       char *msg, int msg_len);
+
+/* Stage wait limit of the TMA-staged fine-grid kernels (robustness support,
+ * no counterpart in the paper).  Each kernel stages its input planes into a
+ * shared-memory ring through asynchronous tensor copies and waits for them
+ * with a bounded wait: after a first non-blocking test it polls for at most
+ * `cycles` clock64 cycles (0 restores the default, 2^31 cycles, about one
+ * second).  A wait that runs out marks the launch's results invalid in a
+ * per-context device word, stops the kernel from issuing further copies and
+ * lets it drain the copies already in flight before it exits; every entry
+ * point that launches such a kernel (set-up, solve, cycle, applies, kernel
+ * benchmark) reads and clears the word and then returns THERMO_ECUDA.  The
+ * context stays usable.  A tiny limit (1 cycle) makes the waits run out on
+ * purpose, which is how the time-out path is tested.  EINVAL if cycles < 0. */
+thermo_status thermo_set_stage_wait(thermo_ctx *ctx, long long cycles);
+
 /* Last error message of this context (never NULL).  Context management: no
  * counterpart in the paper. */
 const char *thermo_last_error(const thermo_ctx *ctx);
@@ -241,7 +275,9 @@ void thermo_destroy(thermo_ctx *ctx);
 /* y = A u with the Dirichlet-eliminated operator of Sec. 2.2 Eq. (5) (identity rows on Gamma_D,
  * no coupling to Gamma_D columns), in the given arithmetic:
  * THERMO_FP64 (FP64), THERMO_MIXED (FP32 data and math) or
- * THERMO_MIXED_BF16S (BF16 data, FP32 math).  u, y: device double[nodes]. */
+ * THERMO_MIXED_BF16S (BF16 data, FP32 math).  u, y: device double[nodes].
+ * Synchronises the stream to read the stage time-out word (see
+ * thermo_set_stage_wait); THERMO_ECUDA if a kernel gave up waiting. */
 thermo_status thermo_apply(thermo_ctx *ctx, int precision, const double *u, double *y);
 
 /* q = A p and pq = p^T A p with the fused kernel of the outer CG loop (the

@@ -41,6 +41,9 @@ struct Geom {
   // fine tile decomposition (nodes); tiles are block-aligned
   int TX, TY, ZC;           // tile width / height, z planes per CTA chunk
   int NZ2, NZD;             // z chunks (ragged) of the two-nodes-per-lane and float-float engines
+  // bounded waits of the TMA-staged fine kernels (one word per context, on its device)
+  int* err;                 // set to 1 by a kernel whose stage wait gave up
+  long long wait;           // stage wait limit in clock64 cycles after a first non-blocking test
 };
 
 __host__ __device__ __forceinline__ long long nidx(const Geom& g, int x, int y, int z) {

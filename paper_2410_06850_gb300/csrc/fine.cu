@@ -97,7 +97,6 @@ struct FineArgs {
   double* partial;  // dot partials, one per CTA
   unsigned* counter;
   double* dot;
-  int* err;         // set to 1 if a stage wait gave up (never expected)
 };
 
 template <class C, bool CUBE>
@@ -216,16 +215,9 @@ __global__ void __launch_bounds__(FNT, sizeof(S) == 8 ? 1 : (OP == F_RESTRICT ? 
   auto wait_group = [&](int q) {
     if (stage_bad) return;
     const unsigned parity = (unsigned)(((q - zs + 1) / NS) & 1);
-    uint64_t* bar = bars + stage_of(q);
-    bool ok = false;
-    const long long t0 = clock64();
-    while (!ok) {
-      ok = mbar_try_wait(bar, parity);
-      if (!ok && clock64() - t0 > (1LL << 31)) break;  // ~1 s: give up, flag, never hang
-    }
-    if (!ok) {
+    if (!mbar_wait_limited(bars + stage_of(q), parity, g.wait)) {  // bounded: give up, flag, never hang
       stage_bad = 1;
-      atomicExch(a.err, 1);
+      atomicExch(g.err, 1);
     }
   };
 
@@ -235,8 +227,9 @@ __global__ void __launch_bounds__(FNT, sizeof(S) == 8 ? 1 : (OP == F_RESTRICT ? 
     mbar_fence_init();
   }
   __syncthreads();
+  int qhi = zs - 2;  // last group issued (thread 0)
   if (tid == 0)
-    for (int q = zs - 1; q < zs - 1 + (NS - 3); ++q) issue(q);
+    for (int q = zs - 1; q < zs - 1 + (NS - 3); ++q) issue(q), qhi = q;
 
   C VA[3][3], VB[3][3], VC[3][3], KA[2][2], KB[2][2], KC[2][2];
 #pragma unroll
@@ -371,9 +364,10 @@ __global__ void __launch_bounds__(FNT, sizeof(S) == 8 ? 1 : (OP == F_RESTRICT ? 
       }
       __syncthreads();
     }
-    if (tid == 0) {
+    if (tid == 0 && !stage_bad) {  // after a wait gave up no stage is refilled
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");  // earlier generic accesses before TMA writes
       issue(t + NS - 2);
+      qhi = t + NS - 2;
     }
     if (rowwarp) {
       const S* s1 = sV(t + 1);
@@ -410,6 +404,7 @@ __global__ void __launch_bounds__(FNT, sizeof(S) == 8 ? 1 : (OP == F_RESTRICT ? 
     if (t + 2 > ze) break;
     step(t + 2, VC, VA, VB, KC, KA);
   }
+  if (tid == 0) mbar_drain(bars, NS, zs - 1, qhi);
 
   if (DOT) {
     for (int o = 16; o > 0; o >>= 1) dacc += __shfl_down_sync(0xffffffffu, dacc, o);
@@ -527,22 +522,6 @@ unsigned fine_num_ctas(const Geom& g) {
   return d.x * d.y * d.z;
 }
 
-int* fine_err_word() {
-  static int* p = nullptr;
-  static std::once_flag once;
-  std::call_once(once, [] { cudaMalloc(&p, sizeof(int)) == cudaSuccess ? cudaMemset(p, 0, sizeof(int)) : cudaErrorMemoryAllocation; });
-  return p;
-}
-
-int fine_stage_errors(bool reset) {
-  int* p = fine_err_word();
-  int h = 0;
-  if (!p) return 0;
-  cudaMemcpy(&h, p, sizeof(int), cudaMemcpyDeviceToHost);
-  if (reset && h) cudaMemset(p, 0, sizeof(int));
-  return h;
-}
-
 template <class S, class To>
 static FineArgs<S, To> fargs(const Geom& g, const uint32_t* mask, const S* kap) {
   FineArgs<S, To> a;
@@ -550,7 +529,6 @@ static FineArgs<S, To> fargs(const Geom& g, const uint32_t* mask, const S* kap) 
   a.g = g;
   a.mask = mask;
   a.kap = kap;
-  a.err = fine_err_word();
   for (int i = 0; i < 8; ++i) a.cc[i] = (typename Cv<S>::C)g.c[i];
   return a;
 }

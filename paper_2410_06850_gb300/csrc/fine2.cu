@@ -67,7 +67,6 @@ struct QArgs {
   const uint32_t* mask;
   float cA, cB;  // e' = e + cA (e - w) + cB D^-1 (r - A e)
   float c0, c3;  // K0 coefficients
-  int* err;
 };
 struct alignas(64) QMaps {
   CUtensorMap v, k, m, r, w;
@@ -152,16 +151,9 @@ __global__ void __launch_bounds__(QNT, 3) q_tile(const __grid_constant__ QArgs<S
   auto wait_group = [&](int q) {
     if (stage_bad) return;
     const unsigned parity = (unsigned)(((q - zs + 1) / QNS) & 1);
-    uint64_t* bar = bars + stage_of(q);
-    bool ok = false;
-    const long long t0 = clock64();
-    while (!ok) {
-      ok = mbar_try_wait(bar, parity);
-      if (!ok && clock64() - t0 > (1LL << 31)) break;  // ~1 s: give up, flag, never hang
-    }
-    if (!ok) {
+    if (!mbar_wait_limited(bars + stage_of(q), parity, g.wait)) {  // bounded: give up, flag, never hang
       stage_bad = 1;
-      atomicExch(a.err, 1);
+      atomicExch(g.err, 1);
     }
   };
 
@@ -172,6 +164,7 @@ __global__ void __launch_bounds__(QNT, 3) q_tile(const __grid_constant__ QArgs<S
   }
   __syncthreads();
   static_assert(QNS == 6, "the two-plane step keeps four groups resident and two in flight");
+  int qhi = zs + 2;  // last group issued (thread 0)
   if (tid == 0)
     for (int q = zs - 1; q <= zs + 2; ++q) issue(q);
 
@@ -370,10 +363,11 @@ __global__ void __launch_bounds__(QNT, 3) q_tile(const __grid_constant__ QArgs<S
     }
     wait_group(t + 1);
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && !stage_bad) {  // after a wait gave up no stage is refilled
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       issue(t + 3);
       issue(t + 4);
+      qhi = t + 4;
     }
     plane(t);
     if (t + 1 <= ze) {
@@ -381,6 +375,7 @@ __global__ void __launch_bounds__(QNT, 3) q_tile(const __grid_constant__ QArgs<S
       plane(t + 1);
     }
   }
+  if (tid == 0) mbar_drain(bars, QNS, zs - 1, qhi);
 }
 
 template <class T>
@@ -434,7 +429,6 @@ QArgs<S, To> qargs(const Geom& g, const uint32_t* mask, const S* kap) {
   a.kap = kap;
   a.c0 = (float)g.c[0];
   a.c3 = (float)g.c[3];
-  a.err = fine_err_word();
   return a;
 }
 

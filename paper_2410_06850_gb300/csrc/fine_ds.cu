@@ -65,7 +65,6 @@ struct DsArgs {
   double* partial;  // dot partials: [0, nedge) from ds_edge, then one per CTA
   unsigned* counter;
   double* dot;
-  int* err;
   int nedge;        // partials written by ds_edge before this kernel
 };
 struct alignas(64) DsMaps {
@@ -281,16 +280,9 @@ __global__ void __launch_bounds__(DNT, 2) ds_apply(const __grid_constant__ DsArg
   auto wait_group = [&](int q) {
     if (stage_bad) return;
     const unsigned parity = (unsigned)(((q - zs + 1) / DNS) & 1);
-    uint64_t* bar = bars + stage_of(q);
-    bool ok = false;
-    const long long t0 = clock64();
-    while (!ok) {
-      ok = mbar_try_wait(bar, parity);
-      if (!ok && clock64() - t0 > (1LL << 31)) break;  // ~1 s: give up, flag, never hang
-    }
-    if (!ok) {
+    if (!mbar_wait_limited(bars + stage_of(q), parity, g.wait)) {  // bounded: give up, flag, never hang
       stage_bad = 1;
-      atomicExch(a.err, 1);
+      atomicExch(g.err, 1);
     }
   };
 
@@ -300,8 +292,9 @@ __global__ void __launch_bounds__(DNT, 2) ds_apply(const __grid_constant__ DsArg
     mbar_fence_init();
   }
   __syncthreads();
+  int qhi = zs - 2;  // last group issued (thread 0)
   if (tid == 0)
-    for (int q = zs - 1; q < zs - 1 + (DNS - 3); ++q) issue(q);
+    for (int q = zs - 1; q < zs - 1 + (DNS - 3); ++q) issue(q), qhi = q;
 
   const float2 c3h = F2(a.c3h, a.c3h), c3l = F2(a.c3l, a.c3l);
   double dacc = 0.0;
@@ -380,9 +373,10 @@ __global__ void __launch_bounds__(DNT, 2) ds_apply(const __grid_constant__ DsArg
   for (int t = zs - 2; t <= ze; ++t) {
     wait_group(t + 1);
     __syncthreads();
-    if (tid == 0) {
+    if (tid == 0 && !stage_bad) {  // after a wait gave up no stage is refilled
       asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
       issue(t + DNS - 2);
+      qhi = t + DNS - 2;
     }
     if (t + 1 <= ze + 1) {  // split the landed p plane into hi / lo floats
       const double* src = sV(t + 1);
@@ -399,6 +393,7 @@ __global__ void __launch_bounds__(DNT, 2) ds_apply(const __grid_constant__ DsArg
     if (t < zs) continue;
     if (w < TY) pair(t, w, 2 * lane);
   }
+  if (tid == 0) mbar_drain(bars, DNS, zs - 1, qhi);
 
   if (DOT) {
     for (int o = 16; o > 0; o >>= 1) dacc += __shfl_down_sync(0xffffffffu, dacc, o);
@@ -465,7 +460,6 @@ cudaError_t fine_apply_ds(const Geom& g, const uint32_t* mask, const float* khi,
   a.partial = partial;
   a.counter = counter;
   a.dot = dot;
-  a.err = fine_err_word();
   DsMaps tm;
   cudaError_t e;
   if ((e = get_map(&tm.v, u + g.base, CU_TENSOR_MAP_DATA_TYPE_FLOAT64, 8, g.P, g.RYn, g.nz + 2, DW, g.TY + 3)) !=

@@ -6,7 +6,6 @@ namespace thermo {
 
 // ---- fine.cu
 unsigned fine_num_ctas(const Geom& g);
-int fine_stage_errors(bool reset);  // nonzero if a fine kernel gave up waiting for a TMA stage
 cudaError_t fine_apply_f64(const Geom& g, const uint32_t* mask, const double* kap, const double* u, double* y,
                            double* partial, unsigned* counter, double* dot, cudaStream_t st, bool mask_input = false);
 template <class S>
@@ -134,7 +133,9 @@ cudaError_t group_rap(const CLevel& prev, const CLevel& cur, const double* Psi, 
 cudaError_t fix_inactive(const CLevel& lv, const uint8_t* act, double* tiles, cudaStream_t st);
 cudaError_t l1_inverse(const CLevel& lv, const double* tiles, double* Dinv64, float* Dinv32, cudaStream_t st);
 cudaError_t dense_assemble(const CLevel& lv, const double* tiles, double* A, cudaStream_t st);
-cudaError_t cholesky_inverse(int n, double* A, double* work, int* status, cudaStream_t st);
+// ---- dense.cu : blocked FP64 Cholesky + explicit inverse of the coarsest operator
+long long cholesky_work_size(int n);  // doubles of scratch cholesky_inverse needs
+cudaError_t cholesky_inverse(int n, double* A, double* Ainv, double* work, int* status, cudaStream_t st);
 cudaError_t cvt_f64_f32(const double* a, float* b, long long n, cudaStream_t st);
 cudaError_t phi_natural(const Geom& g, const double* phi_pad, int L1, double* out, cudaStream_t st);
 

@@ -904,91 +904,6 @@ cudaError_t dense_assemble(const CLevel& lv, const double* tiles, double* A, cud
   return cudaGetLastError();
 }
 
-// Right-looking Cholesky (lower), one column per step; then A^-1 column by
-// column with forward/back substitution.  Symmetrised input.
-__global__ void k_symm(int n, double* A) {
-  for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < (long long)n * n;
-       w += (long long)gridDim.x * blockDim.x) {
-    const int i = (int)(w / n), j = (int)(w % n);
-    if (i > j) {
-      const double v = 0.5 * (A[(long long)i * n + j] + A[(long long)j * n + i]);
-      A[(long long)i * n + j] = v;
-      A[(long long)j * n + i] = v;
-    }
-  }
-}
-__global__ void k_chol_col(int n, int k, double* A, int* status) {
-  __shared__ double dk;
-  if (threadIdx.x == 0) {
-    const double d = A[(long long)k * n + k];
-    if (!(d > 0.0) || !isfinite(d)) {
-      atomicExch(status, k + 1);
-      dk = 1.0;
-    } else {
-      dk = sqrt(d);
-    }
-  }
-  __syncthreads();
-  const double d = dk;
-  for (int i = k + threadIdx.x + blockIdx.x * blockDim.x; i < n; i += blockDim.x * gridDim.x) {
-    if (i == k)
-      A[(long long)k * n + k] = d;
-    else
-      A[(long long)i * n + k] /= d;
-  }
-}
-__global__ void k_chol_update(int n, int k, double* A) {
-  // A[i][j] -= L[i][k] L[j][k] for k < j <= i
-  const long long m = n - k - 1;
-  for (long long w = blockIdx.x * (long long)blockDim.x + threadIdx.x; w < m * m; w += (long long)gridDim.x * blockDim.x) {
-    const int i = k + 1 + (int)(w / m), j = k + 1 + (int)(w % m);
-    if (j > i) continue;
-    A[(long long)i * n + j] -= A[(long long)i * n + k] * A[(long long)j * n + k];
-  }
-}
-// X[:, col] = A^-1 e_col using the lower factor Lf (row-major, lower part)
-__global__ void k_chol_inv(int n, const double* __restrict__ Lf, double* __restrict__ X) {
-  extern __shared__ __align__(16) unsigned char sm[];
-  double* y = (double*)sm;
-  const int col = blockIdx.x;
-  for (int i = threadIdx.x; i < n; i += blockDim.x) y[i] = (i == col) ? 1.0 : 0.0;
-  __syncthreads();
-  for (int i = 0; i < n; ++i) {  // forward: L y = e
-    const double yi = y[i] / Lf[(long long)i * n + i];
-    __syncthreads();
-    if (threadIdx.x == 0) y[i] = yi;
-    for (int k = i + 1 + threadIdx.x; k < n; k += blockDim.x) y[k] -= Lf[(long long)k * n + i] * yi;
-    __syncthreads();
-  }
-  for (int i = n - 1; i >= 0; --i) {  // backward: L^T x = y
-    const double xi = y[i] / Lf[(long long)i * n + i];
-    __syncthreads();
-    if (threadIdx.x == 0) y[i] = xi;
-    for (int k = threadIdx.x; k < i; k += blockDim.x) y[k] -= Lf[(long long)i * n + k] * xi;
-    __syncthreads();
-  }
-  for (int i = threadIdx.x; i < n; i += blockDim.x) X[(long long)i * n + col] = y[i];
-}
-cudaError_t cholesky_inverse(int n, double* A, double* work, int* status, cudaStream_t st) {
-  long long nb = ((long long)n * n + 255) / 256;
-  if (nb > 152 * 32) nb = 152 * 32;
-  note_launch(), k_symm<<<(unsigned)nb, 256, 0, st>>>(n, A);
-  for (int k = 0; k < n; ++k) {
-    note_launch(), k_chol_col<<<1, 256, 0, st>>>(n, k, A, status);
-    const long long m = (long long)(n - k - 1) * (n - k - 1);
-    if (m > 0) {
-      long long b2 = (m + 255) / 256;
-      if (b2 > 152 * 16) b2 = 152 * 16;
-      note_launch(), k_chol_update<<<(unsigned)b2, 256, 0, st>>>(n, k, A);
-    }
-  }
-  const size_t sm = (size_t)n * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(k_chol_inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-  if (e != cudaSuccess) return e;
-  note_launch(), k_chol_inv<<<n, 256, sm, st>>>(n, A, work);
-  return cudaGetLastError();
-}
-
 __global__ void k_cvt(const double* __restrict__ a, float* __restrict__ b, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     b[i] = (float)a[i];

@@ -17,6 +17,7 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "chebyshev.h"
+#include "tma.cuh"
 
 using namespace thermo;
 
@@ -90,6 +91,7 @@ struct thermo_ctx {
   Lev lev[THERMO_MAX_LEVELS + 1];
   double* Ainv = nullptr;
   double* cholA = nullptr;
+  double* cholW = nullptr;     // scratch of the blocked factorisation / inverse
   int ncoarse = 0;
   int* gcum_dev = nullptr;
   // scalars and reductions
@@ -135,6 +137,18 @@ static cudaError_t dalloc(thermo_ctx* ctx, T** p, size_t n) {
   e = cudaMemsetAsync(v, 0, n * sizeof(T) + 64, ctx->st);
   *p = (T*)v;
   return e;
+}
+
+// The context's stage time-out word is nonzero when one of its TMA-staged fine
+// kernels gave up waiting for a plane since the last check: that launch's
+// results are invalid.  Reads and resets the word (synchronises the stream).
+static thermo_status stage_check(thermo_ctx* ctx) {
+  CK(cudaMemcpyAsync(ctx->status_h + 4, ctx->g.err, sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  if (ctx->status_h[4] == 0) return THERMO_OK;
+  CK(cudaMemsetAsync(ctx->g.err, 0, sizeof(int), ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return fail(ctx, THERMO_ECUDA, "a fine-grid kernel gave up waiting for a TMA stage (its results are invalid)");
 }
 
 static double now_ms() {
@@ -325,6 +339,8 @@ extern "C" thermo_status thermo_create(const int grid[3], const double h[3], con
   }
   // allocations
   const long long ns = g.nsize, es = g.esize;
+  CK(dalloc(ctx, &ctx->g.err, 1));  // stage time-out word of this context's fine kernels
+  ctx->g.wait = kStageWait;
   CK(dalloc(ctx, &ctx->bits, g.msize));
   CK(dalloc(ctx, &ctx->k64, es));
   CK(dalloc(ctx, &ctx->k32, es));
@@ -369,6 +385,7 @@ extern "C" thermo_status thermo_create(const int grid[3], const double h[3], con
   }
   CK(dalloc(ctx, &ctx->Ainv, (long long)ctx->ncoarse * ctx->ncoarse));
   CK(dalloc(ctx, &ctx->cholA, (long long)ctx->ncoarse * ctx->ncoarse));
+  CK(dalloc(ctx, &ctx->cholW, cholesky_work_size(ctx->ncoarse)));
   {
     std::vector<int> gc(THERMO_MAX_LEVELS, 1);
     int acc = 1;
@@ -391,7 +408,7 @@ extern "C" thermo_status thermo_create(const int grid[3], const double h[3], con
     ctx->red.nblocks = (int)np;
   }
   CK(cudaMallocHost((void**)&ctx->sc_h, sizeof(CgScalars)));
-  CK(cudaMallocHost((void**)&ctx->status_h, 4 * sizeof(int)));
+  CK(cudaMallocHost((void**)&ctx->status_h, 8 * sizeof(int)));
   CK(cudaMallocHost((void**)&ctx->dscal_h, 16 * sizeof(double)));
   // boundary data and load
   CK(mask_to_bits(g, mask, ctx->bits, ctx->st));
@@ -485,7 +502,11 @@ extern "C" thermo_status thermo_setup_precond(thermo_ctx* ctx) {
         CK(cudaMemcpyAsync(ctx->dscal_h, ctx->dscal, sizeof(double), cudaMemcpyDeviceToHost, st));
         CK(cudaStreamSynchronize(st));
         lam = sqrt(ctx->dscal_h[0]);
-        if (!(lam > 0.0) || !std::isfinite(lam)) return fail(ctx, THERMO_EINVAL, "power iteration failed (lmax = %g)", lam);
+        if (!(lam > 0.0) || !std::isfinite(lam)) {
+          const thermo_status se = stage_check(ctx);  // a timed-out stage explains a bad estimate
+          if (se != THERMO_OK) return se;
+          return fail(ctx, THERMO_EINVAL, "power iteration failed (lmax = %g)", lam);
+        }
         CK(vec_scale(g, 1.0 / lam, ctx->p, st));
       }
       ctx->lmax = lam;
@@ -524,10 +545,14 @@ extern "C" thermo_status thermo_setup_precond(thermo_ctx* ctx) {
   }
   CK(cvt_f64_f32(ctx->phi64, ctx->phi32, g.nsize * L1, st));
   CK(dense_assemble(ctx->lev[ctx->nlev].cl, ctx->lev[ctx->nlev].T64, ctx->cholA, st));
-  CK(cholesky_inverse(ctx->ncoarse, ctx->cholA, ctx->Ainv, ctx->status_dev, st));
+  CK(cholesky_inverse(ctx->ncoarse, ctx->cholA, ctx->Ainv, ctx->cholW, ctx->status_dev, st));
   CK(cudaMemcpyAsync(ctx->status_h, ctx->status_dev, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   ctx->t_setup_ms = now_ms() - t0;
+  {
+    const thermo_status se = stage_check(ctx);
+    if (se != THERMO_OK) return se;
+  }
   if (ctx->status_h[0] != 0)
     return fail(ctx, THERMO_ESINGULAR, "coarsest Cholesky: non-positive pivot at %d", ctx->status_h[0] - 1);
   ctx->have_precond = true;
@@ -846,7 +871,12 @@ extern "C" thermo_status thermo_solve(thermo_ctx* ctx, const double* rhs, double
   ctx->hist.clear();
   if (!std::isfinite(bnorm)) return fail(ctx, THERMO_EINVAL, "right-hand side is not finite");
   if (!std::isfinite(rn)) {
-    inf.status = THERMO_EBREAKDOWN;
+    const thermo_status se = stage_check(ctx);
+    inf.status = se != THERMO_OK ? se : THERMO_EBREAKDOWN;
+    if (se != THERMO_OK) {
+      if (info) *info = inf;
+      return se;
+    }
     if (info) *info = inf;
     return fail(ctx, THERMO_EBREAKDOWN, "initial residual is not finite (check the density)");
   }
@@ -948,7 +978,10 @@ extern "C" thermo_status thermo_solve(thermo_ctx* ctx, const double* rhs, double
   CK(unpack_nodes(g, ctx->u, u, st));
   CK(cudaStreamSynchronize(st));
   kt_fold(ctx);
-  if (fine_stage_errors(true)) result = fail(ctx, THERMO_ECUDA, "a fine-grid kernel timed out waiting for its TMA stage");
+  {
+    const thermo_status se = stage_check(ctx);
+    if (se != THERMO_OK) result = se;
+  }
   inf.iters = it;
   inf.restarts = restarts + refinements;
   inf.t_solve_ms = now_ms() - t0;
@@ -1006,7 +1039,7 @@ extern "C" thermo_status thermo_apply(thermo_ctx* ctx, int precision, const doub
     return fail(ctx, THERMO_EINVAL, "unknown precision %d", precision);
   }
   CK(unpack_nodes(g, ctx->q, y, st));
-  return THERMO_OK;
+  return stage_check(ctx);
 }
 
 extern "C" thermo_status thermo_apply_dot(thermo_ctx* ctx, const double* p, double* q, double* pq) {
@@ -1021,7 +1054,7 @@ extern "C" thermo_status thermo_apply_dot(thermo_ctx* ctx, const double* p, doub
   CK(cudaMemcpyAsync(ctx->dscal_h, ctx->dscal, sizeof(double), cudaMemcpyDeviceToHost, st));
   CK(cudaStreamSynchronize(st));
   *pq = ctx->dscal_h[0];
-  return THERMO_OK;
+  return stage_check(ctx);
 }
 
 extern "C" thermo_status thermo_vcycle(thermo_ctx* ctx, const double* r, double* z) {
@@ -1040,9 +1073,7 @@ extern "C" thermo_status thermo_vcycle(thermo_ctx* ctx, const double* r, double*
   } else {
     CK(unpack_nodes(g, ctx->z64, z, st));
   }
-  CK(cudaStreamSynchronize(st));
-  if (fine_stage_errors(true)) return fail(ctx, THERMO_ECUDA, "a fine-grid kernel timed out waiting for its TMA stage");
-  return THERMO_OK;
+  return stage_check(ctx);
 }
 
 extern "C" thermo_status thermo_load_vector(thermo_ctx* ctx, double* f) {
@@ -1281,5 +1312,55 @@ extern "C" thermo_status thermo_bench_kernel(thermo_ctx* ctx, int which, int rep
   cudaEventDestroy(e1);
   *ms_per_launch = ms / reps;
   if (bytes_per_launch) *bytes_per_launch = bytes;
+  return stage_check(ctx);
+}
+
+extern "C" thermo_status thermo_dense_spd_inverse(int n, const double* A, double* Ainv, void* stream, int* pivot,
+                                                  char* msg, int msg_len) {
+  auto say = [&](thermo_status s, const char* fmt, ...) {
+    if (msg && msg_len > 0) {
+      va_list ap;
+      va_start(ap, fmt);
+      vsnprintf(msg, (size_t)msg_len, fmt, ap);
+      va_end(ap);
+    }
+    return s;
+  };
+  if (pivot) *pivot = 0;
+  if (msg && msg_len > 0) msg[0] = 0;
+  if (n < 1 || n > 20000 || !A || !Ainv) return say(THERMO_EINVAL, "need 1 <= n <= 20000 and device A, Ainv");
+  cudaStream_t st = (cudaStream_t)stream;
+  double *F = nullptr, *work = nullptr;
+  int* status = nullptr;
+  int hs = 0;
+  thermo_status res = THERMO_OK;
+  cudaError_t e = cudaMalloc(&F, (size_t)n * n * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&work, (size_t)cholesky_work_size(n) * sizeof(double));
+  if (e == cudaSuccess) e = cudaMalloc(&status, sizeof(int));
+  if (e != cudaSuccess) {
+    res = say(THERMO_ENOMEM, "scratch allocation failed: %s", cudaGetErrorString(e));
+  } else {
+    if (e == cudaSuccess) e = cudaMemsetAsync(status, 0, sizeof(int), st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(F, A, (size_t)n * n * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    if (e == cudaSuccess) e = cholesky_inverse(n, F, Ainv, work, status, st);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&hs, status, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess)
+      res = say(THERMO_ECUDA, "%s", cudaGetErrorString(e));
+    else if (hs != 0) {
+      if (pivot) *pivot = hs - 1;
+      res = say(THERMO_ESINGULAR, "non-positive pivot at row %d: the matrix is not positive definite", hs - 1);
+    }
+  }
+  cudaFree(F);
+  cudaFree(work);
+  cudaFree(status);
+  return res;
+}
+
+extern "C" thermo_status thermo_set_stage_wait(thermo_ctx* ctx, long long cycles) {
+  if (!ctx) return THERMO_EINVAL;
+  if (cycles < 0) return fail(ctx, THERMO_EINVAL, "the stage wait limit must be >= 0 (0 selects the default)");
+  ctx->g.wait = cycles == 0 ? kStageWait : cycles;
   return THERMO_OK;
 }

@@ -28,6 +28,36 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
       : "memory");
   return ok != 0;
 }
+__device__ __forceinline__ bool mbar_test_wait(uint64_t* bar, unsigned parity) {
+  unsigned ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.test_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// default stage wait: 2^31 clock64 cycles, about one second at the GB300's clocks
+constexpr long long kStageWait = 1LL << 31;
+// Wait for the phase of parity `parity` of *bar to complete, giving up after
+// `limit` clock64 cycles (limit 0: one non-blocking test).  false: gave up.
+__device__ __forceinline__ bool mbar_wait_limited(uint64_t* bar, unsigned parity, long long limit) {
+  if (mbar_test_wait(bar, parity)) return true;
+  const long long t0 = clock64();
+  while (clock64() - t0 < limit)
+    if (mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+// Ring of `ns` stages in which group q (q >= q0) lands on stage (q - q0) % ns
+// in phase (q - q0) / ns.  Before the issuing thread exits, wait (default
+// limit) for the last ns groups issued, q0 .. qhi, so that no bulk copy into
+// the CTA's shared memory is still in flight when the CTA retires (after a
+// stage wait gave up, the consumers skip their waits).  Groups already
+// waited on return at once.
+__device__ __forceinline__ void mbar_drain(uint64_t* bars, int ns, int q0, int qhi) {
+  for (int q = (qhi - ns + 1 > q0 ? qhi - ns + 1 : q0); q <= qhi; ++q)
+    mbar_wait_limited(bars + (q - q0) % ns, (unsigned)(((q - q0) / ns) & 1), kStageWait);
+}
 __device__ __forceinline__ void tma_load3(void* dst, const CUtensorMap* map, int c0, int c1, int c2, uint64_t* bar) {
   asm volatile(
       "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];\n" ::"r"(
@@ -42,7 +72,5 @@ __device__ __forceinline__ void tma_load3(void* dst, const CUtensorMap* map, int
 // and box; thread-safe).
 cudaError_t get_map(CUtensorMap* out, const void* base, CUtensorMapDataType dt, int esize, long long d0,
                     long long d1, long long d2, int b0, int b1);
-// device word set to 1 by a fine kernel whose stage wait gave up
-int* fine_err_word();
 
 }  // namespace thermo

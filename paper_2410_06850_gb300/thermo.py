@@ -31,7 +31,8 @@ EXPORTED = ["thermo_default_options", "thermo_create", "thermo_set_density", "th
             "thermo_destroy", "thermo_apply", "thermo_vcycle", "thermo_load_vector",
             "thermo_hierarchy", "thermo_export_level", "thermo_filter", "thermo_oc_update",
             "thermo_launch_count", "thermo_bench_kernel", "thermo_apply_dot",
-          "thermo_kernel_timers", "thermo_kernel_time", "thermo_dot_noalloc", "thermo_residual_history"]
+            "thermo_kernel_timers", "thermo_kernel_time", "thermo_dot_noalloc", "thermo_residual_history",
+            "thermo_set_stage_wait", "thermo_dense_spd_inverse"]
 
 
 class thermo_options(C.Structure):
@@ -98,6 +99,8 @@ def lib():
         L.thermo_residual_history.argtypes = [vp, C.POINTER(C.c_double), i]
         L.thermo_residual_history.restype = C.c_int
         L.thermo_kernel_time.argtypes = [vp, i, dp, C.POINTER(C.c_longlong), dp, dp]
+        L.thermo_set_stage_wait.argtypes = [vp, C.c_longlong]
+        L.thermo_dense_spd_inverse.argtypes = [i, vp, vp, vp, ip, C.c_char_p, i]
         for n in EXPORTED:
             if n not in ("thermo_last_error", "thermo_destroy", "thermo_launch_count"):
                 getattr(L, n).restype = C.c_int
@@ -237,6 +240,10 @@ class Solver:
         self._check(lib().thermo_apply_dot(self.ctx, _ptr(p), _ptr(q), C.byref(d)))
         return q, d.value
 
+    def set_stage_wait(self, cycles=0):
+        """Stage wait limit (clock64 cycles) of the TMA-staged fine kernels; 0 = default."""
+        return self._check(lib().thermo_set_stage_wait(self.ctx, int(cycles)))
+
     def residual_history(self):
         """Relative recursive residuals of the last solve, one per convergence check."""
         n = lib().thermo_residual_history(self.ctx, None, 0)
@@ -313,6 +320,21 @@ def dot_noalloc(x, y, out):
     if rc != OK:
         raise ThermoError(rc, msg.value.decode())
     return out
+
+
+def dense_spd_inverse(A):
+    """(A^-1, status, pivot, message) through thermo_dense_spd_inverse: the
+    blocked FP64 Cholesky + inverse of the coarsest-level solve applied to a
+    caller's dense matrix (CUDA float64 tensor, n x n, contiguous)."""
+    if A.device.type != "cuda" or A.dtype != torch.float64 or A.dim() != 2 or A.shape[0] != A.shape[1]:
+        raise ValueError("dense_spd_inverse needs a square CUDA float64 tensor")
+    A = A.contiguous()
+    X = torch.empty_like(A)
+    piv = C.c_int(-1)
+    msg = C.create_string_buffer(256)
+    st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = lib().thermo_dense_spd_inverse(int(A.shape[0]), _ptr(A), _ptr(X), st, C.byref(piv), msg, 256)
+    return X, rc, piv.value, msg.value.decode()
 
 
 def launch_count() -> int:

@@ -69,3 +69,44 @@ def test_bad_options_rejected():
     for kw in (dict(block=3), dict(nu_fine=0), dict(nvec=[7, 17])):
         with pytest.raises(ThermoError):
             Solver(pr["grid"], pr["h"], torch.as_tensor(pr["mask"]), torch.as_tensor(pr["source"]), **kw)
+
+
+def test_stage_wait_time_out_reports_ecuda_and_context_recovers():
+    """The bounded waits of the TMA-staged fine kernels (FP32 sweeps, fused
+    restriction, float-float and FP64 applies) made to run out on purpose
+    through a one-cycle wait limit: every entry point that launched one
+    returns ECUDA, the kernels drain their copies and exit, and with the
+    default limit restored the same context reproduces its earlier results
+    and solves to the oracle's residual."""
+    from helpers import oracle_problem
+    pr = small_problem(64, kind="chan", seed=3, kmin=1e-6)
+    s = gpu_solver(pr, prec=1)
+    s.setup_precond()
+    n = s.nnode
+    rng = np.random.default_rng(11)
+    r = torch.as_tensor(rng.standard_normal(n))
+    z0 = s.vcycle(r)
+    p = torch.as_tensor(rng.standard_normal(n)) * torch.as_tensor(1 - pr["mask"].astype(np.float64))
+    q0, d0 = s.apply_dot(p)
+    y0 = s.apply(r, thermo.FP64)
+    s.set_stage_wait(1)
+    for call in (lambda: s.vcycle(r), lambda: s.apply_dot(p), lambda: s.apply(r, thermo.FP64),
+                 lambda: s.apply(r, thermo.MIXED), s.setup_precond):
+        with pytest.raises(ThermoError) as e:
+            call()
+        assert e.value.status == thermo.ECUDA, e.value
+    s.set_stage_wait(0)
+    s.setup_precond()
+    assert torch.equal(s.vcycle(r), z0)
+    q1, d1 = s.apply_dot(p)
+    assert torch.equal(q1, q0) and d1 == d0
+    assert torch.equal(s.apply(r, thermo.FP64), y0)
+    u, info = s.solve(tol=1e-10)
+    assert info["status"] == thermo.OK
+    P = oracle_problem(pr)
+    res = P["b"] - P["A"] @ u.cpu().numpy()
+    assert np.linalg.norm(res) <= 1.5e-10 * np.linalg.norm(P["b"])
+    with pytest.raises(ThermoError) as e:
+        s.set_stage_wait(-1)
+    assert e.value.status == thermo.EINVAL
+    s.close()

@@ -1,0 +1,100 @@
+"""Solution parity at scale: solutions of the CUDA path through the C ABI
+against the FP64 oracle's own MMG-preconditioned CG (Sec. 4 solver with the
+multigrid cycle of Algorithm 1 as preconditioner) on the channel-tree
+workloads at contrasts 1e3, 1e6 and 1e9, for the plain FP64 form and the
+mixed form (FP32 cycle inside FP64 flexible CG).
+
+* 64^3: the oracle runs inside the test; whole solutions are compared.
+* 128^3: the oracle's reference solution at 4096 seeded nodes, its norms and
+  its compliance come from tests/golden/oracle_chan128_*.json, written by
+  tests/golden/make_oracle_solutions.py (which calls only the oracle).
+
+Bars (the target accuracy of the solver): relative solution error <= 1e-8,
+both in the 2-norm and node by node against the max-norm of the reference;
+the FP64 form's iteration count at tol 1e-8 within +-2 of the oracle's (the
+two build their local bases with different eigensolvers, so counts can
+differ by one or two).  Each assertion message states the counts.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+import torch
+
+from helpers import gpu_solver, oracle_problem, small_problem
+from oracle import krylov, mmg
+import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+KMINS = [1e-3, 1e-6, 1e-9]
+
+
+def _errors(u, ref):
+    d = u - ref
+    return float(np.linalg.norm(d) / np.linalg.norm(ref)), float(np.max(np.abs(d)) / np.max(np.abs(ref)))
+
+
+@pytest.fixture(scope="module", params=KMINS, ids=["1e3", "1e6", "1e9"])
+def chan64(request):
+    kmin = request.param
+    pr = small_problem(64, kind="chan", seed=3, kmin=kmin)
+    P = oracle_problem(pr)
+    H = mmg.MMG(P)
+    free = ~P["mask"]
+    u0 = H.coarse_guess(P["b"])
+    _, i8 = krylov.pcg(P["A"], P["b"], precond=H, u0=u0, tol=1e-8, free=free)
+    us, ist = krylov.pcg(P["A"], P["b"], precond=H, u0=u0, tol=1e-13, free=free)
+    return pr, P, us, i8["iters"], ist
+
+
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_solution_matches_oracle_64(chan64, prec):
+    pr, P, us, it_or, ist = chan64
+    s = gpu_solver(pr, prec=prec)
+    s.setup_precond()
+    u, info = s.solve(tol=1e-8)
+    e2, einf = _errors(u.cpu().numpy(), us)
+    msg = (f"kmin={pr['kmin']:g} prec={prec}: iters {info['iters']} (oracle {it_or}), err2 {e2:.2e}, "
+           f"errinf {einf:.2e}, oracle reference true residual {ist['relres_true']:.1e}")
+    assert info["rel_res_true"] <= 1e-8, msg
+    assert e2 <= 1e-8 and einf <= 1e-8, msg
+    if prec == 0:
+        assert abs(info["iters"] - it_or) <= 2, msg
+    s.close()
+
+
+def _golden(name):
+    p = os.path.join(GOLDEN, f"oracle_{name}.json")
+    if not os.path.exists(p):
+        pytest.skip(f"{p} not generated")
+    with open(p) as f:
+        return json.load(f)
+
+
+@pytest.mark.parametrize("name", ["chan128_1e3", "chan128_1e6", "chan128_1e9"])
+@pytest.mark.parametrize("prec", [0, 1], ids=["fp64", "mixed"])
+def test_solution_matches_oracle_128_sampled(name, prec):
+    gd = _golden(name)
+    pr = W.problem(name)
+    s = gpu_solver(pr, prec=prec)
+    s.setup_precond()
+    assert [lv["nvec"] for lv in s.hierarchy()] == gd["hierarchy"]["nvec"]
+    u, info = s.solve(tol=1e-8)
+    idx = np.asarray(gd["samples"])
+    ref = np.asarray(gd["values"])
+    ug = u[torch.as_tensor(idx, device=u.device)].cpu().numpy()
+    einf = float(np.max(np.abs(ug - ref)) / gd["norminf"])
+    e2s = float(np.linalg.norm(ug - ref) / np.linalg.norm(ref))
+    en = abs(float(torch.linalg.norm(u)) - gd["norm2"]) / gd["norm2"]
+    c = s.compliance(u)
+    ec = abs(c - gd["compliance"]) / abs(gd["compliance"])
+    msg = (f"{name} prec={prec}: iters {info['iters']} (oracle {gd['iters_1e-8']}), sampled errinf {einf:.2e}, "
+           f"sampled err2 {e2s:.2e}, norm {en:.2e}, compliance {ec:.2e}")
+    assert info["rel_res_true"] <= 1e-8, msg
+    assert einf <= 1e-8 and e2s <= 1e-8 and en <= 1e-8 and ec <= 1e-8, msg
+    if prec == 0:
+        assert abs(info["iters"] - gd["iters_1e-8"]) <= 2, msg
+    s.close()
