@@ -24,6 +24,7 @@
 #include <math.h>
 
 #include "common.cuh"
+#include "eigen.cuh"
 #include "kernels.h"
 
 namespace thermo {
@@ -249,12 +250,13 @@ __device__ __forceinline__ double kappa_sum8(const Geom& g, const double* k64, i
 // Eq. (8): level-1 bases.  Blocks are launched per class (last in x/y/z or
 // not) so that the shared-memory footprint matches the block's node count.
 constexpr int EIG_NT = 256;
+constexpr int EIG_EXTRA = 8;  // Ritz vectors beyond L carried into the FP64 refinement
 
 struct L1Smem {
   // offsets in bytes
-  size_t C, V, X, W, tmp, m, H, Y, cs, sn, cs64, sn64, pp, qq, sel, list, lmap, lam, sh, total;
+  size_t C, Y, X, W, m, H, Yr, cs64, sn64, pp, qq, sel, list, lmap, lam, lam32, scr, sh, total;
 };
-__host__ __device__ inline L1Smem l1_smem(int n2, int L, int nmap) {
+__host__ __device__ inline L1Smem l1_smem(int n2, int K, int nmap) {
   L1Smem s;
   size_t o = 0;
   auto al = [&](size_t bytes) {
@@ -262,30 +264,34 @@ __host__ __device__ inline L1Smem l1_smem(int n2, int L, int nmap) {
     o += (bytes + 15) & ~(size_t)15;
     return r;
   };
-  const int k2 = (L + 1) & ~1;
-  s.C = al((size_t)n2 * n2 * 4);
-  s.V = al((size_t)n2 * n2 * 4);
-  s.X = al((size_t)n2 * L * 8);
-  s.W = al((size_t)n2 * L * 8);
-  s.tmp = al((size_t)n2 * L * 8 + 8 * 64);
+  const int k2 = (K + 1) & ~1;
+  s.C = al((size_t)n2 * (n2 + 1) * 4);
+  s.Y = al((size_t)K * n2 * 4);
+  // X and W are contiguous: the FP32 eigensolver's factor storage aliases them
+  s.X = al((size_t)n2 * K * 8);
+  s.W = al((size_t)n2 * K * 8 + 8 * 64);
   s.m = al((size_t)n2 * 8);
   s.H = al((size_t)k2 * k2 * 8);
-  s.Y = al((size_t)k2 * k2 * 8);
-  s.cs = al((size_t)n2 / 2 * 4);
-  s.sn = al((size_t)n2 / 2 * 4);
+  s.Yr = al((size_t)k2 * k2 * 8);
   s.cs64 = al((size_t)k2 * 8);
   s.sn64 = al((size_t)k2 * 8);
-  s.pp = al((size_t)(n2 / 2 + k2) * 4);
-  s.qq = al((size_t)(n2 / 2 + k2) * 4);
-  s.sel = al((size_t)(n2 + k2) * 4);
+  s.pp = al((size_t)k2 * 4);
+  s.qq = al((size_t)k2 * 4);
+  s.sel = al((size_t)k2 * 4);
   s.list = al((size_t)n2 * 4);
   s.lmap = al((size_t)nmap * 4);
   s.lam = al((size_t)k2 * 8);
+  s.lam32 = al((size_t)k2 * 4);
+  s.scr = al(eig_scratch_floats(n2) * 4);
   s.sh = al(40 * 8);
   s.total = o;
   return s;
 }
 
+// One CTA per block: assemble C = M^-1/2 Ã M^-1/2 (FP32) over the block's free
+// nodes, take its K = L + 8 smallest eigenvectors with the FP32 solver of
+// eigen.cuh, map them to phi = M^-1/2 v in FP64, M-orthonormalise (FP64 MGS)
+// and refine by an FP64 Rayleigh-Ritz step on the sparse Ã; keep the L lowest.
 __global__ void __launch_bounds__(EIG_NT) k_level1_eigen(Geom g, const uint32_t* __restrict__ bits,
                                                          const double* __restrict__ k64, int L, int lx, int ly, int lz,
                                                          int n2, double* __restrict__ phi, double* __restrict__ eig,
@@ -301,17 +307,16 @@ __global__ void __launch_bounds__(EIG_NT) k_level1_eigen(Geom g, const uint32_t*
   const int wx = b + lx, wy = b + ly, wz = b + lz;  // nodes per axis of this block
   const int X0 = bx * b, Y0 = by * b, Z0 = bz * b;
   const int nmap = wx * wy * wz;
-  L1Smem S = l1_smem(n2, L, nmap);
+  const int Kmax = (L + EIG_EXTRA) < n2 ? (L + EIG_EXTRA) : n2;
+  L1Smem S = l1_smem(n2, Kmax, nmap);
+  const int lda = n2 + 1;
   float* C = (float*)(sm + S.C);
-  float* V = (float*)(sm + S.V);
+  float* Yf = (float*)(sm + S.Y);
   double* X = (double*)(sm + S.X);
   double* W = (double*)(sm + S.W);
-  double* tmp = (double*)(sm + S.tmp);
   double* m = (double*)(sm + S.m);
   double* H = (double*)(sm + S.H);
-  double* Y = (double*)(sm + S.Y);
-  float* cs = (float*)(sm + S.cs);
-  float* sn = (float*)(sm + S.sn);
+  double* Yr = (double*)(sm + S.Yr);
   double* cs64 = (double*)(sm + S.cs64);
   double* sn64 = (double*)(sm + S.sn64);
   int* pp = (int*)(sm + S.pp);
@@ -320,6 +325,8 @@ __global__ void __launch_bounds__(EIG_NT) k_level1_eigen(Geom g, const uint32_t*
   int* list = (int*)(sm + S.list);
   int* lmap = (int*)(sm + S.lmap);
   double* lam = (double*)(sm + S.lam);
+  float* lam32 = (float*)(sm + S.lam32);
+  float* scr = (float*)(sm + S.scr);
   double* sh = (double*)(sm + S.sh);
   const int tid = threadIdx.x, nt = blockDim.x;
   const long long cell = bx + (long long)g.nbx * (by + (long long)g.nby * bz);
@@ -341,13 +348,14 @@ __global__ void __launch_bounds__(EIG_NT) k_level1_eigen(Geom g, const uint32_t*
   __syncthreads();
   const int n = (int)sh[34];
   const int kk = n < L ? n : L;
+  const int K = n < Kmax ? n : Kmax;
   // mass and the Neumann matrix scaled by M^-1/2
   for (int i = tid; i < n; i += nt) {
     const int k = list[i];
     const int x = X0 + k % wx, y = Y0 + (k / wx) % wy, z = Z0 + k / (wx * wy);
     m[i] = kappa_sum8(g, k64, x, y, z) * g.vol * 0.125;
   }
-  for (int i = tid; i < n2 * n2; i += nt) C[i] = 0.f;
+  for (int i = tid; i < n * lda; i += nt) C[i] = 0.f;
   __syncthreads();
   for (int i = tid; i < n; i += nt) {
     const int k = list[i];
@@ -363,27 +371,25 @@ __global__ void __launch_bounds__(EIG_NT) k_level1_eigen(Geom g, const uint32_t*
           if (j < 0) continue;
           const double a = coupling(g, k64, x, y, z, ox, oy, oz);
           diag -= a;
-          C[i * n2 + j] = (float)(a / sqrt(m[i] * m[j]));
+          C[i * lda + j] = (float)(a / sqrt(m[i] * m[j]));
         }
-    C[i * n2 + i] = (float)(diag / m[i]);
-  }
-  for (int i = n + tid; i < n2; i += nt) C[i * n2 + i] = 3.0e38f;  // padding: never selected
-  __syncthreads();
-  if (n > 0) jacobi_eigen<float>(C, V, n2, cs, sn, pp, qq, sh, 14, 3e-7);
-  select_smallest<float>(C, n2, kk, sel);
-  // FP64 basis phi = M^-1/2 v, M-orthonormalised
-  for (int w = tid; w < n * L; w += nt) {
-    const int i = w / L, a = w % L;
-    X[w] = a < kk ? (double)V[i * n2 + sel[a]] / sqrt(m[i]) : 0.0;
+    C[i * lda + i] = (float)(diag / m[i]);
   }
   __syncthreads();
-  mgs(X, m, n, L, kk, sh);
+  if (n > 0) eig_lowest(C, lda, n, K, lam32, Yf, n2, scr, (float*)X, sh);
+  // FP64 basis phi = M^-1/2 v over the K vectors, M-orthonormalised
+  for (int w = tid; w < n * K; w += nt) {
+    const int i = w / K, a = w % K;
+    X[w] = (double)Yf[a * n2 + i] / sqrt(m[i]);
+  }
+  __syncthreads();
+  mgs(X, m, n, K, K, sh);
   // W = Ã X (difference form: (Ã x)_i = sum_{j in B} A_ij (x_j - x_i))
   for (int i = tid; i < n; i += nt) {
     const int k = list[i];
     const int x = X0 + k % wx, y = Y0 + (k / wx) % wy, z = Z0 + k / (wx * wy);
-    double acc[32];
-    for (int a = 0; a < kk; ++a) acc[a] = 0.0;
+    double acc[16];
+    for (int a = 0; a < K; ++a) acc[a] = 0.0;
     for (int oz = -1; oz <= 1; ++oz)
       for (int oy = -1; oy <= 1; ++oy)
         for (int ox = -1; ox <= 1; ++ox) {
@@ -393,18 +399,19 @@ __global__ void __launch_bounds__(EIG_NT) k_level1_eigen(Geom g, const uint32_t*
           const int j = lmap[xx + wx * (yy + wy * zz)];
           if (j < 0) continue;
           const double aij = coupling(g, k64, x, y, z, ox, oy, oz);
-          for (int a = 0; a < kk; ++a) acc[a] += aij * (X[j * L + a] - X[i * L + a]);
+          for (int a = 0; a < K; ++a) acc[a] += aij * (X[j * K + a] - X[i * K + a]);
         }
-    for (int a = 0; a < kk; ++a) W[i * L + a] = acc[a];
+    for (int a = 0; a < K; ++a) W[i * K + a] = acc[a];
   }
   __syncthreads();
-  if (kk > 0) rr_finish(X, W, n, L, kk, H, Y, cs64, sn64, pp + n2 / 2, qq + n2 / 2, sh, tmp, lam, sel + n2);
-  // outputs
+  // Rayleigh-Ritz on span(X): sorted Ritz pairs in X, lam (W reused as scratch)
+  if (K > 0) rr_finish(X, W, n, K, K, H, Yr, cs64, sn64, pp, qq, sh, W, lam, sel);
+  // outputs: the L lowest
   for (int k = tid; k < nmap; k += nt) {
     const int x = X0 + k % wx, y = Y0 + (k / wx) % wy, z = Z0 + k / (wx * wy);
     const int i = lmap[k];
     const long long nd = nidx(g, x, y, z);
-    for (int a = 0; a < L; ++a) phi[nd * L + a] = (i >= 0 && a < kk) ? X[i * L + a] : 0.0;
+    for (int a = 0; a < L; ++a) phi[nd * L + a] = (i >= 0 && a < kk) ? X[i * K + a] : 0.0;
   }
   if (tid < L) {
     eig[cell * L + tid] = tid < kk ? lam[tid] : 0.0;
@@ -422,7 +429,9 @@ cudaError_t level1_eigen(const Geom& g, const uint32_t* bits, const double* k64,
         if (nb <= 0) continue;
         const int nmap = (g.b + lx) * (g.b + ly) * (g.b + lz);
         const int n2 = (nmap + 1) & ~1;
-        const L1Smem S = l1_smem(n2, L1, nmap);
+        const int Kmax = (L1 + EIG_EXTRA) < n2 ? (L1 + EIG_EXTRA) : n2;
+        const L1Smem S = l1_smem(n2, Kmax, nmap);
+        if (S.total > 227 * 1024 || eig_lu_floats(n2, Kmax) * 4 > 2 * (size_t)n2 * Kmax * 8) return cudaErrorInvalidValue;
         cudaError_t e = cudaFuncSetAttribute(k_level1_eigen, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)S.total);
         if (e != cudaSuccess) return e;
@@ -565,9 +574,9 @@ cudaError_t level1_rap(const Geom& g, const uint32_t* bits, const double* k64, i
 // ---------------------------------------------------------------------------
 // Eq. (9): one CTA per group G of g^3 cells of the previous level.
 struct GSmem {
-  size_t C, V, X, W, tmp, H, Y, cs, sn, cs64, sn64, pp, qq, sel, act, lam, sh, total;
+  size_t C, Y, X, W, H, Yr, cs64, sn64, pp, qq, sel, alist, lam, lam32, scr, sh, total;
 };
-__host__ __device__ inline GSmem g_smem(int n2, int L) {
+__host__ __device__ inline GSmem g_smem(int n2, int K) {
   GSmem s;
   size_t o = 0;
   auto al = [&](size_t bytes) {
@@ -575,23 +584,22 @@ __host__ __device__ inline GSmem g_smem(int n2, int L) {
     o += (bytes + 15) & ~(size_t)15;
     return r;
   };
-  const int k2 = (L + 1) & ~1;
-  s.C = al((size_t)n2 * n2 * 4);
-  s.V = al((size_t)n2 * n2 * 4);
-  s.X = al((size_t)n2 * L * 8);
-  s.W = al((size_t)n2 * L * 8);
-  s.tmp = al((size_t)n2 * L * 8 + 8 * 64);
+  const int k2 = (K + 1) & ~1;
+  s.C = al((size_t)n2 * (n2 + 1) * 4);
+  s.Y = al((size_t)K * n2 * 4);
+  s.X = al((size_t)n2 * K * 8);  // X, W contiguous (aliased by the FP32 solver's factors)
+  s.W = al((size_t)n2 * K * 8 + 8 * 64);
   s.H = al((size_t)k2 * k2 * 8);
-  s.Y = al((size_t)k2 * k2 * 8);
-  s.cs = al((size_t)n2 / 2 * 4);
-  s.sn = al((size_t)n2 / 2 * 4);
+  s.Yr = al((size_t)k2 * k2 * 8);
   s.cs64 = al((size_t)k2 * 8);
   s.sn64 = al((size_t)k2 * 8);
-  s.pp = al((size_t)(n2 / 2 + k2) * 4);
-  s.qq = al((size_t)(n2 / 2 + k2) * 4);
-  s.sel = al((size_t)(n2 + k2) * 4);
-  s.act = al((size_t)n2 * 4);
+  s.pp = al((size_t)k2 * 4);
+  s.qq = al((size_t)k2 * 4);
+  s.sel = al((size_t)k2 * 4);
+  s.alist = al((size_t)n2 * 4);
   s.lam = al((size_t)k2 * 8);
+  s.lam32 = al((size_t)k2 * 4);
+  s.scr = al(eig_scratch_floats(n2) * 4);
   s.sh = al(40 * 8);
   s.total = o;
   return s;
@@ -605,106 +613,109 @@ __device__ __forceinline__ long long cell_of_local(const CLevel& prev, const CLe
 }
 __device__ __forceinline__ int nbr_index(int dx, int dy, int dz) { return (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1); }
 
+// entry (di, dj) of Ã_G = (A_prev)_GG - blockdiag D_c over local dofs (cell lc * Lp + i)
+__device__ __forceinline__ double group_entry(const CLevel& prev, const CLevel& cur, long long G,
+                                              const double* __restrict__ Tp, const double* __restrict__ Dc, int di,
+                                              int dj) {
+  const int g = cur.g, Lp = prev.L;
+  const int lci = di / Lp, i = di % Lp, lcj = dj / Lp, j = dj % Lp;
+  const int dx = lcj % g - lci % g, dy = (lcj / g) % g - (lci / g) % g, dz = lcj / (g * g) - lci / (g * g);
+  if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1) return 0.0;
+  const long long c = cell_of_local(prev, cur, G, lci);
+  double v = Tp[((c * 27 + nbr_index(dx, dy, dz)) * Lp + i) * Lp + j];
+  if (lci == lcj) v -= Dc[(c * Lp + i) * Lp + j];
+  return v;
+}
+
+// One CTA per group: Ã_G over the group's active dofs (FP32, symmetrised), its
+// K = L + 8 smallest eigenvectors with the FP32 solver of eigen.cuh, FP64
+// Gram-Schmidt and an FP64 Rayleigh-Ritz step on Ã_G from the FP64 tiles;
+// the L lowest form Psi (mass = identity: the "mass trick" after Eq. (9)).
 __global__ void __launch_bounds__(EIG_NT) k_group_eigen(CLevel prev, CLevel cur, const double* __restrict__ Tp,
                                                         const double* __restrict__ Dc, const uint8_t* __restrict__ actp,
                                                         int n2, double* __restrict__ Psi, double* __restrict__ eig,
                                                         uint8_t* __restrict__ actc) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int g = cur.g, Lp = prev.L, L = cur.L, ng = g * g * g, n = ng * Lp;
-  GSmem S = g_smem(n2, L);
+  const int Kmax = (L + EIG_EXTRA) < n2 ? (L + EIG_EXTRA) : n2;
+  GSmem S = g_smem(n2, Kmax);
+  const int lda = n2 + 1;
   float* C = (float*)(sm + S.C);
-  float* V = (float*)(sm + S.V);
+  float* Yf = (float*)(sm + S.Y);
   double* X = (double*)(sm + S.X);
   double* W = (double*)(sm + S.W);
-  double* tmp = (double*)(sm + S.tmp);
   double* H = (double*)(sm + S.H);
-  double* Y = (double*)(sm + S.Y);
-  float* cs = (float*)(sm + S.cs);
-  float* sn = (float*)(sm + S.sn);
+  double* Yr = (double*)(sm + S.Yr);
   double* cs64 = (double*)(sm + S.cs64);
   double* sn64 = (double*)(sm + S.sn64);
   int* pp = (int*)(sm + S.pp);
   int* qq = (int*)(sm + S.qq);
   int* sel = (int*)(sm + S.sel);
-  int* act = (int*)(sm + S.act);
+  int* alist = (int*)(sm + S.alist);
   double* lam = (double*)(sm + S.lam);
+  float* lam32 = (float*)(sm + S.lam32);
+  float* scr = (float*)(sm + S.scr);
   double* sh = (double*)(sm + S.sh);
   const int tid = threadIdx.x, nt = blockDim.x;
   const long long G = blockIdx.x;
-  // active dofs (compact order = local dof order)
-  for (int d = tid; d < n; d += nt) {
-    const long long c = cell_of_local(prev, cur, G, d / Lp);
-    act[d] = actp[c * Lp + d % Lp];
-  }
-  for (int i = tid; i < n2 * n2; i += nt) C[i] = 0.f;
-  __syncthreads();
+  // compact list of active dofs (local dof order), serial for determinism
   if (tid == 0) {
     int na = 0;
-    for (int d = 0; d < n; ++d) na += act[d] ? 1 : 0;
+    for (int d = 0; d < n; ++d) {
+      const long long c = cell_of_local(prev, cur, G, d / Lp);
+      if (actp[c * Lp + d % Lp]) alist[na++] = d;
+    }
     sh[34] = na;
   }
   __syncthreads();
   const int na = (int)sh[34];
   const int kk = na < L ? na : L;
-  // Ã_G = (A_prev)_GG - blockdiag D_c  (inactive dofs: huge diagonal)
-  for (int w = tid; w < n * n; w += nt) {
-    const int di = w / n, dj = w % n;
-    const int lci = di / Lp, i = di % Lp, lcj = dj / Lp, j = dj % Lp;
-    const int dx = lcj % g - lci % g, dy = (lcj / g) % g - (lci / g) % g, dz = lcj / (g * g) - lci / (g * g);
-    double v = 0.0;
-    if (dx >= -1 && dx <= 1 && dy >= -1 && dy <= 1 && dz >= -1 && dz <= 1) {
-      const long long c = cell_of_local(prev, cur, G, lci);
-      v = Tp[((c * 27 + nbr_index(dx, dy, dz)) * Lp + i) * Lp + j];
-      if (lci == lcj) v -= Dc[(c * Lp + i) * Lp + j];
-    }
-    if (!act[di] || !act[dj]) v = (di == dj) ? 3.0e38 : 0.0;
-    C[di * n2 + dj] = (float)v;
+  const int K = na < Kmax ? na : Kmax;
+  for (int w = tid; w < na * na; w += nt) {
+    const int a = w / na, bcol = w % na;
+    C[a * lda + bcol] = (float)group_entry(prev, cur, G, Tp, Dc, alist[a], alist[bcol]);
   }
-  for (int i = n + tid; i < n2; i += nt) C[i * n2 + i] = 3.0e38f;
   __syncthreads();
   // symmetrise (the FP64 tiles are symmetric up to rounding)
-  for (int w = tid; w < n * n; w += nt) {
-    const int di = w / n, dj = w % n;
-    if (di < dj) {
-      const float v = 0.5f * (C[di * n2 + dj] + C[dj * n2 + di]);
-      C[di * n2 + dj] = v;
-      C[dj * n2 + di] = v;
+  for (int w = tid; w < na * na; w += nt) {
+    const int a = w / na, bcol = w % na;
+    if (a < bcol) {
+      const float v = 0.5f * (C[a * lda + bcol] + C[bcol * lda + a]);
+      C[a * lda + bcol] = v;
+      C[bcol * lda + a] = v;
     }
   }
   __syncthreads();
-  jacobi_eigen<float>(C, V, n2, cs, sn, pp, qq, sh, 14, 3e-7);
-  select_smallest<float>(C, n2, kk, sel);
-  for (int w = tid; w < n * L; w += nt) {
-    const int i = w / L, a = w % L;
-    X[w] = (a < kk && act[i]) ? (double)V[i * n2 + sel[a]] : 0.0;
+  if (na > 0) eig_lowest(C, lda, na, K, lam32, Yf, n2, scr, (float*)X, sh);
+  for (int w = tid; w < na * K; w += nt) {
+    const int i = w / K, a = w % K;
+    X[w] = (double)Yf[a * n2 + i];
   }
   __syncthreads();
-  mgs(X, nullptr, n, L, kk, sh);
-  // W = Ã_G X in FP64 from the tiles
-  for (int w = tid; w < n * kk; w += nt) {
-    const int di = w / kk, a = w % kk;
-    const int lci = di / Lp, i = di % Lp;
-    const long long c = cell_of_local(prev, cur, G, lci);
-    double s = 0.0;
-    if (act[di]) {
-      for (int lcj = 0; lcj < ng; ++lcj) {
-        const int dx = lcj % g - lci % g, dy = (lcj / g) % g - (lci / g) % g, dz = lcj / (g * g) - lci / (g * g);
-        if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1) continue;
-        const double* T = Tp + ((c * 27 + nbr_index(dx, dy, dz)) * Lp + i) * Lp;
-        for (int j = 0; j < Lp; ++j) {
-          double t = T[j];
-          if (lci == lcj) t -= Dc[(c * Lp + i) * Lp + j];
-          if (act[lcj * Lp + j]) s += t * X[(lcj * Lp + j) * L + a];
-        }
-      }
+  mgs(X, nullptr, na, K, K, sh);
+  // W = Ã_G X in FP64 from the tiles (active rows and columns)
+  for (int w = tid; w < na * K; w += nt) {
+    const int ia = w / K, a = w % K;
+    const int di = alist[ia];
+    double sacc = 0.0;
+    for (int ja = 0; ja < na; ++ja) {
+      const int dj = alist[ja];
+      const int lci = di / Lp, lcj = dj / Lp;
+      const int dx = lcj % g - lci % g, dy = (lcj / g) % g - (lci / g) % g, dz = lcj / (g * g) - lci / (g * g);
+      if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1) continue;
+      sacc += group_entry(prev, cur, G, Tp, Dc, di, dj) * X[ja * K + a];
     }
-    W[di * L + a] = s;
+    W[w] = sacc;
   }
   __syncthreads();
-  if (kk > 0) rr_finish(X, W, n, L, kk, H, Y, cs64, sn64, pp + n2 / 2, qq + n2 / 2, sh, tmp, lam, sel + n2);
-  for (int w = tid; w < n * L; w += nt) {
-    const int i = w / L, a = w % L;
-    Psi[G * (long long)n * L + w] = a < kk ? X[i * L + a] : 0.0;
+  if (K > 0) rr_finish(X, W, na, K, K, H, Yr, cs64, sn64, pp, qq, sh, W, lam, sel);
+  // Psi rows in local dof order (inactive rows zero), the L lowest columns
+  double* out = Psi + G * (long long)n * L;
+  for (int w = tid; w < n * L; w += nt) out[w] = 0.0;
+  __syncthreads();
+  for (int w = tid; w < na * L; w += nt) {
+    const int ia = w / L, a = w % L;
+    out[alist[ia] * L + a] = a < kk ? X[ia * K + a] : 0.0;
   }
   if (tid < L) {
     eig[G * L + tid] = tid < kk ? lam[tid] : 0.0;
@@ -716,7 +727,8 @@ cudaError_t group_eigen(const CLevel& prev, const CLevel& cur, const double* til
                         cudaStream_t st) {
   const int n = cur.g * cur.g * cur.g * prev.L;
   const int n2 = (n + 1) & ~1;
-  const GSmem S = g_smem(n2, cur.L);
+  const int Kmax = (cur.L + EIG_EXTRA) < n2 ? (cur.L + EIG_EXTRA) : n2;
+  const GSmem S = g_smem(n2, Kmax);
   if (S.total > 227 * 1024) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(k_group_eigen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.total);
   if (e != cudaSuccess) return e;
