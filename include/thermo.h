@@ -120,6 +120,8 @@ typedef struct {
                                        residual each time the recursive residual has
                                        dropped by this many decades (iterative refinement
                                        around the low-precision cycle); 0: never */
+  int density_fp32;                 /* 0: thermo_set_density's x is double[M]; 1: float[M]
+                                       (widened to FP64 on the device; default 0) */
 } thermo_options;
 
 typedef struct {
@@ -163,11 +165,22 @@ thermo_status thermo_create(const int grid[3], const double h[3],
                             const double *source, void *cuda_stream,
                             const thermo_options *opt, thermo_ctx **out);
 
-/* Set the design (Sec. 2.1 Eq. (1)): x device double[M] in [0,1] (not
- * checked), p >= 1, 0 < kmin <= kmax.  kappa is evaluated once per element
- * here and kept in FP64/FP32/BF16 copies.  Marks the preconditioner stale. */
-thermo_status thermo_set_density(thermo_ctx *ctx, const double *x, double p,
+/* Set the design (Sec. 2.1 Eq. (1)): x device double[M] (float[M] when
+ * opt.density_fp32 = 1) in [0,1] (not checked), p >= 1, 0 < kmin <= kmax.
+ * kappa is evaluated once per element here and kept in FP64/FP32/BF16
+ * copies.  Marks the preconditioner stale. */
+thermo_status thermo_set_density(thermo_ctx *ctx, const void *x, double p,
                                  double kmin, double kmax);
+
+/* As thermo_set_density (Sec. 2.1 Eq. (1)), but a preconditioner built for an
+ * earlier design stays in use: the operator, the load lifting and the fine
+ * smoother's conductivities follow the new design, while the coarse spaces,
+ * Galerkin operators and the smoother's spectral interval are the old ones.
+ * CG then solves the new system with the old preconditioner, which stays
+ * effective for small design changes (a finite-difference perturbation of a
+ * few elements, a damped design step).  If no preconditioner exists yet this
+ * is thermo_set_density.  Same arguments and errors. */
+thermo_status thermo_update_density(thermo_ctx *ctx, const void *x, double p, double kmin, double kmax);
 
 /* Build the MMG hierarchy for the current design (Sec. 3): local spectral
  * problems (Eq. (8)) on every block, M-orthonormal bases, Galerkin operators,
@@ -381,8 +394,10 @@ thermo_status thermo_bench_kernel(thermo_ctx *ctx, int which, int reps, double *
  *   THERMO_KT_COARSE   everything below the fine grid in one V-cycle
  *   THERMO_KT_CGVEC    CG vector kernels (update, beta, direction, conversion)
  * bytes/flops are the algorithmic DRAM bytes and floating-point operations of
- * the timed launches: compulsory traffic of each array once, 0 where not
- * defined (coarse). */
+ * the timed launches: compulsory traffic of each array once per launch (for
+ * THERMO_KT_COARSE: every coarse launch of the cycle, tiles 27 L^2 and l1
+ * inverses L^2 per cell, vectors, group bases, the coarsest FP64 inverse;
+ * levels small enough to stay in L2 are counted all the same). */
 enum {
   THERMO_KT_APPLY64 = 0,
   THERMO_KT_SMOOTH = 1,

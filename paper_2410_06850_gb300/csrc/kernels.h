@@ -41,6 +41,7 @@ cudaError_t count_mask(const Geom& g, const uint8_t* nat, long long n, int* out,
 cudaError_t simp_kappa(const Geom& g, const double* x, double p, double kmin, double kmax, double* k64,
                        float* k32, bf16* k16, float* klo, cudaStream_t st);
 cudaError_t load_vector(const Geom& g, const double* q, double* f, cudaStream_t st);
+cudaError_t widen_f32(const float* a, double* b, long long n, cudaStream_t st);
 cudaError_t dirichlet_rhs(const Geom& g, const uint32_t* bits, const double* k64, const double* f,
                           const double* TDpad, double* b, cudaStream_t st);
 // y = a*x + b*y style helpers on padded FP64 vectors (interior rows)

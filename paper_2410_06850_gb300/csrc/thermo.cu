@@ -62,6 +62,7 @@ struct thermo_ctx {
   std::vector<double> hist;  // relative recursive residual at each check of the last solve
   bool kt_on = false;
   KTimer kt[THERMO_KT_COUNT];
+  double coarse_bytes = 0.0;  // algorithmic bytes of the coarse launches of the current cycle (timers on)
   cudaStream_t st = nullptr;
   thermo_options opt;
   Geom g;
@@ -235,6 +236,7 @@ extern "C" thermo_status thermo_create(const int grid[3], const double h[3], con
   if (opt.smoother == 1 && (opt.cheb_degree < 1 || opt.cheb_degree > 64 || !(opt.cheb_ratio > 1.0) || opt.power_iters < 1))
     return fail(ctx, THERMO_EINVAL, "Chebyshev needs 1 <= degree <= 64, ratio > 1, power_iters >= 1");
   if (opt.nvec[0] < 1 || opt.nvec[0] > 6) return fail(ctx, THERMO_EINVAL, "nvec[0] must be in 1..6");
+  if (opt.density_fp32 != 0 && opt.density_fp32 != 1) return fail(ctx, THERMO_EINVAL, "density_fp32 must be 0 or 1");
   Geom& g = ctx->g;
   memset(&g, 0, sizeof(g));
   g.Nx = grid[0];
@@ -440,12 +442,15 @@ extern "C" const char* thermo_last_error(const thermo_ctx* ctx) {
   return ctx->err.c_str();
 }
 
-extern "C" thermo_status thermo_set_density(thermo_ctx* ctx, const double* x, double p, double kmin, double kmax) {
+extern "C" thermo_status thermo_set_density(thermo_ctx* ctx, const void* x, double p, double kmin, double kmax) {
   if (!ctx) return THERMO_EINVAL;
   if (!x) return fail(ctx, THERMO_EINVAL, "x is NULL");
   if (!(p >= 1.0) || !(kmin > 0.0) || !(kmax >= kmin) || !std::isfinite(kmax))
     return fail(ctx, THERMO_EINVAL, "need p >= 1 and 0 < kmin <= kmax");
-  CK(cudaMemcpyAsync(ctx->xd, x, ctx->nelem * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
+  if (ctx->opt.density_fp32)
+    CK(widen_f32(static_cast<const float*>(x), ctx->xd, ctx->nelem, ctx->st));
+  else
+    CK(cudaMemcpyAsync(ctx->xd, x, ctx->nelem * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
   CK(simp_kappa(ctx->g, ctx->xd, p, kmin, kmax, ctx->k64, ctx->k32, ctx->k16, ctx->klo, ctx->st));
   // lifted right-hand side b = f - A_FD T_D (b_D = T_D)
   CK(dirichlet_rhs(ctx->g, ctx->bits, ctx->k64, ctx->f, ctx->TD, ctx->blift, ctx->st));
@@ -455,6 +460,14 @@ extern "C" thermo_status thermo_set_density(thermo_ctx* ctx, const double* x, do
   ctx->have_density = true;
   ctx->have_precond = false;
   return THERMO_OK;
+}
+
+extern "C" thermo_status thermo_update_density(thermo_ctx* ctx, const void* x, double p, double kmin, double kmax) {
+  if (!ctx) return THERMO_EINVAL;
+  const bool keep = ctx->have_precond;
+  const thermo_status s = thermo_set_density(ctx, x, p, kmin, kmax);
+  if (s == THERMO_OK) ctx->have_precond = keep;
+  return s;
 }
 
 // ---------------------------------------------------------------------------
@@ -648,12 +661,31 @@ static double fine_bytes(const Geom& g, double s_node, double s_elem) {
   return n * s_node + m * s_elem + n / 8.0;  // + Dirichlet bitmask
 }
 
+// algorithmic bytes of the coarse kernels (each array once): tiles 27 L^2 per cell,
+// l1 inverses L^2 per cell, vectors L per cell, group bases g^3 Lprev L per group
+static double cb_tiles(const CLevel& c, double ts) { return (double)c.ncell * 27.0 * c.L * c.L * ts; }
+static double cb_vec(const CLevel& c, double ts) { return (double)c.ncell * c.L * ts; }
+static double cb_psi(const CLevel& f, const CLevel& c, double ts) {
+  return (double)c.ncell * c.g * c.g * c.g * f.L * c.L * ts;
+}
+static inline void cb_add(thermo_ctx* ctx, double b) {
+  if (ctx->kt_on) ctx->coarse_bytes += b;
+}
+
 template <class T>
 static cudaError_t coarse_cycle(thermo_ctx* ctx, int l) {
   cudaStream_t st = ctx->st;
   Lev& lv = ctx->lev[l];
   cudaError_t e;
-  if (l == ctx->nlev) return dense_gemv<T>(ctx->ncoarse, ctx->Ainv, lvr<T>(lv), lve<T>(lv), st);
+  const double ts = sizeof(T);
+  if (l == ctx->nlev) {
+    cb_add(ctx, (double)ctx->ncoarse * ctx->ncoarse * 8.0 + 2.0 * ctx->ncoarse * ts);  // FP64 inverse, x, y
+    return dense_gemv<T>(ctx->ncoarse, ctx->Ainv, lvr<T>(lv), lve<T>(lv), st);
+  }
+  const CLevel& cl = lv.cl;
+  const double b_smooth0 = (double)cl.ncell * cl.L * cl.L * ts + 2.0 * cb_vec(cl, ts);
+  const double b_smooth = cb_tiles(cl, ts) + (double)cl.ncell * cl.L * cl.L * ts + 3.0 * cb_vec(cl, ts);
+  const double b_resid = cb_tiles(cl, ts) + 3.0 * cb_vec(cl, ts);
   // sweeps on this level: nu_coarse, multiplied by nu_growth per level below level 1
   int nu = ctx->opt.nu_coarse;
   for (int k = 1; k < l && nu < 64; ++k) nu *= ctx->opt.nu_growth;
@@ -661,8 +693,10 @@ static cudaError_t coarse_cycle(thermo_ctx* ctx, int l) {
   T* E = lve<T>(lv);
   T* Tt = lvt<T>(lv);
   if ((e = coarse_smooth0<T>(lv.cl, lvD<T>(lv), lvr<T>(lv), E, st)) != cudaSuccess) return e;
+  cb_add(ctx, b_smooth0);
   for (int s = 1; s < nu; ++s) {
     if ((e = coarse_smooth<T>(lv.cl, lvT<T>(lv), lvD<T>(lv), lvr<T>(lv), E, Tt, st)) != cudaSuccess) return e;
+    cb_add(ctx, b_smooth);
     std::swap(E, Tt);
   }
   Lev& nx = ctx->lev[l + 1];
@@ -671,12 +705,16 @@ static cudaError_t coarse_cycle(thermo_ctx* ctx, int l) {
   const int reps = (ctx->opt.w_from > 0 && l >= ctx->opt.w_from && l + 1 < ctx->nlev) ? 2 : 1;
   for (int c = 0; c < reps; ++c) {
     if ((e = coarse_residual<T>(lv.cl, lvT<T>(lv), lvr<T>(lv), E, lvs<T>(lv), st)) != cudaSuccess) return e;
+    cb_add(ctx, b_resid);
     if ((e = coarse_restrict<T>(lv.cl, nx.cl, lvP<T>(nx), lvs<T>(lv), lvr<T>(nx), st)) != cudaSuccess) return e;
+    cb_add(ctx, cb_psi(cl, nx.cl, ts) + cb_vec(cl, ts) + cb_vec(nx.cl, ts));
     if ((e = coarse_cycle<T>(ctx, l + 1)) != cudaSuccess) return e;
     if ((e = coarse_prolong<T>(lv.cl, nx.cl, lvP<T>(nx), lve<T>(nx), E, st)) != cudaSuccess) return e;
+    cb_add(ctx, cb_psi(cl, nx.cl, ts) + cb_vec(nx.cl, ts) + 2.0 * cb_vec(cl, ts));
   }
   for (int s = 0; s < nu; ++s) {
     if ((e = coarse_smooth<T>(lv.cl, lvT<T>(lv), lvD<T>(lv), lvr<T>(lv), E, Tt, st)) != cudaSuccess) return e;
+    cb_add(ctx, b_smooth);
     std::swap(E, Tt);
   }
   if (E != lve<T>(lv)) {
@@ -728,12 +766,13 @@ static cudaError_t vcycle_fine(thermo_ctx* ctx, const S* kap, const S* r, S* b0,
   if ((e = fine_restrict<S>(g, ctx->bits, kap, r, buf[cur], phi, rc, L1, st)) != cudaSuccess) return e;
   kt_end(ctx, THERMO_KT_RESTRICT, ctx->kt_on ? fine_bytes(g, 2 * s + L1 * c, s) + (double)l1.cl.ncell * L1 * c : 0.0);
   kt_begin(ctx, THERMO_KT_COARSE);
+  ctx->coarse_bytes = 0.0;
   if (sizeof(C) == 8)
     e = coarse_cycle<double>(ctx, 1);
   else
     e = coarse_cycle<float>(ctx, 1);
   if (e != cudaSuccess) return e;
-  kt_end(ctx, THERMO_KT_COARSE, 0.0);
+  kt_end(ctx, THERMO_KT_COARSE, ctx->coarse_bytes);
   // prolongation (in place) and post-smoothing from the prolonged iterate
   kt_begin(ctx, THERMO_KT_PROLONG);
   if ((e = fine_prolong<S>(g, phi, ec, buf[cur], L1, st)) != cudaSuccess) return e;

@@ -188,6 +188,15 @@ cudaError_t simp_kappa(const Geom& g, const double* x, double p, double kmin, do
   return cudaGetLastError();
 }
 
+__global__ void k_widen(const float* __restrict__ a, double* __restrict__ b, long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    b[i] = (double)a[i];
+}
+cudaError_t widen_f32(const float* a, double* b, long long n, cudaStream_t st) {
+  note_launch(), k_widen<<<grid1(n), 256, 0, st>>>(a, b, n);
+  return cudaGetLastError();
+}
+
 // f_i = sum_{e contains i} q_e |e| / 8
 __global__ void k_load(Geom g, const double* __restrict__ q, double* __restrict__ f) {
   const long long n = (long long)g.nx * g.ny * g.nz;

@@ -32,7 +32,7 @@ EXPORTED = ["thermo_default_options", "thermo_create", "thermo_set_density", "th
             "thermo_hierarchy", "thermo_export_level", "thermo_filter", "thermo_oc_update",
             "thermo_launch_count", "thermo_bench_kernel", "thermo_apply_dot",
             "thermo_kernel_timers", "thermo_kernel_time", "thermo_dot_noalloc", "thermo_residual_history",
-            "thermo_set_stage_wait", "thermo_dense_spd_inverse"]
+            "thermo_set_stage_wait", "thermo_dense_spd_inverse", "thermo_update_density"]
 
 
 class thermo_options(C.Structure):
@@ -42,7 +42,8 @@ class thermo_options(C.Structure):
                 ("max_iter", C.c_int), ("flexible", C.c_int), ("check_every", C.c_int),
                 ("smoother", C.c_int), ("cheb_degree", C.c_int), ("cheb_ratio", C.c_double),
                 ("power_iters", C.c_int), ("outer_apply", C.c_int),
-                ("nu_growth", C.c_int), ("w_from", C.c_int), ("restart_decades", C.c_double)]
+                ("nu_growth", C.c_int), ("w_from", C.c_int), ("restart_decades", C.c_double),
+                ("density_fp32", C.c_int)]
 
 
 class thermo_solve_info(C.Structure):
@@ -75,6 +76,7 @@ def lib():
         L.thermo_default_options.argtypes = [ip, C.POINTER(thermo_options)]
         L.thermo_create.argtypes = [ip, dp, vp, vp, vp, vp, C.POINTER(thermo_options), C.POINTER(vp)]
         L.thermo_set_density.argtypes = [vp, vp, C.c_double, C.c_double, C.c_double]
+        L.thermo_update_density.argtypes = [vp, vp, C.c_double, C.c_double, C.c_double]
         L.thermo_setup_precond.argtypes = [vp]
         L.thermo_solve.argtypes = [vp, vp, vp, C.c_double, C.POINTER(thermo_solve_info)]
         L.thermo_sensitivity.argtypes = [vp, vp, vp]
@@ -195,9 +197,17 @@ class Solver:
             pass
 
     # -- C ABI, same names
+    def _design(self, x):
+        return _dev(x, torch.float32 if self.options.density_fp32 else torch.float64)
+
     def set_density(self, x, p, kmin, kmax):
-        self._x = _dev(x, torch.float64)
+        self._x = self._design(x)
         return self._check(lib().thermo_set_density(self.ctx, _ptr(self._x), float(p), float(kmin), float(kmax)))
+
+    def update_density(self, x, p, kmin, kmax):
+        """thermo_update_density: new design, the current preconditioner kept."""
+        self._x = self._design(x)
+        return self._check(lib().thermo_update_density(self.ctx, _ptr(self._x), float(p), float(kmin), float(kmax)))
 
     def setup_precond(self):
         return self._check(lib().thermo_setup_precond(self.ctx))

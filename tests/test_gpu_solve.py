@@ -340,3 +340,46 @@ def test_coarse_guess_is_the_galerkin_solution(kind, kmin):
         H = mmg.MMG(P)
         assert relerr(u0, H.coarse_guess(P["b"])) < 1e-4
     s.close()
+
+
+def test_fp32_density_input_matches_fp64_input():
+    """opt.density_fp32: thermo_set_density reads float x (widened on the
+    device); for an FP32-representable design the solution is bitwise the one
+    of the FP64 input."""
+    pr = small_problem(32, kind="smooth")
+    x32 = pr["x"].astype(np.float32)
+    s64 = gpu_solver(dict(pr, x=x32.astype(np.float64)), prec=1)
+    s32 = gpu_solver(dict(pr, x=x32), prec=1, density_fp32=1)
+    out = []
+    for s in (s64, s32):
+        s.setup_precond()
+        u, info = s.solve(tol=1e-10)
+        out.append((u.cpu().numpy(), info["iters"], s.sensitivity(u).cpu().numpy()))
+        s.close()
+    assert out[0][1] == out[1][1]
+    assert np.array_equal(out[0][0], out[1][0]) and np.array_equal(out[0][2], out[1][2])
+
+
+def test_update_density_keeps_the_preconditioner():
+    """thermo_update_density: a perturbed design is solved with the preconditioner
+    of the earlier design (no new set-up), to the oracle's residual on the new
+    operator; thermo_set_density instead marks the preconditioner stale."""
+    pr = small_problem(32, kind="smooth", kmin=1e-3)
+    s = gpu_solver(pr, prec=1)
+    s.setup_precond()
+    u0, i0 = s.solve(tol=1e-10)
+    x2 = pr["x"].copy()
+    for e in (100, 5000, 20000):  # finite-difference sized perturbations
+        x2[e] += 1e-3
+    s.update_density(torch.as_tensor(x2), pr["p"], pr["kmin"], pr["kmax"])
+    u, info = s.solve(tol=1e-10)
+    P = oracle_problem(dict(pr, x=x2))
+    res = P["b"] - P["A"] @ u.cpu().numpy()
+    assert np.linalg.norm(res) <= 1.5e-10 * np.linalg.norm(P["b"])
+    assert info["iters"] <= i0["iters"] + 2, (info["iters"], i0["iters"])
+    from paper_2410_06850_gb300 import ThermoError, thermo
+    s.set_density(torch.as_tensor(x2), pr["p"], pr["kmin"], pr["kmax"])
+    with pytest.raises(ThermoError) as e:
+        s.solve()
+    assert e.value.status == thermo.ESTATE
+    s.close()
