@@ -122,6 +122,11 @@ typedef struct {
                                        around the low-precision cycle); 0: never */
   int density_fp32;                 /* 0: thermo_set_density's x is double[M]; 1: float[M]
                                        (widened to FP64 on the device; default 0) */
+  int fine_engine;                  /* FP32 fine sweeps and applies on cubic elements:
+                                       0 (default) the separable engine (box sums of the
+                                       Q1 operator, one x column per warp, rows in
+                                       registers); 1 the two-nodes-per-lane engine
+                                       (grids with Nx a multiple of 64) */
 } thermo_options;
 
 typedef struct {

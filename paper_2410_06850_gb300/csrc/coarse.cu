@@ -21,6 +21,36 @@ __device__ __forceinline__ long long nbr_cell(const CLevel& lv, long long c, int
   return nx + (long long)lv.mx * (ny + (long long)lv.my * nz);
 }
 
+// row . x of one tile row; with a compile-time L that fills whole 16-byte
+// vectors (rows and cell vectors then start on 16-byte boundaries) the loads
+// are 16 bytes wide
+template <class T, int LT>
+__device__ __forceinline__ T row_dot(const T* __restrict__ row, const T* __restrict__ xv, int L) {
+  T s = T(0);
+  if constexpr (LT > 0 && sizeof(T) == 4 && LT % 4 == 0) {
+#pragma unroll
+    for (int j = 0; j < LT; j += 4) {
+      const float4 a = *reinterpret_cast<const float4*>(row + j);
+      const float4 b = *reinterpret_cast<const float4*>(xv + j);
+      s = fma(a.x, b.x, s);
+      s = fma(a.y, b.y, s);
+      s = fma(a.z, b.z, s);
+      s = fma(a.w, b.w, s);
+    }
+  } else if constexpr (LT > 0 && sizeof(T) == 8 && LT % 2 == 0) {
+#pragma unroll
+    for (int j = 0; j < LT; j += 2) {
+      const double2 a = *reinterpret_cast<const double2*>(row + j);
+      const double2 b = *reinterpret_cast<const double2*>(xv + j);
+      s = fma(a.x, b.x, s);
+      s = fma(a.y, b.y, s);
+    }
+  } else {
+    for (int j = 0; j < L; ++j) s += row[j] * xv[j];
+  }
+  return s;
+}
+
 // (A x)_row for row (c, i); LT > 0: compile-time L, LT == 0: runtime lv.L
 template <class T, int LT>
 __device__ __forceinline__ T tile_row(const CLevel& lv, const T* __restrict__ tiles, const T* __restrict__ x,
@@ -31,10 +61,7 @@ __device__ __forceinline__ T tile_row(const CLevel& lv, const T* __restrict__ ti
     bool ok;
     const long long nc = nbr_cell(lv, c, n, ok);
     if (!ok) continue;
-    const T* row = tiles + (((c * 27 + n) * L) + i) * (long long)L;
-    const T* xv = x + nc * L;
-#pragma unroll
-    for (int j = 0; j < L; ++j) s += row[j] * xv[j];
+    s += row_dot<T, LT>(tiles + (((c * 27 + n) * L) + i) * (long long)L, x + nc * L, L);
   }
   return s;
 }
@@ -108,22 +135,28 @@ __global__ void k_ccell(CLevel lv, const T* __restrict__ tiles, const T* __restr
   extern __shared__ __align__(16) unsigned char sm_raw[];
   const int L = lv.L;
   const int LL = L * L;
-  T* ts = reinterpret_cast<T*>(sm_raw);  // [27][L][L]
-  T* xs = ts + 27 * LL;                  // [27][L] (zero outside the grid)
+  constexpr int V = 16 / sizeof(T);      // elements per 16-byte chunk
+  const long long c = blockIdx.x;
+  // the cell's 27 tiles start at element c * 27 L^2, generally not on a 16-byte
+  // boundary: copy the aligned 16-byte chunks that cover them (the allocation
+  // has slack past its end) and index the tiles from the head offset
+  const long long e0 = c * 27 * (long long)LL;
+  const long long a0 = e0 & ~(long long)(V - 1);
+  const int head = (int)(e0 - a0);
+  const int nchunk = (int)((e0 + 27 * LL - a0 + V - 1) / V);
+  T* buf = reinterpret_cast<T*>(sm_raw);  // nchunk * V elements
+  T* ts = buf + head;                     // [27][L][L]
+  T* xs = buf + ((nchunk * V + V - 1) / V) * V;  // [27][L] (zero outside the grid)
   T* part = xs + 27 * L;                 // [27][L]
   T* res = part + 27 * L;                // [L]
-  const long long c = blockIdx.x;
   const int cx = (int)(c % lv.mx);
   const long long tt = c / lv.mx;
   const int cy = (int)(tt % lv.my), cz = (int)(tt / lv.my);
-  const T* tg = tiles + c * 27 * (long long)LL;
-  // asynchronous element copies (all in flight at once), completed before the barrier
-  for (int k = threadIdx.x; k < 27 * LL; k += blockDim.x) {
-    const unsigned dst = (unsigned)__cvta_generic_to_shared(ts + k);
-    if (sizeof(T) == 8)
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(dst), "l"(tg + k) : "memory");
-    else
-      asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(dst), "l"(tg + k) : "memory");
+  // asynchronous 16-byte copies (all in flight at once), completed before the barrier
+  for (int k = threadIdx.x; k < nchunk; k += blockDim.x) {
+    const unsigned dst = (unsigned)__cvta_generic_to_shared(buf + (long long)k * V);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(tiles + a0 + (long long)k * V)
+                 : "memory");
   }
   asm volatile("cp.async.commit_group;\n" ::: "memory");
   for (int k = threadIdx.x; k < 27 * L; k += blockDim.x) {
@@ -174,7 +207,8 @@ template <class T, int MODE>
 static void launch_ccell(const CLevel& lv, const T* tiles, const T* Dinv, const T* r, const T* x, T* out,
                          cudaStream_t st) {
   const int nt = ((27 * lv.L + 31) / 32) * 32;
-  const size_t sm = ((size_t)27 * lv.L * lv.L + (size_t)55 * lv.L) * sizeof(T);
+  const size_t V = 16 / sizeof(T);
+  const size_t sm = ((size_t)27 * lv.L * lv.L + 2 * V + (size_t)55 * lv.L) * sizeof(T);
   if (sm > 48 * 1024) cudaFuncSetAttribute(k_ccell<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   note_launch(), k_ccell<T, MODE><<<(unsigned)lv.ncell, nt > 1024 ? 1024 : nt, sm, st>>>(lv, tiles, Dinv, r, x, out);
 }
@@ -204,6 +238,37 @@ __global__ void k_crestrict(CLevel f, CLevel cs, const T* __restrict__ Psi, cons
         }
     rc[t] = s;
   }
+}
+
+// The same restriction with Q = g^3 <= 32 threads per output (one per cell of
+// the group, lanes of one warp), their partial sums over the cell's Lf basis
+// rows combined by a fixed shuffle tree: Q times the parallelism for the small
+// deep levels, where one thread per output left most of the GPU idle.
+template <class T, int Q>
+__global__ void k_crestrict_q(CLevel f, CLevel cs, const T* __restrict__ Psi, const T* __restrict__ res,
+                              T* __restrict__ rc) {
+  const int g = cs.g, Lf = f.L, Lc = cs.L;
+  const int nloc = g * g * g * Lf;
+  const long long nout = cs.ncell * Lc;
+  const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const int lc = (int)(gt % Q);
+  const long long t = gt / Q;
+  T s = T(0);
+  if (t < nout) {
+    const long long G = t / Lc;
+    const int k = (int)(t - G * Lc);
+    const int gx = (int)(G % cs.mx);
+    const long long tt = G / cs.mx;
+    const int gy = (int)(tt % cs.my), gz = (int)(tt / cs.my);
+    const int lx = lc % g, ly = (lc / g) % g, lz = lc / (g * g);
+    const long long c = (gx * g + lx) + (long long)f.mx * ((gy * g + ly) + (long long)f.my * (gz * g + lz));
+    const T* ps = Psi + G * (long long)nloc * Lc + (long long)lc * Lf * Lc + k;
+    const T* rv = res + c * Lf;
+    for (int i = 0; i < Lf; ++i) s = fma(ps[(long long)i * Lc], rv[i], s);
+  }
+#pragma unroll
+  for (int o = Q / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (t < nout && lc == 0) rc[t] = s;
 }
 
 // e[c][i] += sum_k Psi[G(c)][lc*Lf + i][k] ec[G][k]
@@ -303,7 +368,14 @@ cudaError_t coarse_smooth(const CLevel& lv, const T* tiles, const T* Dinv, const
 }
 template <class T>
 cudaError_t coarse_restrict(const CLevel& f, const CLevel& cs, const T* Psi, const T* res, T* rc, cudaStream_t st) {
-  note_launch(), k_crestrict<T><<<cgrid(cs.ncell * cs.L, 128), 128, 0, st>>>(f, cs, Psi, res, rc);
+  const long long nout = cs.ncell * cs.L;
+  const int q = cs.g * cs.g * cs.g;
+  if (q == 8) {
+    const long long nb = (nout * 8 + 255) / 256;
+    note_launch(), k_crestrict_q<T, 8><<<(unsigned)nb, 256, 0, st>>>(f, cs, Psi, res, rc);
+  } else {
+    note_launch(), k_crestrict<T><<<cgrid(nout, 128), 128, 0, st>>>(f, cs, Psi, res, rc);
+  }
   return cudaGetLastError();
 }
 template <class T>

@@ -41,6 +41,7 @@ struct Geom {
   // fine tile decomposition (nodes); tiles are block-aligned
   int TX, TY, ZC;           // tile width / height, z planes per CTA chunk
   int NZ2, NZD;             // z chunks (ragged) of the two-nodes-per-lane and float-float engines
+  int NZ3;                  // z chunks of the separable FP32 engine (0: engine not used)
   // bounded waits of the TMA-staged fine kernels (one word per context, on its device)
   int* err;                 // set to 1 by a kernel whose stage wait gave up
   long long wait;           // stage wait limit in clock64 cycles after a first non-blocking test

@@ -554,6 +554,9 @@ cudaError_t fine_apply_f64(const Geom& g, const uint32_t* mask, const double* ka
 template <class S>
 cudaError_t fine_apply_lp(const Geom& g, const uint32_t* mask, const S* kap, const S* u, S* y, cudaStream_t st,
                           bool mask_input) {
+  if constexpr (sizeof(S) == 4) {
+    if (!mask_input && fine3_supported(g)) return fine3_apply(g, mask, kap, u, y, st);
+  }
   if (!mask_input && fine2_supported(g)) return fine2_apply<S>(g, mask, kap, u, y, st);
   auto a = fargs<S, S>(g, mask, kap);
   a.v = u;
@@ -585,6 +588,9 @@ static cudaError_t fine2_smooth_dispatch(const Geom& g, const uint32_t* mask, co
   if constexpr (sizeof(S) == 8) {
     return cudaErrorInvalidValue;
   } else {
+    if constexpr (sizeof(S) == 4 && sizeof(To) == 4) {
+      if (fine3_supported(g)) return fine3_smooth<To>(g, mask, kap, r, e, w, out, cA, cB, st);
+    }
     return fine2_smooth<S, To>(g, mask, kap, r, e, w, out, cA, cB, st);
   }
 }
@@ -593,7 +599,7 @@ static cudaError_t fine2_smooth_dispatch(const Geom& g, const uint32_t* mask, co
 template <class S, class To>
 cudaError_t fine_smooth(const Geom& g, const uint32_t* mask, const S* kap, const S* r, const S* e, const S* w,
                         To* out, typename Cv<S>::C cA, typename Cv<S>::C cB, cudaStream_t st) {
-  if (sizeof(S) < 8 && fine2_supported(g))
+  if (sizeof(S) < 8 && (fine2_supported(g) || (sizeof(S) == 4 && fine3_supported(g))))
     return fine2_smooth_dispatch(g, mask, kap, r, e, w, out, (float)cA, (float)cB, st);
   auto a = fargs<S, To>(g, mask, kap);
   a.r = r;

@@ -70,6 +70,16 @@ cudaError_t fine2_smooth(const Geom& g, const uint32_t* mask, const S* kap, cons
                          float cA, float cB, cudaStream_t st);
 template <class S>
 cudaError_t fine2_apply(const Geom& g, const uint32_t* mask, const S* kap, const S* u, S* y, cudaStream_t st);
+// separable FP32 fine sweeps / applies (fine3.cu): cubic elements, any grid
+bool fine3_supported(const Geom& g);
+int fine3_tiles_x(const Geom& g);
+int fine3_tiles_y(const Geom& g);
+int fine3_ctas_per_sm();
+template <class To>
+cudaError_t fine3_smooth(const Geom& g, const uint32_t* mask, const float* kap, const float* r, const float* e,
+                         const float* w, To* out, float cA, float cB, cudaStream_t st);
+cudaError_t fine3_apply(const Geom& g, const uint32_t* mask, const float* kap, const float* u, float* y,
+                        cudaStream_t st);
 // float-float FP64-accurate fine apply (+ fused p.q when dot != NULL); see fine_ds.cu
 bool fine_ds_supported(const Geom& g);
 unsigned fine_ds_num_ctas(const Geom& g);

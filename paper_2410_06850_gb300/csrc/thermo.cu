@@ -237,6 +237,7 @@ extern "C" thermo_status thermo_create(const int grid[3], const double h[3], con
     return fail(ctx, THERMO_EINVAL, "Chebyshev needs 1 <= degree <= 64, ratio > 1, power_iters >= 1");
   if (opt.nvec[0] < 1 || opt.nvec[0] > 6) return fail(ctx, THERMO_EINVAL, "nvec[0] must be in 1..6");
   if (opt.density_fp32 != 0 && opt.density_fp32 != 1) return fail(ctx, THERMO_EINVAL, "density_fp32 must be 0 or 1");
+  if (opt.fine_engine != 0 && opt.fine_engine != 1) return fail(ctx, THERMO_EINVAL, "fine_engine must be 0 or 1");
   Geom& g = ctx->g;
   memset(&g, 0, sizeof(g));
   g.Nx = grid[0];
@@ -301,6 +302,12 @@ extern "C" thermo_status thermo_create(const int grid[3], const double h[3], con
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 0;
     if (sms > 0 && fine2_supported(g)) g.NZ2 = balanced_zchunks(fine2_tiles_xy(g), (long long)sms * fine2_ctas_per_sm(), g.Nz);
+    g.NZ3 = 0;
+    if (sms > 0 && g.cube && opt.fine_engine == 0) {
+      const int per = fine3_ctas_per_sm();
+      if (per > 0)
+        g.NZ3 = balanced_zchunks((long long)fine3_tiles_x(g) * fine3_tiles_y(g), (long long)sms * per, g.Nz);
+    }
     if (sms > 0 && fine_ds_supported(g))
       g.NZD = balanced_zchunks(fine_ds_tiles_xy(g), (long long)sms * fine_ds_ctas_per_sm(), g.Nz);
   }

@@ -39,17 +39,23 @@ def test_apply_fp64_matches_oracle(case):
     s.close()
 
 
-LP_CASES = [dict(N=32), dict(N=64), dict(N=0, grid=(128, 64, 40), h=(1 / 128,) * 3)]
+LP_CASES = [dict(N=32), dict(N=64), dict(N=0, grid=(128, 64, 40), h=(1 / 128,) * 3),
+            dict(N=0, grid=(40, 44, 36), h=(1 / 44,) * 3), dict(N=96),
+            dict(N=64, engine=1), dict(N=0, grid=(32, 16, 24), h=(1 / 32, 1 / 16, 1 / 24))]
 
 
-@pytest.mark.parametrize("case", LP_CASES, ids=["32", "64", "box128x64x40"])
+@pytest.mark.parametrize("case", LP_CASES, ids=["32", "64", "box128x64x40", "box40x44x36", "96",
+                                                 "64_two_per_lane", "box32x16x24_noncubic"])
 @pytest.mark.parametrize("prec,tol", [(1, 2e-6), (2, 3e-2)])
 def test_apply_low_precision_normwise(prec, tol, case):
-    """FP32 and BF16-storage applies (32^3: one node per lane; 64^3 and the box:
-    two nodes per lane with packed f32x2 plus the closing column/row kernel)."""
+    """FP32 and BF16-storage applies.  FP32 on cubic elements: the separable
+    engine (tiles of 30 x 32 nodes, so these grids end in partial tiles in x and
+    y, and 97 nodes leave a one-row last tile); engine 1 and BF16 storage: two
+    nodes per lane (Nx a multiple of 64) or one node per lane; non-cubic
+    elements: one node per lane."""
     pr = small_problem(case["N"], kind="rand", kmin=1e-3, grid=case.get("grid"), h=case.get("h"))
     P = oracle_problem(pr)
-    s = gpu_solver(pr, prec=prec)
+    s = gpu_solver(pr, prec=prec, fine_engine=case.get("engine", 0))
     n = P["A"].shape[0]
     u = W.uniform01(6, n) - 0.5
     y = s.apply(torch.as_tensor(u), prec).cpu().numpy()
