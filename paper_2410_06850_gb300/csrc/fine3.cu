@@ -72,12 +72,13 @@ struct Maps3 {
   CUtensorMap v, k, m, r, w;
 };
 
-// OP 0: out = A v; OP 1: sweep.  VAR bit 0: iterate present, bit 1: cA (e - w)
-// term, bit 2: w staged (else zero).
+// OP 0: out = A v; OP 1: sweep; OP 2: residual out = r - A v.  VAR bit 0:
+// iterate present, bit 1: cA (e - w) term, bit 2: w staged (else zero).
 template <class To, int OP, int VAR>
 __global__ void __launch_bounds__(NT3, 2) f3_tile(const __grid_constant__ Args3<To> a,
                                                   const __grid_constant__ Maps3 tm) {
   constexpr bool SM = OP == 1;
+  constexpr bool HRS = OP >= 1;  // r staged
   constexpr bool HV = !SM || (VAR & 1);
   constexpr bool HCA = SM && (VAR & 2);
   constexpr bool HW = SM && (VAR & 4);
@@ -109,7 +110,7 @@ __global__ void __launch_bounds__(NT3, 2) f3_tile(const __grid_constant__ Args3<
     const int qk = q - 1;
     const bool hk = qk >= zs - 1 && qk <= ze;
     const bool hc = qk >= zs && qk <= ze;
-    const unsigned bytes = (hv ? bytesV : 0u) + (hk ? bytesK : 0u) + (hc ? bytesM : 0u) + (hc && SM ? bytesR : 0u) +
+    const unsigned bytes = (hv ? bytesV : 0u) + (hk ? bytesK : 0u) + (hc ? bytesM : 0u) + (hc && HRS ? bytesR : 0u) +
                            (hc && HW ? bytesR : 0u);
     const int s = stage_of(q);
     uint64_t* bar = bars + s;
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(NT3, 2) f3_tile(const __grid_constant__ Args3<
     if (hk) tma_load3(b + LY::BV, &tm.k, xs, y0, qk + 1, bar);
     if (hc) {
       tma_load3(b + LY::BV + LY::BK, &tm.m, mx, y0 + 1, qk + 1, bar);
-      if (SM) tma_load3(b + LY::BV + LY::BK + LY::BM, &tm.r, xs, y0 + 1, qk + 1, bar);
+      if (HRS) tma_load3(b + LY::BV + LY::BK + LY::BM, &tm.r, xs, y0 + 1, qk + 1, bar);
       if (HW) tma_load3(b + LY::BV + LY::BK + LY::BM + LY::BR, &tm.w, xs, y0 + 1, qk + 1, bar);
     }
   };
@@ -254,8 +255,10 @@ __global__ void __launch_bounds__(NT3, 2) f3_tile(const __grid_constant__ Args3<
         nx.vm[i] = ctr;
       }
       float e;
-      if (!SM) {
+      if (OP == 0) {
         e = Av;
+      } else if (OP == 2) {
+        e = sr[i * WB3] - Av;
       } else {
         // D = (h/3) K8; every lane evaluates (its staged columns exist), only valid ones store
         e = __fdividef(cB * (sr[i * WB3] - Av), cc4 * K8);
@@ -283,6 +286,7 @@ __global__ void __launch_bounds__(NT3, 2) f3_tile(const __grid_constant__ Args3<
 template <class To, int OP, int VAR>
 cudaError_t f3_launch(const Args3<To>& a, cudaStream_t st) {
   constexpr bool SM = OP == 1;
+  constexpr bool HRS = OP >= 1;
   constexpr bool HW = SM && (VAR & 4);
   constexpr bool HV = !SM || (VAR & 1);
   const Geom& g = a.g;
@@ -294,7 +298,7 @@ cudaError_t f3_launch(const Args3<To>& a, cudaStream_t st) {
   if ((e = get_map(&tm.k, a.kap + g.base, F32, 4, g.P, g.RYe, g.Nz + 2, WB3, TY3 + 1)) != cudaSuccess) return e;
   if ((e = get_map(&tm.m, a.mask, CU_TENSOR_MAP_DATA_TYPE_UINT32, 4, g.mwr, g.RYn, g.nz + 2, MW3, TY3)) != cudaSuccess)
     return e;
-  if ((e = get_map(&tm.r, SM ? a.r + g.base : nullptr, F32, 4, g.P, g.RYn, g.nz + 2, WB3, TY3)) != cudaSuccess)
+  if ((e = get_map(&tm.r, HRS ? a.r + g.base : nullptr, F32, 4, g.P, g.RYn, g.nz + 2, WB3, TY3)) != cudaSuccess)
     return e;
   if ((e = get_map(&tm.w, HW ? a.w + g.base : nullptr, F32, 4, g.P, g.RYn, g.nz + 2, WB3, TY3)) != cudaSuccess)
     return e;
@@ -303,6 +307,57 @@ cudaError_t f3_launch(const Args3<To>& a, cudaStream_t st) {
   const dim3 grid(fine3_tiles_x(g), fine3_tiles_y(g), g.NZ3);
   note_launch(), k<<<grid, NT3, Lay3::SMEM, st>>>(a, tm);
   return cudaGetLastError();
+}
+
+// rc[B][j] = sum over the nodes i of level-1 block B of Phi[i][j] res[i] (Phi
+// node-major, L values per node).  One CTA per strip of blocks sharing (by, bz):
+// thread x walks the strip's node rows (4 per axis, 5 for the last block of an
+// axis, which also owns the closing node plane / row), each row read with
+// coalesced loads; the last thread of a row also takes the closing node x = Nx.
+// The four threads of a block then combine by a fixed shuffle tree.
+template <int L>
+__global__ void k_blk_restrict(Geom g, const float* __restrict__ res, const float* __restrict__ phi,
+                               float* __restrict__ rc) {
+  const int by = blockIdx.x, bz = blockIdx.y, x = threadIdx.x;
+  const int b = g.b;
+  const int ylo = by * b, yhi = (by == g.nby - 1) ? g.Ny : ylo + b - 1;
+  const int zlo = bz * b, zhi = (bz == g.nbz - 1) ? g.Nz : zlo + b - 1;
+  float acc[L];
+#pragma unroll
+  for (int j = 0; j < L; ++j) acc[j] = 0.f;
+  const bool closing = x == g.Nx - 1;  // also owns node x = Nx
+  for (int z = zlo; z <= zhi; ++z)
+    for (int y = ylo; y <= yhi; ++y) {
+      const long long n = nidx(g, x, y, z);
+      const float rv = res[n];
+      const float* ph = phi + n * L;
+      if constexpr (L == 4) {  // node-major Phi: 16-byte aligned rows of four
+        const float4 p4 = *reinterpret_cast<const float4*>(ph);
+        acc[0] = fmaf(p4.x, rv, acc[0]);
+        acc[1] = fmaf(p4.y, rv, acc[1]);
+        acc[2] = fmaf(p4.z, rv, acc[2]);
+        acc[3] = fmaf(p4.w, rv, acc[3]);
+      } else {
+#pragma unroll
+        for (int j = 0; j < L; ++j) acc[j] = fmaf(ph[j], rv, acc[j]);
+      }
+      if (closing) {
+        const float r2 = res[n + 1];
+#pragma unroll
+        for (int j = 0; j < L; ++j) acc[j] = fmaf(ph[L + j], r2, acc[j]);
+      }
+    }
+  // blocks of 4 threads along x (b = 4): fixed-order shuffle tree
+#pragma unroll
+  for (int j = 0; j < L; ++j) {
+    acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], 1);
+    acc[j] += __shfl_xor_sync(0xffffffffu, acc[j], 2);
+  }
+  if ((x & 3) == 0) {
+    const long long B = (x >> 2) + (long long)g.nbx * (by + (long long)g.nby * bz);
+#pragma unroll
+    for (int j = 0; j < L; ++j) rc[B * L + j] = acc[j];
+  }
 }
 
 template <class To>
@@ -352,6 +407,25 @@ cudaError_t fine3_apply(const Geom& g, const uint32_t* mask, const float* kap, c
   a.v = u;
   a.out = y;
   return f3_launch<float, 0, 1>(a, st);
+}
+
+bool fine3_restrict_supported(const Geom& g, int L1) {
+  return fine3_supported(g) && g.b == 4 && g.Nx <= 1024 && g.Nx % 32 == 0 && L1 == 4;
+}
+
+// level-1 restriction of the cycle (Algorithm 1): res = r - A e (FP32, zero on
+// Gamma_D) by the separable engine into `res`, then rc = Phi^T res block by block
+cudaError_t fine3_restrict(const Geom& g, const uint32_t* mask, const float* kap, const float* r, const float* e,
+                           const float* phi, float* res, float* rc, int L1, cudaStream_t st) {
+  if (!fine3_restrict_supported(g, L1)) return cudaErrorInvalidValue;
+  auto a = args3<float>(g, mask, kap);
+  a.r = r;
+  a.v = e;
+  a.out = res;
+  cudaError_t err = f3_launch<float, 2, 1>(a, st);
+  if (err != cudaSuccess) return err;
+  note_launch(), k_blk_restrict<4><<<dim3(g.nby, g.nbz), g.Nx, 0, st>>>(g, res, phi, rc);
+  return cudaGetLastError();
 }
 
 template cudaError_t fine3_smooth<float>(const Geom&, const uint32_t*, const float*, const float*, const float*,

@@ -80,6 +80,9 @@ cudaError_t fine3_smooth(const Geom& g, const uint32_t* mask, const float* kap, 
                          const float* w, To* out, float cA, float cB, cudaStream_t st);
 cudaError_t fine3_apply(const Geom& g, const uint32_t* mask, const float* kap, const float* u, float* y,
                         cudaStream_t st);
+bool fine3_restrict_supported(const Geom& g, int L1);
+cudaError_t fine3_restrict(const Geom& g, const uint32_t* mask, const float* kap, const float* r, const float* e,
+                           const float* phi, float* res, float* rc, int L1, cudaStream_t st);
 // float-float FP64-accurate fine apply (+ fused p.q when dot != NULL); see fine_ds.cu
 bool fine_ds_supported(const Geom& g);
 unsigned fine_ds_num_ctas(const Geom& g);

@@ -770,7 +770,17 @@ static cudaError_t vcycle_fine(thermo_ctx* ctx, const S* kap, const S* r, S* b0,
     cur = nxt;
   }
   kt_begin(ctx, THERMO_KT_RESTRICT);
-  if ((e = fine_restrict<S>(g, ctx->bits, kap, r, buf[cur], phi, rc, L1, st)) != cudaSuccess) return e;
+  if constexpr (sizeof(S) == 4 && sizeof(C) == 4) {
+    // residual by the separable engine, then the block-strip restriction
+    if (fine3_restrict_supported(g, L1))
+      e = fine3_restrict(g, ctx->bits, (const float*)kap, (const float*)r, (const float*)buf[cur], (const float*)phi,
+                         ctx->tmp32, (float*)rc, L1, st);
+    else
+      e = fine_restrict<S>(g, ctx->bits, kap, r, buf[cur], phi, rc, L1, st);
+  } else {
+    e = fine_restrict<S>(g, ctx->bits, kap, r, buf[cur], phi, rc, L1, st);
+  }
+  if (e != cudaSuccess) return e;
   kt_end(ctx, THERMO_KT_RESTRICT, ctx->kt_on ? fine_bytes(g, 2 * s + L1 * c, s) + (double)l1.cl.ncell * L1 * c : 0.0);
   kt_begin(ctx, THERMO_KT_COARSE);
   ctx->coarse_bytes = 0.0;
@@ -1309,6 +1319,9 @@ extern "C" thermo_status thermo_bench_kernel(thermo_ctx* ctx, int which, int rep
                                          0.6f, st);
       case 4:
         bytes = n * (8 + 4 * L1) + M * 4;
+        if (fine3_restrict_supported(g, ctx->L1))
+          return fine3_restrict(g, ctx->bits, ctx->k32, ctx->r32, ctx->ea32, ctx->phi32, ctx->tmp32, l1.r32, ctx->L1,
+                                st);
         return fine_restrict<float>(g, ctx->bits, ctx->k32, ctx->r32, ctx->ea32, ctx->phi32, l1.r32, ctx->L1, st);
       case 5:
         bytes = n * (8 + 4 * L1);
