@@ -37,9 +37,9 @@ WORKLOAD = "chan256_1e6"
 FP64_NOMINAL_GFLOPS = 1250.0
 # ncu dram__bytes_read.sum + dram__bytes_write.sum per launch of the current kernels at this
 # workload (profiles/ summaries); None where no capture of the current kernel exists.
-# smooth: the three-term sweep with a staged previous iterate (7 of the 10 sweeps of a cycle);
-# apply_fp64: the float-float outer operator + p.Ap
-TRAFFIC = {"smooth": 315.739648e6 + 55.940096e6, "apply_fp64": None}
+# smooth: the separable three-term sweep, captured on a 192^3 context and scaled by the node count
+# (153.45 MB for 7,189,057 nodes); classes made of many kernels (coarse levels) have none
+TRAFFIC = {"smooth": 153.45e6 * 16974593 / 7189057, "apply_fp64": None, "coarse_levels": None}
 
 
 def _peaks():
