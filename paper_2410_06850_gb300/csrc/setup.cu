@@ -254,7 +254,7 @@ constexpr int EIG_EXTRA = 8;  // Ritz vectors beyond L carried into the FP64 ref
 
 struct L1Smem {
   // offsets in bytes
-  size_t C, Y, X, W, m, H, Yr, cs64, sn64, pp, qq, sel, list, lmap, lam, lam32, scr, sh, total;
+  size_t C, Y, X, W, m, rs, A26, J26, H, Yr, cs64, sn64, pp, qq, sel, list, lmap, lam, lam32, scr, sh, total;
 };
 __host__ __device__ inline L1Smem l1_smem(int n2, int K, int nmap) {
   L1Smem s;
@@ -271,6 +271,9 @@ __host__ __device__ inline L1Smem l1_smem(int n2, int K, int nmap) {
   s.X = al((size_t)n2 * K * 8);
   s.W = al((size_t)n2 * K * 8 + 8 * 64);
   s.m = al((size_t)n2 * 8);
+  s.rs = al((size_t)n2 * 8);
+  s.A26 = al((size_t)n2 * 26 * 8);
+  s.J26 = al((size_t)n2 * 26);
   s.H = al((size_t)k2 * k2 * 8);
   s.Yr = al((size_t)k2 * k2 * 8);
   s.cs64 = al((size_t)k2 * 8);
@@ -315,6 +318,9 @@ __global__ void __launch_bounds__(EIG_NT) k_level1_eigen(Geom g, const uint32_t*
   double* X = (double*)(sm + S.X);
   double* W = (double*)(sm + S.W);
   double* m = (double*)(sm + S.m);
+  double* rs = (double*)(sm + S.rs);       // m^-1/2
+  double* A26 = (double*)(sm + S.A26);     // couplings A_ij to the 26 neighbours (FP64), once per block
+  signed char* J26 = (signed char*)(sm + S.J26);  // their compact indices (-1: outside / Dirichlet)
   double* H = (double*)(sm + S.H);
   double* Yr = (double*)(sm + S.Yr);
   double* cs64 = (double*)(sm + S.cs64);
@@ -349,58 +355,59 @@ __global__ void __launch_bounds__(EIG_NT) k_level1_eigen(Geom g, const uint32_t*
   const int n = (int)sh[34];
   const int kk = n < L ? n : L;
   const int K = n < Kmax ? n : Kmax;
-  // mass and the Neumann matrix scaled by M^-1/2
+  // mass, its inverse square root, and the couplings to the 26 neighbours (FP64, once)
   for (int i = tid; i < n; i += nt) {
     const int k = list[i];
     const int x = X0 + k % wx, y = Y0 + (k / wx) % wy, z = Z0 + k / (wx * wy);
     m[i] = kappa_sum8(g, k64, x, y, z) * g.vol * 0.125;
-  }
-  for (int i = tid; i < n * lda; i += nt) C[i] = 0.f;
-  __syncthreads();
-  for (int i = tid; i < n; i += nt) {
-    const int k = list[i];
-    const int x = X0 + k % wx, y = Y0 + (k / wx) % wy, z = Z0 + k / (wx * wy);
-    double diag = 0.0;
+    rs[i] = 1.0 / sqrt(m[i]);
+    int o = 0;
     for (int oz = -1; oz <= 1; ++oz)
       for (int oy = -1; oy <= 1; ++oy)
         for (int ox = -1; ox <= 1; ++ox) {
           if (!ox && !oy && !oz) continue;
           const int xx = x + ox - X0, yy = y + oy - Y0, zz = z + oz - Z0;
-          if (xx < 0 || yy < 0 || zz < 0 || xx >= wx || yy >= wy || zz >= wz) continue;
-          const int j = lmap[xx + wx * (yy + wy * zz)];
-          if (j < 0) continue;
-          const double a = coupling(g, k64, x, y, z, ox, oy, oz);
-          diag -= a;
-          C[i * lda + j] = (float)(a / sqrt(m[i] * m[j]));
+          int j = -1;
+          if (xx >= 0 && yy >= 0 && zz >= 0 && xx < wx && yy < wy && zz < wz) j = lmap[xx + wx * (yy + wy * zz)];
+          J26[i * 26 + o] = (signed char)j;
+          A26[i * 26 + o] = j >= 0 ? coupling(g, k64, x, y, z, ox, oy, oz) : 0.0;
+          ++o;
         }
-    C[i * lda + i] = (float)(diag / m[i]);
+  }
+  for (int i = tid; i < n * lda; i += nt) C[i] = 0.f;
+  __syncthreads();
+  // the Neumann matrix scaled by M^-1/2 (FP32 entries from FP64 couplings and scales)
+  for (int i = tid; i < n; i += nt) {
+    double diag = 0.0;
+    const float ri = (float)rs[i];
+    for (int o = 0; o < 26; ++o) {
+      const int j = J26[i * 26 + o];
+      if (j < 0) continue;
+      const double a = A26[i * 26 + o];
+      diag -= a;
+      C[i * lda + j] = (float)a * ri * (float)rs[j];
+    }
+    C[i * lda + i] = (float)(diag * rs[i] * rs[i]);
   }
   __syncthreads();
   if (n > 0) eig_lowest(C, lda, n, K, lam32, Yf, n2, scr, (float*)X, sh);
   // FP64 basis phi = M^-1/2 v over the K vectors, M-orthonormalised
   for (int w = tid; w < n * K; w += nt) {
     const int i = w / K, a = w % K;
-    X[w] = (double)Yf[a * n2 + i] / sqrt(m[i]);
+    X[w] = (double)Yf[a * n2 + i] * rs[i];
   }
   __syncthreads();
   mgs(X, m, n, K, K, sh);
   // W = Ã X (difference form: (Ã x)_i = sum_{j in B} A_ij (x_j - x_i))
   for (int i = tid; i < n; i += nt) {
-    const int k = list[i];
-    const int x = X0 + k % wx, y = Y0 + (k / wx) % wy, z = Z0 + k / (wx * wy);
     double acc[16];
     for (int a = 0; a < K; ++a) acc[a] = 0.0;
-    for (int oz = -1; oz <= 1; ++oz)
-      for (int oy = -1; oy <= 1; ++oy)
-        for (int ox = -1; ox <= 1; ++ox) {
-          if (!ox && !oy && !oz) continue;
-          const int xx = x + ox - X0, yy = y + oy - Y0, zz = z + oz - Z0;
-          if (xx < 0 || yy < 0 || zz < 0 || xx >= wx || yy >= wy || zz >= wz) continue;
-          const int j = lmap[xx + wx * (yy + wy * zz)];
-          if (j < 0) continue;
-          const double aij = coupling(g, k64, x, y, z, ox, oy, oz);
-          for (int a = 0; a < K; ++a) acc[a] += aij * (X[j * K + a] - X[i * K + a]);
-        }
+    for (int o = 0; o < 26; ++o) {
+      const int j = J26[i * 26 + o];
+      if (j < 0) continue;
+      const double aij = A26[i * 26 + o];
+      for (int a = 0; a < K; ++a) acc[a] += aij * (X[j * K + a] - X[i * K + a]);
+    }
     for (int a = 0; a < K; ++a) W[i * K + a] = acc[a];
   }
   __syncthreads();
@@ -574,7 +581,7 @@ cudaError_t level1_rap(const Geom& g, const uint32_t* bits, const double* k64, i
 // ---------------------------------------------------------------------------
 // Eq. (9): one CTA per group G of g^3 cells of the previous level.
 struct GSmem {
-  size_t C, Y, X, W, H, Yr, cs64, sn64, pp, qq, sel, alist, lam, lam32, scr, sh, total;
+  size_t C, Y, X, W, H, Yr, cs64, sn64, pp, qq, sel, alist, amap, lam, lam32, scr, sh, total;
 };
 __host__ __device__ inline GSmem g_smem(int n2, int K) {
   GSmem s;
@@ -597,6 +604,7 @@ __host__ __device__ inline GSmem g_smem(int n2, int K) {
   s.qq = al((size_t)k2 * 4);
   s.sel = al((size_t)k2 * 4);
   s.alist = al((size_t)n2 * 4);
+  s.amap = al((size_t)n2 * 4);
   s.lam = al((size_t)k2 * 8);
   s.lam32 = al((size_t)k2 * 4);
   s.scr = al(eig_scratch_floats(n2) * 4);
@@ -612,20 +620,6 @@ __device__ __forceinline__ long long cell_of_local(const CLevel& prev, const CLe
   return (gx * g + lx) + (long long)prev.mx * ((gy * g + ly) + (long long)prev.my * (gz * g + lz));
 }
 __device__ __forceinline__ int nbr_index(int dx, int dy, int dz) { return (dx + 1) + 3 * (dy + 1) + 9 * (dz + 1); }
-
-// entry (di, dj) of Ã_G = (A_prev)_GG - blockdiag D_c over local dofs (cell lc * Lp + i)
-__device__ __forceinline__ double group_entry(const CLevel& prev, const CLevel& cur, long long G,
-                                              const double* __restrict__ Tp, const double* __restrict__ Dc, int di,
-                                              int dj) {
-  const int g = cur.g, Lp = prev.L;
-  const int lci = di / Lp, i = di % Lp, lcj = dj / Lp, j = dj % Lp;
-  const int dx = lcj % g - lci % g, dy = (lcj / g) % g - (lci / g) % g, dz = lcj / (g * g) - lci / (g * g);
-  if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1) return 0.0;
-  const long long c = cell_of_local(prev, cur, G, lci);
-  double v = Tp[((c * 27 + nbr_index(dx, dy, dz)) * Lp + i) * Lp + j];
-  if (lci == lcj) v -= Dc[(c * Lp + i) * Lp + j];
-  return v;
-}
 
 // One CTA per group: Ã_G over the group's active dofs (FP32, symmetrised), its
 // K = L + 8 smallest eigenvectors with the FP32 solver of eigen.cuh, FP64
@@ -652,6 +646,7 @@ __global__ void __launch_bounds__(EIG_NT) k_group_eigen(CLevel prev, CLevel cur,
   int* qq = (int*)(sm + S.qq);
   int* sel = (int*)(sm + S.sel);
   int* alist = (int*)(sm + S.alist);
+  int* amap = (int*)(sm + S.amap);  // local dof -> compact active index (-1: inactive)
   double* lam = (double*)(sm + S.lam);
   float* lam32 = (float*)(sm + S.lam32);
   float* scr = (float*)(sm + S.scr);
@@ -663,7 +658,8 @@ __global__ void __launch_bounds__(EIG_NT) k_group_eigen(CLevel prev, CLevel cur,
     int na = 0;
     for (int d = 0; d < n; ++d) {
       const long long c = cell_of_local(prev, cur, G, d / Lp);
-      if (actp[c * Lp + d % Lp]) alist[na++] = d;
+      amap[d] = -1;
+      if (actp[c * Lp + d % Lp]) amap[d] = na, alist[na++] = d;
     }
     sh[34] = na;
   }
@@ -671,9 +667,27 @@ __global__ void __launch_bounds__(EIG_NT) k_group_eigen(CLevel prev, CLevel cur,
   const int na = (int)sh[34];
   const int kk = na < L ? na : L;
   const int K = na < Kmax ? na : Kmax;
-  for (int w = tid; w < na * na; w += nt) {
-    const int a = w / na, bcol = w % na;
-    C[a * lda + bcol] = (float)group_entry(prev, cur, G, Tp, Dc, alist[a], alist[bcol]);
+  // row ia of Ã_G, one neighbouring cell lcj per thread item: the tile row and the
+  // correction row are located once, then the Lp entries are read in order
+  auto tile_row = [&](int di, int lcj, const double*& T, const double*& D) {
+    const int lci = di / Lp, i = di % Lp;
+    const int dx = lcj % g - lci % g, dy = (lcj / g) % g - (lci / g) % g, dz = lcj / (g * g) - lci / (g * g);
+    T = nullptr;
+    D = nullptr;
+    if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1) return;
+    const long long c = cell_of_local(prev, cur, G, lci);
+    T = Tp + ((c * 27 + nbr_index(dx, dy, dz)) * Lp + i) * Lp;
+    if (lci == lcj) D = Dc + (c * Lp + i) * Lp;
+  };
+  for (int w = tid; w < na * ng; w += nt) {
+    const int ia = w / ng, lcj = w % ng;
+    const double *T, *D;
+    tile_row(alist[ia], lcj, T, D);
+    for (int j = 0; j < Lp; ++j) {
+      const int ja = amap[lcj * Lp + j];
+      if (ja < 0) continue;
+      C[ia * lda + ja] = T ? (float)(T[j] - (D ? D[j] : 0.0)) : 0.f;
+    }
   }
   __syncthreads();
   // symmetrise (the FP64 tiles are symmetric up to rounding)
@@ -698,12 +712,15 @@ __global__ void __launch_bounds__(EIG_NT) k_group_eigen(CLevel prev, CLevel cur,
     const int ia = w / K, a = w % K;
     const int di = alist[ia];
     double sacc = 0.0;
-    for (int ja = 0; ja < na; ++ja) {
-      const int dj = alist[ja];
-      const int lci = di / Lp, lcj = dj / Lp;
-      const int dx = lcj % g - lci % g, dy = (lcj / g) % g - (lci / g) % g, dz = lcj / (g * g) - lci / (g * g);
-      if (dx < -1 || dx > 1 || dy < -1 || dy > 1 || dz < -1 || dz > 1) continue;
-      sacc += group_entry(prev, cur, G, Tp, Dc, di, dj) * X[ja * K + a];
+    for (int lcj = 0; lcj < ng; ++lcj) {
+      const double *T, *D;
+      tile_row(di, lcj, T, D);
+      if (!T) continue;
+      for (int j = 0; j < Lp; ++j) {
+        const int ja = amap[lcj * Lp + j];
+        if (ja < 0) continue;
+        sacc += (T[j] - (D ? D[j] : 0.0)) * X[ja * K + a];
+      }
     }
     W[w] = sacc;
   }
