@@ -25,7 +25,7 @@ __device__ double cta_sum(double v, double* sh);  // setup.cu
 
 // 1. in place: A (n x n, leading dimension lda, full symmetric storage) ->
 // d[0..n-1], e[0..n-2]; reflector k in A[k+1..n-1][k] (v[k+1] = x0 - alpha), tau[k].
-// p: n floats of scratch.
+// p: n floats of scratch.  blockDim.x must be 256 (the update's 16 x 16 grid).
 __device__ void eig_tridiag(float* A, int lda, int n, float* d, float* e, float* tau, float* p, double* sh) {
   const int tid = threadIdx.x, nt = blockDim.x;
   for (int k = 0; k + 2 < n; ++k) {
@@ -53,11 +53,17 @@ __device__ void eig_tridiag(float* A, int lda, int n, float* d, float* e, float*
     __syncthreads();
     const float t = tau[k];
     if (t == 0.f) continue;  // uniform: every thread reads the same shared value
-    for (int i = k + 1 + tid; i < n; i += nt) {
-      const float* row = A + i * lda;
+    // p = t A22 v: four threads per row (a fixed shuffle tree combines them)
+    for (int i0 = k + 1; i0 < n; i0 += nt / 4) {
+      const int i = i0 + (tid >> 2);
       float acc = 0.f;
-      for (int j = k + 1; j < n; ++j) acc = fmaf(row[j], A[j * lda + k], acc);
-      p[i] = t * acc;
+      if (i < n) {
+        const float* row = A + i * lda;
+        for (int j = k + 1 + (tid & 3); j < n; j += 4) acc = fmaf(row[j], A[j * lda + k], acc);
+      }
+      acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+      acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+      if (i < n && (tid & 3) == 0) p[i] = t * acc;
     }
     __syncthreads();
     double pv = 0.0;
@@ -66,10 +72,11 @@ __device__ void eig_tridiag(float* A, int lda, int n, float* d, float* e, float*
     const float kc = (float)(0.5 * t * pv);
     for (int i = k + 1 + tid; i < n; i += nt) p[i] -= kc * A[i * lda + k];  // w = p - K v
     __syncthreads();
-    const int m = n - k - 1;
-    for (int w = tid; w < m * m; w += nt) {
-      const int i = k + 1 + w / m, j = k + 1 + w % m;
-      A[i * lda + j] -= A[i * lda + k] * p[j] + p[i] * A[j * lda + k];
+    // rank-2 update on a 16 x 16 thread grid (no index division)
+    for (int i = k + 1 + (tid >> 4); i < n; i += nt / 16) {
+      const float vi = A[i * lda + k], wi = p[i];
+      float* row = A + i * lda;
+      for (int j = k + 1 + (tid & 15); j < n; j += 16) row[j] -= vi * p[j] + wi * A[j * lda + k];
     }
     __syncthreads();
   }
@@ -83,20 +90,24 @@ __device__ void eig_tridiag(float* A, int lda, int n, float* d, float* e, float*
   __syncthreads();
 }
 
-// number of eigenvalues of T below x (Sturm sequence of the LDL^T pivots)
-__device__ __forceinline__ int eig_sturm(const float* d, const float* e, int n, float x, float pivmin) {
+// number of eigenvalues of T below x (Sturm sequence of the LDL^T pivots; e2 =
+// the squared off-diagonal; a fast division: only the signs of the pivots count)
+__device__ __forceinline__ int eig_sturm(const float* d, const float* e2, int n, float x, float pivmin) {
   float q = d[0] - x;
   int c = q < 0.f ? 1 : 0;
   for (int i = 1; i < n; ++i) {
     if (fabsf(q) < pivmin) q = -pivmin;
-    q = d[i] - x - e[i - 1] * e[i - 1] / q;
+    q = d[i] - x - __fdividef(e2[i - 1], q);
     c += q < 0.f ? 1 : 0;
   }
   return c;
 }
 
-// 2. (threads j < K) lam[j] = the j-th smallest eigenvalue; tn[0] = Gershgorin bound of ||T||
-__device__ void eig_bisect(const float* d, const float* e, int n, int K, float* lam, float* tn) {
+// 2. (threads j < K) lam[j] = the j-th smallest eigenvalue; tn[0] = Gershgorin bound of ||T||;
+// e2: n floats of scratch (the squared off-diagonal)
+__device__ void eig_bisect(const float* d, const float* e, int n, int K, float* lam, float* tn, float* e2) {
+  for (int i = threadIdx.x; i + 1 < n; i += blockDim.x) e2[i] = e[i] * e[i];
+  __syncthreads();
   const int j = threadIdx.x;
   if (j < K) {
     float lo = 3.0e38f, hi = -3.0e38f;
@@ -111,7 +122,7 @@ __device__ void eig_bisect(const float* d, const float* e, int n, int K, float* 
     for (int it = 0; it < 80 && b - a > tol; ++it) {
       const float mid = 0.5f * (a + b);
       if (mid <= a || mid >= b) break;
-      if (eig_sturm(d, e, n, mid, pivmin) > j)
+      if (eig_sturm(d, e2, n, mid, pivmin) > j)
         b = mid;
       else
         a = mid;
@@ -145,13 +156,13 @@ __device__ void eig_tri_vectors(const float* d, const float* e, int n, int K, co
           const float sub = e[i], nd = d[i + 1] - l, ns = (i + 1 < n - 1) ? e[i + 1] : 0.f, yn = y[i + 1];
           if (fabsf(cd) >= fabsf(sub)) {  // row i pivots
             if (cd == 0.f) cd = eps;
-            const float m = sub / cd;
+            const float m = __fdividef(sub, cd);
             ud[i] = cd, us[i] = cs, us2[i] = 0.f, y[i] = yc;
             cd = nd - m * cs;
             cs = ns;
             yc = yn - m * yc;
           } else {  // rows i and i+1 exchanged
-            const float m = cd / sub;
+            const float m = __fdividef(cd, sub);
             ud[i] = sub, us[i] = nd, us2[i] = ns, y[i] = yn;
             cd = cs - m * nd;
             cs = -m * ns;
@@ -164,7 +175,7 @@ __device__ void eig_tri_vectors(const float* d, const float* e, int n, int K, co
           float s = y[i];
           if (i + 1 < n) s -= us[i] * y[i + 1];
           if (i + 2 < n) s -= us2[i] * y[i + 2];
-          y[i] = s / ud[i];
+          y[i] = __fdividef(s, ud[i]);
         }
         for (int q = jh; q < j; ++q) {  // orthogonalise against the cluster's earlier vectors
           const float* yq = Y + (size_t)q * ldy;
@@ -222,7 +233,7 @@ __device__ void eig_lowest(float* A, int lda, int n, int K, float* lam, float* Y
   float* p = tau + n;
   float* tn = p + n;
   eig_tridiag(A, lda, n, d, e, tau, p, sh);
-  eig_bisect(d, e, n, K, lam, tn);
+  eig_bisect(d, e, n, K, lam, tn, p);
   eig_tri_vectors(d, e, n, K, lam, tn[0], Y, ldy, lu);
   eig_back(A, lda, n, tau, Y, ldy, K);
 }

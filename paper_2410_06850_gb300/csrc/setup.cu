@@ -4,16 +4,17 @@
 // * Eq. (8) on every level-1 block B (one CTA per block): the Neumann form of
 //   the couplings internal to B, Ã_ij = A_ij (i != j in B),
 //   Ã_ii = -sum_{j in B} A_ij, against the kappa-weighted lumped mass
-//   m_i = sum_{e ∋ i} kappa_e |e|/8.  C = M^-1/2 Ã M^-1/2 is diagonalised by a
-//   parallel cyclic Jacobi method in FP32 in shared memory; the L smallest
-//   eigenvectors are refined by an FP64 Rayleigh-Ritz step on the sparse Ã
-//   and M-orthonormalised by FP64 modified Gram-Schmidt.
+//   m_i = sum_{e ∋ i} kappa_e |e|/8.  The L + 8 smallest eigenvectors of
+//   C = M^-1/2 Ã M^-1/2 come from the FP32 solver of eigen.cuh (Householder,
+//   bisection, inverse iteration); mapped to M^-1/2 v in FP64, M-orthonormalised
+//   by Cholesky-QR (twice) and refined by an FP64 Rayleigh-Ritz step on the
+//   sparse Ã, of which the L lowest Ritz vectors are kept.
 // * Eq. (9) on every group G of g^3 cells of the previous level (one CTA per
 //   group): Ã_G = (A_prev)_GG - blockdiag_c P_c^T diag(rho_G) P_c, i.e. the
 //   Galerkin block of G minus the projected couplings that leave G (rho_G is
 //   the fine row sum restricted to G); with M-orthonormal bases the mass is
-//   the identity, so this is a standard eigenproblem (same Jacobi + FP64
-//   Rayleigh-Ritz + Gram-Schmidt).
+//   the identity, so this is a standard eigenproblem over the group's active
+//   dofs (same FP32 solver, FP64 Cholesky-QR and Rayleigh-Ritz on the tiles).
 // * Galerkin operators A_l = R A_{l-1} R^T as 27-neighbour tiles (FP64).
 // * l1-block-Jacobi inverses, dense FP64 Cholesky and explicit inverse of the
 //   coarsest operator.
@@ -205,22 +206,51 @@ __device__ void rr_finish(double* X, const double* W, int n, int ld, int k, doub
   __syncthreads();
 }
 
-// Modified Gram-Schmidt of the k columns of X[n][ld] in <a,b> = sum m_i a_i b_i
-// (m == nullptr: Euclidean).  Columns of zero norm are left zero.
-__device__ void mgs(double* X, const double* m, int n, int ld, int k, double* sh) {
-  for (int j = 0; j < k; ++j) {
-    for (int i = 0; i < j; ++i) {
-      double d = 0.0;
-      for (int r = threadIdx.x; r < n; r += blockDim.x) d += (m ? m[r] : 1.0) * X[r * ld + i] * X[r * ld + j];
-      d = cta_sum(d, sh);
-      for (int r = threadIdx.x; r < n; r += blockDim.x) X[r * ld + j] -= d * X[r * ld + i];
-      __syncthreads();
+// Cholesky-QR, twice, of the k columns of X[n][ld] in <a,b> = sum m_i a_i b_i
+// (m == nullptr: Euclidean): G = X^T M X, G = R^T R (one thread, FP64),
+// X <- X R^-1 (a thread per row).  Three barriers per pass instead of two per
+// pair of columns; the columns come from an eigensolver and are nearly
+// orthonormal, for which Cholesky-QR is stable.  A column whose pivot vanishes
+// (numerically dependent) is set to zero.  G: k x k doubles of scratch.
+__device__ void cholqr(double* X, const double* m, int n, int ld, int k, double* G) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  for (int pass = 0; pass < 2; ++pass) {
+    for (int w = tid; w < k * k; w += nt) {
+      const int a = w / k, b = w % k;
+      if (b < a) continue;
+      double s = 0.0;
+      for (int r = 0; r < n; ++r) s += (m ? m[r] : 1.0) * X[r * ld + a] * X[r * ld + b];
+      G[a * k + b] = s;
     }
-    double nn = 0.0;
-    for (int r = threadIdx.x; r < n; r += blockDim.x) nn += (m ? m[r] : 1.0) * X[r * ld + j] * X[r * ld + j];
-    nn = cta_sum(nn, sh);
-    const double inv = nn > 0.0 ? 1.0 / sqrt(nn) : 0.0;
-    for (int r = threadIdx.x; r < n; r += blockDim.x) X[r * ld + j] *= inv;
+    __syncthreads();
+    if (tid == 0) {
+      for (int a = 0; a < k; ++a) {
+        double dgn = G[a * k + a];
+        for (int c = 0; c < a; ++c) dgn -= G[c * k + a] * G[c * k + a];
+        const double ref = G[a * k + a];
+        if (!(dgn > 1e-24 * (ref > 0.0 ? ref : 1.0))) {  // dependent column: zero it
+          G[a * k + a] = 0.0;
+          for (int b = a + 1; b < k; ++b) G[a * k + b] = 0.0;
+          continue;
+        }
+        const double rd = sqrt(dgn);
+        G[a * k + a] = rd;
+        for (int b = a + 1; b < k; ++b) {
+          double v = G[a * k + b];
+          for (int c = 0; c < a; ++c) v -= G[c * k + a] * G[c * k + b];
+          G[a * k + b] = v / rd;
+        }
+      }
+    }
+    __syncthreads();
+    for (int r = tid; r < n; r += nt) {
+      double* x = X + r * ld;
+      for (int a = 0; a < k; ++a) {
+        double v = x[a];
+        for (int c = 0; c < a; ++c) v -= x[c] * G[c * k + a];
+        x[a] = G[a * k + a] > 0.0 ? v / G[a * k + a] : 0.0;
+      }
+    }
     __syncthreads();
   }
 }
@@ -397,18 +427,18 @@ __global__ void __launch_bounds__(EIG_NT) k_level1_eigen(Geom g, const uint32_t*
     X[w] = (double)Yf[a * n2 + i] * rs[i];
   }
   __syncthreads();
-  mgs(X, m, n, K, K, sh);
-  // W = Ã X (difference form: (Ã x)_i = sum_{j in B} A_ij (x_j - x_i))
-  for (int i = tid; i < n; i += nt) {
-    double acc[16];
-    for (int a = 0; a < K; ++a) acc[a] = 0.0;
+  cholqr(X, m, n, K, K, H);
+  // W = Ã X (difference form: (Ã x)_i = sum_{j in B} A_ij (x_j - x_i)), one (row, vector) item per thread
+  for (int w = tid; w < n * K; w += nt) {
+    const int i = w / K, a = w - (w / K) * K;
+    const double xi = X[i * K + a];
+    double acc = 0.0;
     for (int o = 0; o < 26; ++o) {
       const int j = J26[i * 26 + o];
       if (j < 0) continue;
-      const double aij = A26[i * 26 + o];
-      for (int a = 0; a < K; ++a) acc[a] += aij * (X[j * K + a] - X[i * K + a]);
+      acc += A26[i * 26 + o] * (X[j * K + a] - xi);
     }
-    for (int a = 0; a < K; ++a) W[i * K + a] = acc[a];
+    W[w] = acc;
   }
   __syncthreads();
   // Rayleigh-Ritz on span(X): sorted Ritz pairs in X, lam (W reused as scratch)
@@ -706,7 +736,7 @@ __global__ void __launch_bounds__(EIG_NT) k_group_eigen(CLevel prev, CLevel cur,
     X[w] = (double)Yf[a * n2 + i];
   }
   __syncthreads();
-  mgs(X, nullptr, na, K, K, sh);
+  cholqr(X, nullptr, na, K, K, H);
   // W = Ã_G X in FP64 from the tiles (active rows and columns)
   for (int w = tid; w < na * K; w += nt) {
     const int ia = w / K, a = w % K;
