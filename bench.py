@@ -384,6 +384,100 @@ def run_compare(args, mask_d, q_d):
     return 0
 
 
+def hierarchy_bytes(s, lean):
+    """Device bytes of the multilevel hierarchy of a set-up context: Phi, and per
+    level the Galerkin tiles, l1 inverses, bases Psi, flags and eigenvalues and
+    cycle vectors; the coarsest level's dense operator, inverse and scratch."""
+    h = s.hierarchy()
+    ts = 4 if lean else 12  # FP32 only, or FP64 + FP32 copies
+    nn = (s.grid[0] + 3) * (s.grid[1] + 3) * (((s.grid[0] + 3 + 31) // 32) * 32)
+    b = nn * h[0]["nvec"] * ts
+    for l, lv in enumerate(h):
+        nc = lv["cells"][0] * lv["cells"][1] * lv["cells"][2]
+        L = lv["nvec"]
+        top = l == len(h) - 1
+        b += nc * 27 * L * L * (8 if (top and lean) else (ts if not top else 8))
+        b += nc * L * L * ts + nc * L * 9 + nc * L * 4 * (4 if lean else 8)
+        if l > 0:
+            b += nc * 8 * h[l - 1]["nvec"] * L * ts
+    n = h[-1]["ndof"]
+    return b + 3 * n * n * 8
+
+
+def run_large(args):
+    """The large configuration: one context at N^3 (default 1024^3) in the lean
+    form (FP32 design and hierarchy, FP64 outer vectors), contrast 1e6, channel
+    tree at volume fraction 0.1; create, set_density, set-up, one solve to tol
+    from the coarse guess, one sensitivity.  Prints one JSON line with the
+    times, the iteration count, the true residual, the context's device memory
+    (measured and planned) and the hierarchy's share of it."""
+    import numpy as np
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    import workloads as W
+    from paper_2410_06850_gb300 import Solver, thermo
+
+    N = args.large
+    name = f"chan{N}v10"
+    t0 = time.perf_counter()
+    pr = W.problem(name)
+    grid = pr["grid"]
+    t_gen = time.perf_counter() - t0
+    opts = dict(lean=1, density_fp32=1)
+    plan = thermo.plan_bytes(grid, **opts)
+    M = grid[0] * grid[1] * grid[2]
+    mask_d = torch.as_tensor(pr["mask"]).cuda()
+    q_d = torch.ones(M, dtype=torch.float64, device="cuda")  # q = 1 (uniform source)
+    x_d = torch.as_tensor(pr["x"]).cuda()
+    del pr["x"], pr["mask"]
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    with ClockSampler() as clk:
+        t0 = time.perf_counter()
+        s = Solver(grid, pr["h"], mask_d, q_d, **opts)
+        torch.cuda.synchronize()
+        t_create = time.perf_counter() - t0
+        ctx_bytes = free0 - torch.cuda.mem_get_info()[0]
+        del mask_d, q_d
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s.set_density(x_d, pr["p"], pr["kmin"], pr["kmax"])
+        s.setup_precond()
+        torch.cuda.synchronize()
+        t_setup = time.perf_counter() - t0
+        u = torch.zeros(s.nnode, dtype=torch.float64, device="cuda")
+        t0 = time.perf_counter()
+        u, info = s.solve(u=u, tol=args.tol)
+        torch.cuda.synchronize()
+        t_solve = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        dc = s.sensitivity(u)
+        c = s.compliance(u)
+        torch.cuda.synchronize()
+        t_sens = time.perf_counter() - t0
+    peak = torch.cuda.mem_get_info()
+    hb = hierarchy_bytes(s, True)
+    line = {
+        "metric": f"{N}^3 lean-form solve to {args.tol:g} + sensitivity (s)", "value": round(t_solve, 4),
+        "unit": "s", "higher_is_better": False, "n_gpus": 1, "dtype": "f64 outer / f32 cycle",
+        "data": "synthetic", "config": {"workload": name, "grid": list(grid), "contrast": 1e6, "volfrac": 0.1,
+                                        "form": "mixed, lean (FP32 hierarchy), FP32 design"},
+        "iters": info["iters"], "rel_res_true": info["rel_res_true"], "status": info["status"],
+        "seconds": {"generate_inputs_host": round(t_gen, 2), "create": round(t_create, 3),
+                    "set_density_setup": round(t_setup, 3), "solve": round(t_solve, 3),
+                    "sensitivity_compliance": round(t_sens, 4)},
+        "dofs": s.nnode, "compliance": c, "dc_sum": float(dc.sum()),
+        "memory_gb": {"context_measured": round(ctx_bytes / 1e9, 2), "context_planned": round(plan / 1e9, 2),
+                      "hierarchy": round(hb / 1e9, 2), "hierarchy_budget": 180.0,
+                      "device_free_after": round(peak[0] / 1e9, 2), "device_total": round(peak[1] / 1e9, 2)},
+        "clocks": clk.summary(),
+    }
+    print(json.dumps(line), flush=True)
+    s.close()
+    return 0
+
+
 def golden(name):
     """The oracle's reference solution of a workload at seeded nodes, if written
     (tests/golden/make_oracle_solutions.py, which calls only the oracle)."""
@@ -428,6 +522,8 @@ def main():
     ap.add_argument("--kernels-only", action="store_true", help="only time the kernels and one solve per form")
     ap.add_argument("--fd-check", type=int, default=0,
                     help="with --topopt: central finite differences on N seeded elements of the final design")
+    ap.add_argument("--large", type=int, default=0,
+                    help="the large configuration at N^3 (1024: the full size) in the lean form; one JSON line")
     ap.add_argument("--compare", action="store_true",
                     help="FP64 MMG-PCG vs CG vs Jacobi-PCG on the workload (default chan128) and print one JSON line")
     args = ap.parse_args()
@@ -437,6 +533,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    if args.large:
+        return run_large(args)
 
     import torch
     import __graft_entry__ as ge

@@ -127,6 +127,17 @@ typedef struct {
                                        Q1 operator, one x column per warp, rows in
                                        registers); 1 the two-nodes-per-lane engine
                                        (grids with Nx a multiple of 64) */
+  int lean;                         /* 0 (default): FP64 and FP32 copies of the hierarchy.
+                                       1 (mixed forms only): the hierarchy is stored once,
+                                       in FP32 (Phi, Psi, the tiles of every level but the
+                                       coarsest, the l1 inverses); each level's tiles and
+                                       bases are computed in FP64 arithmetic from the
+                                       stored FP32 tiles of the level below and rounded
+                                       once; the FP64 set-up intermediates (Phi before
+                                       rounding, Psi, the row-sum corrections) live in the
+                                       memory of the CG and cycle vectors, which set-up
+                                       does not use; the coarse initial guess runs the FP32
+                                       chain.  Roughly halves the context's device memory. */
 } thermo_options;
 
 typedef struct {
@@ -169,6 +180,15 @@ thermo_status thermo_create(const int grid[3], const double h[3],
                             const double *dirichlet_value,
                             const double *source, void *cuda_stream,
                             const thermo_options *opt, thermo_ctx **out);
+
+/* Device bytes thermo_create would allocate for this grid and these options
+ * (opt NULL = defaults; has_dirichlet_value: whether a dirichlet_value array
+ * will be given), without touching a GPU: the same allocation plan run
+ * without allocating.  Counts the context's own buffers (each rounded up to
+ * 512 bytes), not the caller's inputs or the CUDA context.  Returns EINVAL
+ * for grids or options thermo_create rejects. */
+thermo_status thermo_plan_bytes(const int grid[3], const thermo_options *opt,
+                                int has_dirichlet_value, long long *bytes);
 
 /* Set the design (Sec. 2.1 Eq. (1)): x device double[M] (float[M] when
  * opt.density_fp32 = 1) in [0,1] (not checked), p >= 1, 0 < kmin <= kmax.

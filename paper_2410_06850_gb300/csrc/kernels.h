@@ -38,7 +38,8 @@ cudaError_t pack_nodes(const Geom& g, const double* nat, double* pad, cudaStream
 cudaError_t unpack_nodes(const Geom& g, const double* pad, double* nat, cudaStream_t st);
 cudaError_t mask_to_bits(const Geom& g, const uint8_t* nat, uint32_t* bits, cudaStream_t st);
 cudaError_t count_mask(const Geom& g, const uint8_t* nat, long long n, int* out, cudaStream_t st);
-cudaError_t simp_kappa(const Geom& g, const double* x, double p, double kmin, double kmax, double* k64,
+template <class X>  // X: stored design type (double or float)
+cudaError_t simp_kappa(const Geom& g, const X* x, double p, double kmin, double kmax, double* k64,
                        float* k32, bf16* k16, float* klo, cudaStream_t st);
 cudaError_t load_vector(const Geom& g, const double* q, double* f, cudaStream_t st);
 cudaError_t widen_f32(const float* a, double* b, long long n, cudaStream_t st);
@@ -59,7 +60,8 @@ cudaError_t cg_beta_dot(const Geom& g, const double* r, const void* z, int zk, c
 cudaError_t cg_pupdate(const Geom& g, const void* z, int z_kind, double* p, const CgScalars* sc, int first,
                        cudaStream_t st);
 cudaError_t vec_to_f64(const Geom& g, const void* src, int kind, double* dst, cudaStream_t st);
-cudaError_t fine_prolong_add(const Geom& g, const double* phi, int L1, const double* ec, double* u, cudaStream_t st);
+template <class C>  // u += Phi ec with Phi, ec stored as C (double or float), FP64 sums
+cudaError_t fine_prolong_add(const Geom& g, const C* phi, int L1, const C* ec, double* u, cudaStream_t st);
 // two-nodes-per-lane FP32-compute fine sweeps / applies (fine2.cu): cubic
 // elements, Nx a multiple of 64
 bool fine2_supported(const Geom& g);
@@ -96,7 +98,8 @@ cudaError_t power_start(const Geom& g, const uint32_t* bits, double* v, cudaStre
 cudaError_t vec_scale(const Geom& g, double a, double* v, cudaStream_t st);
 cudaError_t fill_const(double* a, long long n, double v, cudaStream_t st);
 cudaError_t vec_axpy_pad(const Geom& g, double a, const double* x, double* y, cudaStream_t st);
-cudaError_t sensitivity(const Geom& g, const double* upad, const double* x, double p, double kmin, double kmax,
+template <class X>
+cudaError_t sensitivity(const Geom& g, const double* upad, const X* x, double p, double kmin, double kmax,
                         double* dc, cudaStream_t st);
 cudaError_t density_filter(int Nx, int Ny, int Nz, const double* in, double* out, double rmin, int transpose,
                            cudaStream_t st);
@@ -135,22 +138,28 @@ cudaError_t level1_eigen(const Geom& g, const uint32_t* bits, const double* k64,
                          double* eig, uint8_t* active, int* status, cudaStream_t st);
 cudaError_t level1_rowsum_corr(const Geom& g, const uint32_t* bits, const double* k64, int L1,
                                const double* phi64, int nt, const int* gcum, double* D, cudaStream_t st);
+template <class TO>  // TO: stored tile type (double or float); sums in FP64
 cudaError_t level1_rap(const Geom& g, const uint32_t* bits, const double* k64, int L1, const double* phi64,
-                       double* tiles, cudaStream_t st);
-cudaError_t group_eigen(const CLevel& prev, const CLevel& cur, const double* tiles_prev, const double* Dcorr,
+                       TO* tiles, cudaStream_t st);
+template <class TI>  // TI: stored type of the previous level's tiles
+cudaError_t group_eigen(const CLevel& prev, const CLevel& cur, const TI* tiles_prev, const double* Dcorr,
                         const uint8_t* act_prev, double* Psi, double* eig, uint8_t* act_cur, int* status,
                         cudaStream_t st);
 cudaError_t group_project_corr(const CLevel& prev, const CLevel& cur, const double* Psi, const double* Dprev,
                                double* Dcur, int nt, cudaStream_t st);
-cudaError_t group_rap(const CLevel& prev, const CLevel& cur, const double* Psi, const double* tiles_prev,
-                      double* tiles, cudaStream_t st);
-cudaError_t fix_inactive(const CLevel& lv, const uint8_t* act, double* tiles, cudaStream_t st);
-cudaError_t l1_inverse(const CLevel& lv, const double* tiles, double* Dinv64, float* Dinv32, cudaStream_t st);
+template <class TI, class TO>  // (double, double), (float, float), (float, double)
+cudaError_t group_rap(const CLevel& prev, const CLevel& cur, const double* Psi, const TI* tiles_prev,
+                      TO* tiles, cudaStream_t st);
+template <class TT>
+cudaError_t fix_inactive(const CLevel& lv, const uint8_t* act, TT* tiles, cudaStream_t st);
+template <class TT>  // Dinv64 may be NULL
+cudaError_t l1_inverse(const CLevel& lv, const TT* tiles, double* Dinv64, float* Dinv32, cudaStream_t st);
 cudaError_t dense_assemble(const CLevel& lv, const double* tiles, double* A, cudaStream_t st);
 // ---- dense.cu : blocked FP64 Cholesky + explicit inverse of the coarsest operator
 long long cholesky_work_size(int n);  // doubles of scratch cholesky_inverse needs
 cudaError_t cholesky_inverse(int n, double* A, double* Ainv, double* work, int* status, cudaStream_t st);
 cudaError_t cvt_f64_f32(const double* a, float* b, long long n, cudaStream_t st);
-cudaError_t phi_natural(const Geom& g, const double* phi_pad, int L1, double* out, cudaStream_t st);
+template <class C>
+cudaError_t phi_natural(const Geom& g, const C* phi_pad, int L1, double* out, cudaStream_t st);
 
 }  // namespace thermo

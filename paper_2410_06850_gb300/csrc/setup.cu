@@ -540,9 +540,11 @@ cudaError_t level1_rowsum_corr(const Geom& g, const uint32_t* bits, const double
 // ---------------------------------------------------------------------------
 // Level-1 Galerkin tiles: for block B, Y = A Phi_B on the one-node ring
 // around B, then tile(B', B) = Phi_{B'}^T Y for the 27 neighbours B', stored
-// in B''s row (its neighbour index points back at B).
+// in B''s row (its neighbour index points back at B).  FP64 sums; TO is the
+// stored type (FP32 when the hierarchy is kept in FP32 only).
+template <class TO>
 __global__ void k_level1_rap(Geom g, const uint32_t* __restrict__ bits, const double* __restrict__ k64, int L,
-                             const double* __restrict__ phi, double* __restrict__ tiles) {
+                             const double* __restrict__ phi, TO* __restrict__ tiles) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int b = g.b;
   const long long cell = blockIdx.x;
@@ -595,18 +597,24 @@ __global__ void k_level1_rap(Geom g, const uint32_t* __restrict__ bits, const do
         }
     const long long nc = nbx + (long long)g.nbx * (nby + (long long)g.nby * nbz);
     const int back = (1 - dx) + 3 * (1 - dy) + 9 * (1 - dz);
-    tiles[((nc * 27 + back) * L + a) * L + kcol] = s;
+    tiles[((nc * 27 + back) * L + a) * L + kcol] = (TO)s;
   }
 }
+template <class TO>
 cudaError_t level1_rap(const Geom& g, const uint32_t* bits, const double* k64, int L1, const double* phi64,
-                       double* tiles, cudaStream_t st) {
+                       TO* tiles, cudaStream_t st) {
   const int r = g.b + 3;
   const size_t sm = (size_t)r * r * r * L1 * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(k_level1_rap, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = cudaFuncSetAttribute(k_level1_rap<TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  note_launch(), k_level1_rap<<<(unsigned)((long long)g.nbx * g.nby * g.nbz), 128, sm, st>>>(g, bits, k64, L1, phi64, tiles);
+  note_launch(),
+      k_level1_rap<TO><<<(unsigned)((long long)g.nbx * g.nby * g.nbz), 128, sm, st>>>(g, bits, k64, L1, phi64, tiles);
   return cudaGetLastError();
 }
+template cudaError_t level1_rap<double>(const Geom&, const uint32_t*, const double*, int, const double*, double*,
+                                        cudaStream_t);
+template cudaError_t level1_rap<float>(const Geom&, const uint32_t*, const double*, int, const double*, float*,
+                                       cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // Eq. (9): one CTA per group G of g^3 cells of the previous level.
@@ -655,7 +663,9 @@ __device__ __forceinline__ int nbr_index(int dx, int dy, int dz) { return (dx + 
 // K = L + 8 smallest eigenvectors with the FP32 solver of eigen.cuh, FP64
 // Gram-Schmidt and an FP64 Rayleigh-Ritz step on Ã_G from the FP64 tiles;
 // the L lowest form Psi (mass = identity: the "mass trick" after Eq. (9)).
-__global__ void __launch_bounds__(EIG_NT) k_group_eigen(CLevel prev, CLevel cur, const double* __restrict__ Tp,
+// TI: the stored type of the previous level's tiles (widened on load).
+template <class TI>
+__global__ void __launch_bounds__(EIG_NT) k_group_eigen(CLevel prev, CLevel cur, const TI* __restrict__ Tp,
                                                         const double* __restrict__ Dc, const uint8_t* __restrict__ actp,
                                                         int n2, double* __restrict__ Psi, double* __restrict__ eig,
                                                         uint8_t* __restrict__ actc) {
@@ -699,7 +709,7 @@ __global__ void __launch_bounds__(EIG_NT) k_group_eigen(CLevel prev, CLevel cur,
   const int K = na < Kmax ? na : Kmax;
   // row ia of Ã_G, one neighbouring cell lcj per thread item: the tile row and the
   // correction row are located once, then the Lp entries are read in order
-  auto tile_row = [&](int di, int lcj, const double*& T, const double*& D) {
+  auto tile_row = [&](int di, int lcj, const TI*& T, const double*& D) {
     const int lci = di / Lp, i = di % Lp;
     const int dx = lcj % g - lci % g, dy = (lcj / g) % g - (lci / g) % g, dz = lcj / (g * g) - lci / (g * g);
     T = nullptr;
@@ -711,12 +721,13 @@ __global__ void __launch_bounds__(EIG_NT) k_group_eigen(CLevel prev, CLevel cur,
   };
   for (int w = tid; w < na * ng; w += nt) {
     const int ia = w / ng, lcj = w % ng;
-    const double *T, *D;
+    const TI* T;
+    const double* D;
     tile_row(alist[ia], lcj, T, D);
     for (int j = 0; j < Lp; ++j) {
       const int ja = amap[lcj * Lp + j];
       if (ja < 0) continue;
-      C[ia * lda + ja] = T ? (float)(T[j] - (D ? D[j] : 0.0)) : 0.f;
+      C[ia * lda + ja] = T ? (float)((double)T[j] - (D ? D[j] : 0.0)) : 0.f;
     }
   }
   __syncthreads();
@@ -743,13 +754,14 @@ __global__ void __launch_bounds__(EIG_NT) k_group_eigen(CLevel prev, CLevel cur,
     const int di = alist[ia];
     double sacc = 0.0;
     for (int lcj = 0; lcj < ng; ++lcj) {
-      const double *T, *D;
+      const TI* T;
+      const double* D;
       tile_row(di, lcj, T, D);
       if (!T) continue;
       for (int j = 0; j < Lp; ++j) {
         const int ja = amap[lcj * Lp + j];
         if (ja < 0) continue;
-        sacc += (T[j] - (D ? D[j] : 0.0)) * X[ja * K + a];
+        sacc += ((double)T[j] - (D ? D[j] : 0.0)) * X[ja * K + a];
       }
     }
     W[w] = sacc;
@@ -769,7 +781,8 @@ __global__ void __launch_bounds__(EIG_NT) k_group_eigen(CLevel prev, CLevel cur,
     actc[G * L + tid] = tid < kk ? 1 : 0;
   }
 }
-cudaError_t group_eigen(const CLevel& prev, const CLevel& cur, const double* tiles_prev, const double* Dcorr,
+template <class TI>
+cudaError_t group_eigen(const CLevel& prev, const CLevel& cur, const TI* tiles_prev, const double* Dcorr,
                         const uint8_t* act_prev, double* Psi, double* eig, uint8_t* act_cur, int* status,
                         cudaStream_t st) {
   const int n = cur.g * cur.g * cur.g * prev.L;
@@ -777,12 +790,16 @@ cudaError_t group_eigen(const CLevel& prev, const CLevel& cur, const double* til
   const int Kmax = (cur.L + EIG_EXTRA) < n2 ? (cur.L + EIG_EXTRA) : n2;
   const GSmem S = g_smem(n2, Kmax);
   if (S.total > 227 * 1024) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_group_eigen, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.total);
+  cudaError_t e = cudaFuncSetAttribute(k_group_eigen<TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.total);
   if (e != cudaSuccess) return e;
-  note_launch(), k_group_eigen<<<(unsigned)cur.ncell, EIG_NT, S.total, st>>>(prev, cur, tiles_prev, Dcorr, act_prev, n2, Psi, eig,
-                                                               act_cur);
+  note_launch(), k_group_eigen<TI><<<(unsigned)cur.ncell, EIG_NT, S.total, st>>>(prev, cur, tiles_prev, Dcorr, act_prev,
+                                                                                 n2, Psi, eig, act_cur);
   return cudaGetLastError();
 }
+template cudaError_t group_eigen<double>(const CLevel&, const CLevel&, const double*, const double*, const uint8_t*,
+                                         double*, double*, uint8_t*, int*, cudaStream_t);
+template cudaError_t group_eigen<float>(const CLevel&, const CLevel&, const float*, const double*, const uint8_t*,
+                                        double*, double*, uint8_t*, int*, cudaStream_t);
 
 // D_G^(t) = Psi_G^T blockdiag_{c in G}(D_c^(t)) Psi_G for every later level t
 __global__ void k_group_corr(CLevel prev, CLevel cur, const double* __restrict__ Psi, const double* __restrict__ Dp,
@@ -813,8 +830,10 @@ cudaError_t group_project_corr(const CLevel& prev, const CLevel& cur, const doub
 }
 
 // A_l tiles: tile(G, G') = sum_{c in G, c' in G' adjacent} Psi_G[c]^T T(c,c') Psi_G'[c']
-__global__ void k_group_rap(CLevel prev, CLevel cur, const double* __restrict__ Psi, const double* __restrict__ Tp,
-                            double* __restrict__ T) {
+// (FP64 sums; TI / TO: stored types of the previous and the new tiles)
+template <class TI, class TO>
+__global__ void k_group_rap(CLevel prev, CLevel cur, const double* __restrict__ Psi, const TI* __restrict__ Tp,
+                            TO* __restrict__ T) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int g = cur.g, Lp = prev.L, L = cur.L, ng = g * g * g, n = ng * Lp;
   double* out = (double*)sm;       // [27][L][L]
@@ -836,12 +855,12 @@ __global__ void k_group_rap(CLevel prev, CLevel cur, const double* __restrict__ 
       const long long G2 = Gx + (long long)cur.mx * (Gy + (long long)cur.my * Gz);
       const int lc2 = (ncx % g) + g * ((ncy % g) + g * (ncz % g));
       const int gn = nbr_index(Gx - gx, Gy - gy, Gz - gz);
-      const double* Tc = Tp + (c * 27 + nn) * Lp * Lp;
+      const TI* Tc = Tp + (c * 27 + nn) * Lp * Lp;
       const double* ps2 = Psi + G2 * (long long)n * L + (long long)lc2 * Lp * L;
       for (int w = threadIdx.x; w < Lp * L; w += blockDim.x) {
         const int i = w / L, bb = w % L;
         double s = 0.0;
-        for (int j = 0; j < Lp; ++j) s += Tc[i * Lp + j] * ps2[j * L + bb];
+        for (int j = 0; j < Lp; ++j) s += (double)Tc[i * Lp + j] * ps2[j * L + bb];
         Wt[w] = s;
       }
       __syncthreads();
@@ -854,35 +873,47 @@ __global__ void k_group_rap(CLevel prev, CLevel cur, const double* __restrict__ 
       __syncthreads();
     }
   }
-  for (int i = threadIdx.x; i < 27 * L * L; i += blockDim.x) T[G * 27 * L * L + i] = out[i];
+  for (int i = threadIdx.x; i < 27 * L * L; i += blockDim.x) T[G * 27 * L * L + i] = (TO)out[i];
 }
-cudaError_t group_rap(const CLevel& prev, const CLevel& cur, const double* Psi, const double* tiles_prev, double* tiles,
+template <class TI, class TO>
+cudaError_t group_rap(const CLevel& prev, const CLevel& cur, const double* Psi, const TI* tiles_prev, TO* tiles,
                       cudaStream_t st) {
   const size_t sm = (27 * (size_t)cur.L * cur.L + (size_t)prev.L * cur.L) * sizeof(double);
-  cudaError_t e = cudaFuncSetAttribute(k_group_rap, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = cudaFuncSetAttribute(k_group_rap<TI, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  note_launch(), k_group_rap<<<(unsigned)cur.ncell, 256, sm, st>>>(prev, cur, Psi, tiles_prev, tiles);
+  note_launch(), k_group_rap<TI, TO><<<(unsigned)cur.ncell, 256, sm, st>>>(prev, cur, Psi, tiles_prev, tiles);
   return cudaGetLastError();
 }
+#define INST_GRAP(TI, TO)                                                                                     \
+  template cudaError_t group_rap<TI, TO>(const CLevel&, const CLevel&, const double*, const TI*, TO*, cudaStream_t);
+INST_GRAP(double, double)
+INST_GRAP(float, float)
+INST_GRAP(float, double)
 
 // inactive dofs (zero basis vectors) get an identity row in the centre tile
-__global__ void k_fix_inactive(CLevel lv, const uint8_t* __restrict__ act, double* __restrict__ T) {
+template <class TT>
+__global__ void k_fix_inactive(CLevel lv, const uint8_t* __restrict__ act, TT* __restrict__ T) {
   const long long nd = lv.ncell * lv.L;
   for (long long d = blockIdx.x * (long long)blockDim.x + threadIdx.x; d < nd; d += (long long)gridDim.x * blockDim.x) {
     if (act[d]) continue;
     const long long c = d / lv.L;
     const int i = (int)(d % lv.L);
-    T[((c * 27 + 13) * lv.L + i) * lv.L + i] = 1.0;
+    T[((c * 27 + 13) * lv.L + i) * lv.L + i] = (TT)1;
   }
 }
-cudaError_t fix_inactive(const CLevel& lv, const uint8_t* act, double* tiles, cudaStream_t st) {
+template <class TT>
+cudaError_t fix_inactive(const CLevel& lv, const uint8_t* act, TT* tiles, cudaStream_t st) {
   const long long nd = lv.ncell * lv.L;
-  note_launch(), k_fix_inactive<<<(unsigned)((nd + 255) / 256), 256, 0, st>>>(lv, act, tiles);
+  note_launch(), k_fix_inactive<TT><<<(unsigned)((nd + 255) / 256), 256, 0, st>>>(lv, act, tiles);
   return cudaGetLastError();
 }
+template cudaError_t fix_inactive<double>(const CLevel&, const uint8_t*, double*, cudaStream_t);
+template cudaError_t fix_inactive<float>(const CLevel&, const uint8_t*, float*, cudaStream_t);
 
 // l1-block-Jacobi: inverse of (A_cc + diag(sum_{off-cell} |a_ij|)), FP64 Gauss-Jordan
-__global__ void k_l1inv(CLevel lv, const double* __restrict__ T, double* __restrict__ Di64, float* __restrict__ Di32) {
+// (TT: the stored tile type, widened on load; Di64 may be NULL)
+template <class TT>
+__global__ void k_l1inv(CLevel lv, const TT* __restrict__ T, double* __restrict__ Di64, float* __restrict__ Di32) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int L = lv.L;
   double* M = (double*)sm + threadIdx.x * 2 * L * L;  // [L][2L] augmented
@@ -892,12 +923,12 @@ __global__ void k_l1inv(CLevel lv, const double* __restrict__ T, double* __restr
     double off = 0.0;
     for (int n = 0; n < 27; ++n) {
       if (n == 13) continue;
-      const double* row = T + ((c * 27 + n) * L + i) * L;
-      for (int j = 0; j < L; ++j) off += fabs(row[j]);
+      const TT* row = T + ((c * 27 + n) * L + i) * L;
+      for (int j = 0; j < L; ++j) off += fabs((double)row[j]);
     }
-    const double* row = T + ((c * 27 + 13) * L + i) * L;
+    const TT* row = T + ((c * 27 + 13) * L + i) * L;
     for (int j = 0; j < L; ++j) {
-      M[i * 2 * L + j] = row[j] + (i == j ? off : 0.0);
+      M[i * 2 * L + j] = (double)row[j] + (i == j ? off : 0.0);
       M[i * 2 * L + L + j] = i == j ? 1.0 : 0.0;
     }
   }
@@ -924,20 +955,23 @@ __global__ void k_l1inv(CLevel lv, const double* __restrict__ T, double* __restr
   for (int i = 0; i < L; ++i)
     for (int j = 0; j < L; ++j) {
       const double v = M[i * 2 * L + L + j];
-      Di64[(c * L + i) * L + j] = v;
+      if (Di64) Di64[(c * L + i) * L + j] = v;
       Di32[(c * L + i) * L + j] = (float)v;
     }
 }
-cudaError_t l1_inverse(const CLevel& lv, const double* tiles, double* Dinv64, float* Dinv32, cudaStream_t st) {
+template <class TT>
+cudaError_t l1_inverse(const CLevel& lv, const TT* tiles, double* Dinv64, float* Dinv32, cudaStream_t st) {
   int nt = 64;
   size_t per = 2 * (size_t)lv.L * lv.L * sizeof(double);
   while (nt > 1 && per * nt > 96 * 1024) nt >>= 1;
   const size_t sm = per * nt;
-  cudaError_t e = cudaFuncSetAttribute(k_l1inv, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+  cudaError_t e = cudaFuncSetAttribute(k_l1inv<TT>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   if (e != cudaSuccess) return e;
-  note_launch(), k_l1inv<<<(unsigned)((lv.ncell + nt - 1) / nt), nt, sm, st>>>(lv, tiles, Dinv64, Dinv32);
+  note_launch(), k_l1inv<TT><<<(unsigned)((lv.ncell + nt - 1) / nt), nt, sm, st>>>(lv, tiles, Dinv64, Dinv32);
   return cudaGetLastError();
 }
+template cudaError_t l1_inverse<double>(const CLevel&, const double*, double*, float*, cudaStream_t);
+template cudaError_t l1_inverse<float>(const CLevel&, const float*, double*, float*, cudaStream_t);
 
 // dense coarsest operator A[(c,i)][(c',j)]
 __global__ void k_dense(CLevel lv, const double* __restrict__ T, double* __restrict__ A) {
@@ -975,22 +1009,26 @@ cudaError_t cvt_f64_f32(const double* a, float* b, long long n, cudaStream_t st)
   return cudaGetLastError();
 }
 
-__global__ void k_phi_nat(Geom g, const double* __restrict__ phi, int L, double* __restrict__ out) {
+template <class C>
+__global__ void k_phi_nat(Geom g, const C* __restrict__ phi, int L, double* __restrict__ out) {
   const long long n = (long long)g.nx * g.ny * g.nz;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const int x = (int)(i % g.nx);
     const long long t = i / g.nx;
     const int y = (int)(t % g.ny), z = (int)(t / g.ny);
     const long long nd = nidx(g, x, y, z);
-    for (int a = 0; a < L; ++a) out[i * L + a] = phi[nd * L + a];
+    for (int a = 0; a < L; ++a) out[i * L + a] = (double)phi[nd * L + a];
   }
 }
-cudaError_t phi_natural(const Geom& g, const double* phi_pad, int L1, double* out, cudaStream_t st) {
+template <class C>
+cudaError_t phi_natural(const Geom& g, const C* phi_pad, int L1, double* out, cudaStream_t st) {
   const long long n = (long long)g.nx * g.ny * g.nz;
   long long nb = (n + 255) / 256;
   if (nb > 152 * 32) nb = 152 * 32;
-  note_launch(), k_phi_nat<<<(unsigned)nb, 256, 0, st>>>(g, phi_pad, L1, out);
+  note_launch(), k_phi_nat<C><<<(unsigned)nb, 256, 0, st>>>(g, phi_pad, L1, out);
   return cudaGetLastError();
 }
+template cudaError_t phi_natural<double>(const Geom&, const double*, int, double*, cudaStream_t);
+template cudaError_t phi_natural<float>(const Geom&, const float*, int, double*, cudaStream_t);
 
 }  // namespace thermo

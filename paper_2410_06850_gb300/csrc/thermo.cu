@@ -69,13 +69,20 @@ struct thermo_ctx {
   int L1 = 4;
   long long nnode = 0, nelem = 0;
   std::vector<void*> allocs;
+  bool dry = false;          // allocation plan only: count bytes, allocate nothing
+  long long plan_bytes = 0;
+  bool lean = false;         // FP32-only hierarchy (opt.lean)
+  double* slab64 = nullptr;  // u, r, p, q (lean: also the FP64 set-up intermediates)
+  float* slab32 = nullptr;   // r32, z32, ea32, eb32, ec32, tmp32 (lean: also the row-sum corrections)
+  long long slab64_n = 0, slab32_n = 0;  // elements
   // fine data
   uint32_t* bits = nullptr;
   double* k64 = nullptr;
   float* k32 = nullptr;
   bf16* k16 = nullptr;
   float* klo = nullptr;  // kappa - (double)k32: with k32 a float-float copy of k64
-  double* xd = nullptr;     // design copy (natural)
+  double* xd = nullptr;     // design copy (natural; FP64 input)
+  float* xf = nullptr;      // design copy (natural; FP32 input, opt.density_fp32)
   double *f = nullptr, *blift = nullptr, *TD = nullptr, *zero64 = nullptr;
   double *u = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *bv = nullptr, *tmp = nullptr, *z64 = nullptr;
   double *ea64 = nullptr, *eb64 = nullptr, *ec64 = nullptr;
@@ -131,6 +138,11 @@ static thermo_status fail(thermo_ctx* c, thermo_status s, const char* fmt, ...) 
 
 template <class T>
 static cudaError_t dalloc(thermo_ctx* ctx, T** p, size_t n) {
+  if (ctx->dry) {
+    ctx->plan_bytes += (long long)((n * sizeof(T) + 64 + 511) & ~(size_t)511);
+    *p = nullptr;
+    return cudaSuccess;
+  }
   void* v = nullptr;
   cudaError_t e = cudaMalloc(&v, n * sizeof(T) + 64);
   if (e != cudaSuccess) return e;
@@ -203,22 +215,11 @@ static int pick_tile(int N, int b, int maxt) {
   return 0;
 }
 
-extern "C" thermo_status thermo_create(const int grid[3], const double h[3], const uint8_t* mask, const double* dval,
-                                       const double* source, void* stream, const thermo_options* opt_in,
-                                       thermo_ctx** out) {
-  if (!out) return THERMO_EINVAL;
-  *out = nullptr;
-  if (!grid || !h || !mask || !source) return THERMO_EINVAL;
-  thermo_options opt;
-  if (opt_in)
-    opt = *opt_in;
-  else if (thermo_default_options(grid, &opt) != THERMO_OK)
-    return THERMO_EINVAL;
-  thermo_ctx* ctx = new (std::nothrow) thermo_ctx();
-  if (!ctx) return THERMO_ENOMEM;
-  *out = ctx;
-  ctx->st = (cudaStream_t)stream;
-  ctx->opt = opt;
+// Validation, geometry, hierarchy shape and every device buffer of a context
+// whose options are set.  With ctx->dry, buffers are only counted
+// (ctx->plan_bytes) and nothing touches a GPU.
+static thermo_status build_context(thermo_ctx* ctx, const int grid[3], const double h[3], bool has_dval) {
+  const thermo_options& opt = ctx->opt;
   for (int k = 0; k < 3; ++k) {
     if (grid[k] <= 0 || !(h[k] > 0.0)) return fail(ctx, THERMO_EINVAL, "grid and h must be positive");
   }
@@ -297,7 +298,7 @@ extern "C" thermo_status thermo_create(const int grid[3], const double h[3], con
   }
   if (!g.TX || !g.TY || !g.ZC) return fail(ctx, THERMO_EINVAL, "unsupported grid / block combination");
   g.NZ2 = g.NZD = g.Nz / g.ZC;
-  {
+  if (!ctx->dry) {
     int dev = 0, sms = 0;
     cudaGetDevice(&dev);
     if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) sms = 0;
@@ -348,48 +349,127 @@ extern "C" thermo_status thermo_create(const int grid[3], const double h[3], con
   }
   // allocations
   const long long ns = g.nsize, es = g.esize;
+  const long long nsa = (ns + 127) & ~63LL;  // slab stride: 64-element multiple, >= 64 elements of slack
+  const bool fp64 = opt.prec == THERMO_FP64;
+  if (opt.lean != 0 && opt.lean != 1) return fail(ctx, THERMO_EINVAL, "lean must be 0 or 1");
+  if (opt.lean && (fp64 || opt.pc != THERMO_PC_MMG))
+    return fail(ctx, THERMO_EINVAL, "lean needs a mixed-precision MMG context");
+  ctx->lean = opt.lean != 0;
+  const bool lean = ctx->lean;
   CK(dalloc(ctx, &ctx->g.err, 1));  // stage time-out word of this context's fine kernels
   ctx->g.wait = kStageWait;
   CK(dalloc(ctx, &ctx->bits, g.msize));
   CK(dalloc(ctx, &ctx->k64, es));
   CK(dalloc(ctx, &ctx->k32, es));
-  CK(dalloc(ctx, &ctx->k16, es));
+  if (opt.prec == THERMO_MIXED_BF16S) CK(dalloc(ctx, &ctx->k16, es));
   CK(dalloc(ctx, &ctx->klo, es));
-  CK(dalloc(ctx, &ctx->xd, ctx->nelem));
-  for (double** pp : {&ctx->f, &ctx->blift, &ctx->TD, &ctx->zero64, &ctx->u, &ctx->r, &ctx->p, &ctx->q, &ctx->bv,
-                      &ctx->tmp})
-    CK(dalloc(ctx, pp, ns));
-  if (opt.prec == THERMO_FP64 || opt.pc != THERMO_PC_MMG) {
-    CK(dalloc(ctx, &ctx->z64, ns));
+  if (opt.density_fp32)
+    CK(dalloc(ctx, &ctx->xf, ctx->nelem));
+  else
+    CK(dalloc(ctx, &ctx->xd, ctx->nelem));
+  for (double** pp : {&ctx->f, &ctx->blift, &ctx->tmp}) CK(dalloc(ctx, pp, ns));
+  // a solve's own right-hand side: the lean form shares tmp (no entry point that
+  // uses tmp runs inside a solve)
+  if (opt.lean)
+    ctx->bv = ctx->tmp;
+  else
+    CK(dalloc(ctx, &ctx->bv, ns));
+  if (has_dval) CK(dalloc(ctx, &ctx->TD, ns));
+  if (!lean) CK(dalloc(ctx, &ctx->zero64, ns));
+  if (fp64 || opt.pc != THERMO_PC_MMG) CK(dalloc(ctx, &ctx->z64, ns));
+  if (fp64) {
+    CK(dalloc(ctx, &ctx->ea64, ns));
+    CK(dalloc(ctx, &ctx->eb64, ns));
+    CK(dalloc(ctx, &ctx->ec64, ns));
   }
-  CK(dalloc(ctx, &ctx->ea64, ns));
-  CK(dalloc(ctx, &ctx->eb64, ns));
-  CK(dalloc(ctx, &ctx->ec64, ns));
-  for (float** pp : {&ctx->r32, &ctx->z32, &ctx->ea32, &ctx->eb32, &ctx->ec32, &ctx->tmp32}) CK(dalloc(ctx, pp, ns));
+  // set-up intermediates that the lean form keeps in the slabs: FP64 Phi, each
+  // level's FP64 Psi (one at a time), the row-sum corrections of all levels
+  long long psi_max = 0, dc_total = 0;
+  for (int l = 1; l <= ctx->nlev; ++l) {
+    const CLevel& cl = ctx->lev[l].cl;
+    if (l >= 2) {
+      const long long np = cl.ncell * (long long)cl.g * cl.g * cl.g * ctx->lev[l - 1].cl.L * cl.L;
+      psi_max = np > psi_max ? np : psi_max;
+    }
+    dc_total += (long long)(ctx->nlev - l) * cl.ncell * cl.L * cl.L;
+  }
+  {
+    // u, r, p, q: one slab (lean: also FP64 Phi, then each level's FP64 Psi)
+    long long n64 = 4 * nsa;
+    if (lean) {
+      n64 = std::max(n64, ns * ctx->L1);
+      n64 = std::max(n64, psi_max);
+    }
+    CK(dalloc(ctx, &ctx->slab64, n64));
+    ctx->slab64_n = n64;
+    // r32, z32, ea32, eb32, ec32, tmp32: one slab (lean: also the row-sum corrections)
+    long long n32 = 6 * nsa;
+    const bool dc_in_slab = lean && 2 * dc_total <= n32;
+    CK(dalloc(ctx, &ctx->slab32, n32));
+    ctx->slab32_n = n32;
+    if (!ctx->dry) {
+      double* s64 = ctx->slab64;
+      ctx->u = s64;
+      ctx->r = s64 + nsa;
+      ctx->p = s64 + 2 * nsa;
+      ctx->q = s64 + 3 * nsa;
+      float* s32 = ctx->slab32;
+      float** v32[6] = {&ctx->r32, &ctx->z32, &ctx->ea32, &ctx->eb32, &ctx->ec32, &ctx->tmp32};
+      for (int k = 0; k < 6; ++k) *v32[k] = s32 + k * nsa;
+      if (lean) ctx->phi64 = s64;
+      if (dc_in_slab) {
+        double* d = reinterpret_cast<double*>(s32);
+        for (int l = 1; l <= ctx->nlev; ++l) {
+          Lev& lv = ctx->lev[l];
+          lv.ntc = ctx->nlev - l;
+          if (lv.ntc > 0) {
+            lv.Dc = d;
+            d += (long long)lv.ntc * lv.cl.ncell * lv.cl.L * lv.cl.L;
+          }
+          if (l >= 2) lv.Psi64 = s64;
+        }
+      } else if (lean) {
+        for (int l = 2; l <= ctx->nlev; ++l) ctx->lev[l].Psi64 = s64;
+      }
+    }
+    if (lean && !dc_in_slab)
+      for (int l = 1; l < ctx->nlev; ++l) {
+        Lev& lv = ctx->lev[l];
+        lv.ntc = ctx->nlev - l;
+        CK(dalloc(ctx, &lv.Dc, (long long)lv.ntc * lv.cl.ncell * lv.cl.L * lv.cl.L));
+      }
+  }
   if (opt.prec == THERMO_MIXED_BF16S) {
     for (bf16** pp : {&ctx->r16, &ctx->ea16, &ctx->eb16, &ctx->ec16}) CK(dalloc(ctx, pp, ns));
   }
-  CK(dalloc(ctx, &ctx->phi64, ns * ctx->L1));
+  if (!lean) CK(dalloc(ctx, &ctx->phi64, ns * ctx->L1));
   CK(dalloc(ctx, &ctx->phi32, ns * ctx->L1));
   for (int l = 1; l <= ctx->nlev; ++l) {
     Lev& lv = ctx->lev[l];
     const CLevel& cl = lv.cl;
     const long long nd = cl.ncell * cl.L;
     const long long nt = cl.ncell * 27 * cl.L * cl.L;
-    CK(dalloc(ctx, &lv.T64, nt));
+    if (!lean || l == ctx->nlev) CK(dalloc(ctx, &lv.T64, nt));
     if (l < ctx->nlev) CK(dalloc(ctx, &lv.T32, nt));
-    CK(dalloc(ctx, &lv.Di64, cl.ncell * cl.L * cl.L));
+    if (!lean) CK(dalloc(ctx, &lv.Di64, cl.ncell * cl.L * cl.L));
     CK(dalloc(ctx, &lv.Di32, cl.ncell * cl.L * cl.L));
     if (l >= 2) {
       const long long np = cl.ncell * (long long)cl.g * cl.g * cl.g * ctx->lev[l - 1].cl.L * cl.L;
-      CK(dalloc(ctx, &lv.Psi64, np));
+      if (!lean) CK(dalloc(ctx, &lv.Psi64, np));
       CK(dalloc(ctx, &lv.Psi32, np));
     }
     CK(dalloc(ctx, &lv.act, nd));
     CK(dalloc(ctx, &lv.eig, nd));
     lv.ntc = ctx->nlev - l;
-    if (lv.ntc > 0) CK(dalloc(ctx, &lv.Dc, (long long)lv.ntc * cl.ncell * cl.L * cl.L));
-    for (double** pp : {&lv.r64, &lv.e64, &lv.t64, &lv.s64}) CK(dalloc(ctx, pp, nd));
+    if (!lean && lv.ntc > 0) CK(dalloc(ctx, &lv.Dc, (long long)lv.ntc * cl.ncell * cl.L * cl.L));
+    if (!lean) {
+      CK(dalloc(ctx, &lv.r64, nd));
+      CK(dalloc(ctx, &lv.e64, nd));
+    }
+    if (fp64) {
+      CK(dalloc(ctx, &lv.t64, nd));
+      CK(dalloc(ctx, &lv.s64, nd));
+    }
     for (float** pp : {&lv.r32, &lv.e32, &lv.t32, &lv.s32}) CK(dalloc(ctx, pp, nd));
   }
   CK(dalloc(ctx, &ctx->Ainv, (long long)ctx->ncoarse * ctx->ncoarse));
@@ -403,7 +483,8 @@ extern "C" thermo_status thermo_create(const int grid[3], const double h[3], con
       gc[l - 2] = acc;
     }
     CK(dalloc(ctx, &ctx->gcum_dev, THERMO_MAX_LEVELS));
-    CK(cudaMemcpyAsync(ctx->gcum_dev, gc.data(), THERMO_MAX_LEVELS * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
+    if (!ctx->dry)
+      CK(cudaMemcpyAsync(ctx->gcum_dev, gc.data(), THERMO_MAX_LEVELS * sizeof(int), cudaMemcpyHostToDevice, ctx->st));
   }
   CK(dalloc(ctx, &ctx->sc, 1));
   CK(dalloc(ctx, &ctx->dscal, 16));
@@ -416,9 +497,34 @@ extern "C" thermo_status thermo_create(const int grid[3], const double h[3], con
     CK(dalloc(ctx, &ctx->red.counter, 4));
     ctx->red.nblocks = (int)np;
   }
+  if (ctx->dry) return THERMO_OK;
   CK(cudaMallocHost((void**)&ctx->sc_h, sizeof(CgScalars)));
   CK(cudaMallocHost((void**)&ctx->status_h, 8 * sizeof(int)));
   CK(cudaMallocHost((void**)&ctx->dscal_h, 16 * sizeof(double)));
+  return THERMO_OK;
+}
+
+extern "C" thermo_status thermo_create(const int grid[3], const double h[3], const uint8_t* mask, const double* dval,
+                                       const double* source, void* stream, const thermo_options* opt_in,
+                                       thermo_ctx** out) {
+  if (!out) return THERMO_EINVAL;
+  *out = nullptr;
+  if (!grid || !h || !mask || !source) return THERMO_EINVAL;
+  thermo_options opt;
+  if (opt_in)
+    opt = *opt_in;
+  else if (thermo_default_options(grid, &opt) != THERMO_OK)
+    return THERMO_EINVAL;
+  thermo_ctx* ctx = new (std::nothrow) thermo_ctx();
+  if (!ctx) return THERMO_ENOMEM;
+  *out = ctx;
+  ctx->st = (cudaStream_t)stream;
+  ctx->opt = opt;
+  {
+    const thermo_status s = build_context(ctx, grid, h, dval != nullptr);
+    if (s != THERMO_OK) return s;
+  }
+  const Geom& g = ctx->g;
   // boundary data and load
   CK(mask_to_bits(g, mask, ctx->bits, ctx->st));
   CK(count_mask(g, mask, ctx->nnode, ctx->status_dev + 3, ctx->st));
@@ -430,6 +536,27 @@ extern "C" thermo_status thermo_create(const int grid[3], const double h[3], con
   CK(load_vector(g, source, ctx->f, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
   return THERMO_OK;
+}
+
+extern "C" thermo_status thermo_plan_bytes(const int grid[3], const thermo_options* opt_in, int has_dval,
+                                           long long* bytes) {
+  if (!grid || !bytes) return THERMO_EINVAL;
+  thermo_options opt;
+  if (opt_in)
+    opt = *opt_in;
+  else if (thermo_default_options(grid, &opt) != THERMO_OK)
+    return THERMO_EINVAL;
+  for (int k = 0; k < 3; ++k)
+    if (grid[k] <= 0) return THERMO_EINVAL;
+  thermo_ctx* ctx = new (std::nothrow) thermo_ctx();
+  if (!ctx) return THERMO_ENOMEM;
+  ctx->opt = opt;
+  ctx->dry = true;
+  const double h[3] = {1.0 / grid[0], 1.0 / grid[1], 1.0 / grid[2]};
+  const thermo_status s = build_context(ctx, grid, h, has_dval != 0);
+  if (s == THERMO_OK) *bytes = ctx->plan_bytes;
+  delete ctx;
+  return s;
 }
 
 extern "C" void thermo_destroy(thermo_ctx* ctx) {
@@ -454,11 +581,13 @@ extern "C" thermo_status thermo_set_density(thermo_ctx* ctx, const void* x, doub
   if (!x) return fail(ctx, THERMO_EINVAL, "x is NULL");
   if (!(p >= 1.0) || !(kmin > 0.0) || !(kmax >= kmin) || !std::isfinite(kmax))
     return fail(ctx, THERMO_EINVAL, "need p >= 1 and 0 < kmin <= kmax");
-  if (ctx->opt.density_fp32)
-    CK(widen_f32(static_cast<const float*>(x), ctx->xd, ctx->nelem, ctx->st));
-  else
+  if (ctx->xf) {
+    CK(cudaMemcpyAsync(ctx->xf, x, ctx->nelem * sizeof(float), cudaMemcpyDeviceToDevice, ctx->st));
+    CK(simp_kappa<float>(ctx->g, ctx->xf, p, kmin, kmax, ctx->k64, ctx->k32, ctx->k16, ctx->klo, ctx->st));
+  } else {
     CK(cudaMemcpyAsync(ctx->xd, x, ctx->nelem * sizeof(double), cudaMemcpyDeviceToDevice, ctx->st));
-  CK(simp_kappa(ctx->g, ctx->xd, p, kmin, kmax, ctx->k64, ctx->k32, ctx->k16, ctx->klo, ctx->st));
+    CK(simp_kappa<double>(ctx->g, ctx->xd, p, kmin, kmax, ctx->k64, ctx->k32, ctx->k16, ctx->klo, ctx->st));
+  }
   // lifted right-hand side b = f - A_FD T_D (b_D = T_D)
   CK(dirichlet_rhs(ctx->g, ctx->bits, ctx->k64, ctx->f, ctx->TD, ctx->blift, ctx->st));
   ctx->sp = p;
@@ -544,26 +673,63 @@ extern "C" thermo_status thermo_setup_precond(thermo_ctx* ctx) {
     }
   }
   Lev& l1 = ctx->lev[1];
+  // lean: FP64 Phi shares the CG vectors' slab; clear it (padding nodes included)
+  if (ctx->lean) CK(cudaMemsetAsync(ctx->phi64, 0, g.nsize * L1 * sizeof(double), st));
   CK(level1_eigen(g, ctx->bits, ctx->k64, L1, ctx->phi64, l1.eig, l1.act, ctx->status_dev, st));
   CK(level1_rowsum_corr(g, ctx->bits, ctx->k64, L1, ctx->phi64, l1.ntc, ctx->gcum_dev, l1.Dc, st));
-  CK(level1_rap(g, ctx->bits, ctx->k64, L1, ctx->phi64, l1.T64, st));
-  CK(fix_inactive(l1.cl, l1.act, l1.T64, st));
-  for (int l = 2; l <= ctx->nlev; ++l) {
-    Lev& pv = ctx->lev[l - 1];
-    Lev& cu = ctx->lev[l];
-    CK(group_eigen(pv.cl, cu.cl, pv.T64, pv.Dc, pv.act, cu.Psi64, cu.eig, cu.act, ctx->status_dev, st));
-    if (cu.ntc > 0) CK(group_project_corr(pv.cl, cu.cl, cu.Psi64, pv.Dc, cu.Dc, cu.ntc, st));
-    CK(group_rap(pv.cl, cu.cl, cu.Psi64, pv.T64, cu.T64, st));
-    CK(fix_inactive(cu.cl, cu.act, cu.T64, st));
-    const long long np = cu.cl.ncell * (long long)cu.cl.g * cu.cl.g * cu.cl.g * pv.cl.L * cu.cl.L;
-    CK(cvt_f64_f32(cu.Psi64, cu.Psi32, np, st));
+  if (ctx->lean) {
+    // FP32 hierarchy: every level but the coarsest is rounded once where it is
+    // made; the next level is built (FP64 sums) from what is stored.  FP64 Phi
+    // and Psi live in the CG vectors' slab, one at a time.
+    const int top = ctx->nlev;
+    if (top == 1) {
+      CK(level1_rap<double>(g, ctx->bits, ctx->k64, L1, ctx->phi64, l1.T64, st));
+      CK(fix_inactive<double>(l1.cl, l1.act, l1.T64, st));
+    } else {
+      CK(level1_rap<float>(g, ctx->bits, ctx->k64, L1, ctx->phi64, l1.T32, st));
+      CK(fix_inactive<float>(l1.cl, l1.act, l1.T32, st));
+    }
+    CK(cvt_f64_f32(ctx->phi64, ctx->phi32, g.nsize * L1, st));
+    for (int l = 2; l <= top; ++l) {
+      Lev& pv = ctx->lev[l - 1];
+      Lev& cu = ctx->lev[l];
+      CK(group_eigen<float>(pv.cl, cu.cl, pv.T32, pv.Dc, pv.act, cu.Psi64, cu.eig, cu.act, ctx->status_dev, st));
+      if (cu.ntc > 0) CK(group_project_corr(pv.cl, cu.cl, cu.Psi64, pv.Dc, cu.Dc, cu.ntc, st));
+      if (l == top) {
+        CK((group_rap<float, double>(pv.cl, cu.cl, cu.Psi64, pv.T32, cu.T64, st)));
+        CK(fix_inactive<double>(cu.cl, cu.act, cu.T64, st));
+      } else {
+        CK((group_rap<float, float>(pv.cl, cu.cl, cu.Psi64, pv.T32, cu.T32, st)));
+        CK(fix_inactive<float>(cu.cl, cu.act, cu.T32, st));
+      }
+      const long long np = cu.cl.ncell * (long long)cu.cl.g * cu.cl.g * cu.cl.g * pv.cl.L * cu.cl.L;
+      CK(cvt_f64_f32(cu.Psi64, cu.Psi32, np, st));
+    }
+    for (int l = 1; l < top; ++l) CK(l1_inverse<float>(ctx->lev[l].cl, ctx->lev[l].T32, nullptr, ctx->lev[l].Di32, st));
+    // the fine kernels read the padded layout's ghost nodes as zeros: clear what
+    // set-up left in the vectors' memory
+    CK(cudaMemsetAsync(ctx->slab64, 0, ctx->slab64_n * sizeof(double), st));
+    CK(cudaMemsetAsync(ctx->slab32, 0, ctx->slab32_n * sizeof(float), st));
+  } else {
+    CK(level1_rap<double>(g, ctx->bits, ctx->k64, L1, ctx->phi64, l1.T64, st));
+    CK(fix_inactive<double>(l1.cl, l1.act, l1.T64, st));
+    for (int l = 2; l <= ctx->nlev; ++l) {
+      Lev& pv = ctx->lev[l - 1];
+      Lev& cu = ctx->lev[l];
+      CK(group_eigen<double>(pv.cl, cu.cl, pv.T64, pv.Dc, pv.act, cu.Psi64, cu.eig, cu.act, ctx->status_dev, st));
+      if (cu.ntc > 0) CK(group_project_corr(pv.cl, cu.cl, cu.Psi64, pv.Dc, cu.Dc, cu.ntc, st));
+      CK((group_rap<double, double>(pv.cl, cu.cl, cu.Psi64, pv.T64, cu.T64, st)));
+      CK(fix_inactive<double>(cu.cl, cu.act, cu.T64, st));
+      const long long np = cu.cl.ncell * (long long)cu.cl.g * cu.cl.g * cu.cl.g * pv.cl.L * cu.cl.L;
+      CK(cvt_f64_f32(cu.Psi64, cu.Psi32, np, st));
+    }
+    for (int l = 1; l < ctx->nlev; ++l) {
+      Lev& lv = ctx->lev[l];
+      CK(l1_inverse<double>(lv.cl, lv.T64, lv.Di64, lv.Di32, st));
+      CK(cvt_f64_f32(lv.T64, lv.T32, lv.cl.ncell * 27 * lv.cl.L * lv.cl.L, st));
+    }
+    CK(cvt_f64_f32(ctx->phi64, ctx->phi32, g.nsize * L1, st));
   }
-  for (int l = 1; l < ctx->nlev; ++l) {
-    Lev& lv = ctx->lev[l];
-    CK(l1_inverse(lv.cl, lv.T64, lv.Di64, lv.Di32, st));
-    CK(cvt_f64_f32(lv.T64, lv.T32, lv.cl.ncell * 27 * lv.cl.L * lv.cl.L, st));
-  }
-  CK(cvt_f64_f32(ctx->phi64, ctx->phi32, g.nsize * L1, st));
   CK(dense_assemble(ctx->lev[ctx->nlev].cl, ctx->lev[ctx->nlev].T64, ctx->cholA, st));
   CK(cholesky_inverse(ctx->ncoarse, ctx->cholA, ctx->Ainv, ctx->cholW, ctx->status_dev, st));
   CK(cudaMemcpyAsync(ctx->status_h, ctx->status_dev, 4 * sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -842,11 +1008,33 @@ static void* rptr(thermo_ctx* ctx) {
   return k == 1 ? (void*)ctx->r32 : (k == 2 ? (void*)ctx->r16 : nullptr);
 }
 
-// y = P A_L^-1 P^T v added to u (composite restriction / prolongation, FP64)
+// y = P A_L^-1 P^T v added to u (composite restriction / prolongation: FP64;
+// the lean form has only the FP32 hierarchy and runs the chain in FP32 on a
+// rounded copy of v, adding the FP64-summed prolongation to u)
 static thermo_status coarse_correction(thermo_ctx* ctx, const double* v, double* u) {
   const Geom& g = ctx->g;
   cudaStream_t st = ctx->st;
   Lev& l1 = ctx->lev[1];
+  if (ctx->lean) {
+    CK(vec_copy_cvt(g, v, ctx->r32, 1, st));
+    CK(cudaMemsetAsync(ctx->ea32, 0, g.nsize * sizeof(float), st));
+    CK(fine_restrict<float>(g, ctx->bits, ctx->k32, ctx->r32, ctx->ea32, ctx->phi32, l1.r32, ctx->L1, st));
+    for (int l = 1; l < ctx->nlev; ++l) {
+      Lev& a = ctx->lev[l];
+      Lev& b = ctx->lev[l + 1];
+      CK(coarse_restrict<float>(a.cl, b.cl, b.Psi32, a.r32, b.r32, st));
+    }
+    Lev& top = ctx->lev[ctx->nlev];
+    CK(dense_gemv<float>(ctx->ncoarse, ctx->Ainv, top.r32, top.e32, st));
+    for (int l = ctx->nlev - 1; l >= 1; --l) {
+      Lev& a = ctx->lev[l];
+      Lev& b = ctx->lev[l + 1];
+      CK(cudaMemsetAsync(a.e32, 0, a.cl.ncell * a.cl.L * sizeof(float), st));
+      CK(coarse_prolong<float>(a.cl, b.cl, b.Psi32, b.e32, a.e32, st));
+    }
+    CK(fine_prolong_add<float>(g, ctx->phi32, ctx->L1, l1.e32, u, st));
+    return THERMO_OK;
+  }
   CK(fine_restrict<double>(g, ctx->bits, ctx->k64, v, ctx->zero64, ctx->phi64, l1.r64, ctx->L1, st));
   for (int l = 1; l < ctx->nlev; ++l) {
     Lev& a = ctx->lev[l];
@@ -861,7 +1049,7 @@ static thermo_status coarse_correction(thermo_ctx* ctx, const double* v, double*
     CK(cudaMemsetAsync(a.e64, 0, a.cl.ncell * a.cl.L * sizeof(double), st));
     CK(coarse_prolong<double>(a.cl, b.cl, b.Psi64, b.e64, a.e64, st));
   }
-  CK(fine_prolong_add(g, ctx->phi64, ctx->L1, l1.e64, u, st));
+  CK(fine_prolong_add<double>(g, ctx->phi64, ctx->L1, l1.e64, u, st));
   return THERMO_OK;
 }
 
@@ -903,8 +1091,10 @@ extern "C" thermo_status thermo_solve(thermo_ctx* ctx, const double* rhs, double
   // initial guess
   if (o.guess == THERMO_GUESS_GIVEN || o.guess == THERMO_GUESS_WARM_COARSE) {
     CK(pack_nodes(g, u, ctx->u, st));
-  } else {
+  } else if (ctx->TD) {
     CK(cudaMemcpyAsync(ctx->u, ctx->TD, g.nsize * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  } else {
+    CK(cudaMemsetAsync(ctx->u, 0, g.nsize * sizeof(double), st));
   }
   // the Dirichlet rows are identities: every iterate carries u_D = b_D
   CK(vec_copy_dir(g, ctx->bits, b, ctx->u, st));
@@ -1051,7 +1241,10 @@ extern "C" thermo_status thermo_sensitivity(thermo_ctx* ctx, const double* u, do
   if (!u || !dc) return fail(ctx, THERMO_EINVAL, "NULL argument");
   if (!ctx->have_density) return fail(ctx, THERMO_ESTATE, "sensitivity before set_density");
   CK(pack_nodes(ctx->g, u, ctx->tmp, ctx->st));
-  CK(sensitivity(ctx->g, ctx->tmp, ctx->xd, ctx->sp, ctx->skmin, ctx->skmax, dc, ctx->st));
+  if (ctx->xf)
+    CK(sensitivity<float>(ctx->g, ctx->tmp, ctx->xf, ctx->sp, ctx->skmin, ctx->skmax, dc, ctx->st));
+  else
+    CK(sensitivity<double>(ctx->g, ctx->tmp, ctx->xd, ctx->sp, ctx->skmin, ctx->skmax, dc, ctx->st));
   return THERMO_OK;
 }
 
@@ -1168,14 +1361,27 @@ extern "C" thermo_status thermo_export_level(thermo_ctx* ctx, int level, int wha
     if (level == 1) {
       need = ctx->nnode * ctx->L1;
       if (count < need) return fail(ctx, THERMO_EINVAL, "output too small (%lld < %lld)", count, need);
-      CK(phi_natural(ctx->g, ctx->phi64, ctx->L1, out, st));
+      if (ctx->lean)
+        CK(phi_natural<float>(ctx->g, ctx->phi32, ctx->L1, out, st));
+      else
+        CK(phi_natural<double>(ctx->g, ctx->phi64, ctx->L1, out, st));
       return THERMO_OK;
     }
     need = c.ncell * (long long)c.g * c.g * c.g * ctx->lev[level - 1].cl.L * c.L;
     src = lv.Psi64;
+    if (ctx->lean) {  // the FP32 copy, widened
+      if (count < need) return fail(ctx, THERMO_EINVAL, "output too small (%lld < %lld)", count, need);
+      CK(widen_f32(lv.Psi32, out, need, st));
+      return THERMO_OK;
+    }
   } else if (what == 1) {
     need = c.ncell * 27 * c.L * c.L;
     src = lv.T64;
+    if (!src) {  // lean form: the FP32 tiles, widened
+      if (count < need) return fail(ctx, THERMO_EINVAL, "output too small (%lld < %lld)", count, need);
+      CK(widen_f32(lv.T32, out, need, st));
+      return THERMO_OK;
+    }
   } else if (what == 2) {
     need = c.ncell * c.L;
     src = lv.eig;
@@ -1342,7 +1548,7 @@ extern "C" thermo_status thermo_bench_kernel(thermo_ctx* ctx, int which, int rep
       }
       case 9: {
         bytes = 0.0;
-        if (!ctx->z64) return cudaErrorInvalidValue;
+        if (!ctx->z64 || !ctx->ea64) return cudaErrorInvalidValue;
         const thermo_precision keep = ctx->opt.prec;
         ctx->opt.prec = THERMO_FP64;
         cudaError_t e = apply_precond(ctx);
@@ -1350,6 +1556,7 @@ extern "C" thermo_status thermo_bench_kernel(thermo_ctx* ctx, int which, int rep
         return e;
       }
       case 10:
+        if (!ctx->ea64) return cudaErrorInvalidValue;
         bytes = n * 32 + M * 8;
         return fine_smooth<double, double>(g, ctx->bits, ctx->k64, ctx->r, ctx->ea64, ctx->ec64, ctx->eb64, 0.3, 0.6,
                                            st);

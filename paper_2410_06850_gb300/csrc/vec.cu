@@ -162,10 +162,11 @@ cudaError_t count_mask(const Geom& g, const uint8_t* nat, long long n, int* out,
   return cudaGetLastError();
 }
 
-// Sec. 2.1 Eq. (1): kappa_e = kmin + x_e^p (kmax - kmin), kept in three precisions;
-// klo (optional) is the float remainder kappa - (double)k32, so that k32 + klo is a
+// Sec. 2.1 Eq. (1): kappa_e = kmin + x_e^p (kmax - kmin), kept in FP64, FP32 and
+// (optional, k16) BF16; klo (optional) is the float remainder kappa - (double)k32, so that k32 + klo is a
 // float-float copy of the FP64 value (used by the float-float fine apply)
-__global__ void k_simp(Geom g, const double* __restrict__ x, double p, double kmin, double kmax,
+template <class X>  // the stored design: double, or float when it is given in FP32
+__global__ void k_simp(Geom g, const X* __restrict__ x, double p, double kmin, double kmax,
                        double* __restrict__ k64, float* __restrict__ k32, bf16* __restrict__ k16,
                        float* __restrict__ klo) {
   const long long M = (long long)g.Nx * g.Ny * g.Nz;
@@ -173,20 +174,25 @@ __global__ void k_simp(Geom g, const double* __restrict__ x, double p, double km
     const int ex = (int)(e % g.Nx);
     const long long t = e / g.Nx;
     const int ey = (int)(t % g.Ny), ez = (int)(t / g.Ny);
-    const double k = kmin + pow(x[e], p) * (kmax - kmin);
+    const double k = kmin + pow((double)x[e], p) * (kmax - kmin);
     const long long i = eidx(g, ex, ey, ez);
     const float kh = (float)k;
     k64[i] = k;
     k32[i] = kh;
-    k16[i] = __float2bfloat16_rn(kh);
+    if (k16) k16[i] = __float2bfloat16_rn(kh);
     if (klo) klo[i] = (float)(k - (double)kh);
   }
 }
-cudaError_t simp_kappa(const Geom& g, const double* x, double p, double kmin, double kmax, double* k64, float* k32,
+template <class X>
+cudaError_t simp_kappa(const Geom& g, const X* x, double p, double kmin, double kmax, double* k64, float* k32,
                        bf16* k16, float* klo, cudaStream_t st) {
-  note_launch(), k_simp<<<grid1((long long)g.Nx * g.Ny * g.Nz), 256, 0, st>>>(g, x, p, kmin, kmax, k64, k32, k16, klo);
+  note_launch(), k_simp<X><<<grid1((long long)g.Nx * g.Ny * g.Nz), 256, 0, st>>>(g, x, p, kmin, kmax, k64, k32, k16, klo);
   return cudaGetLastError();
 }
+template cudaError_t simp_kappa<double>(const Geom&, const double*, double, double, double, double*, float*, bf16*,
+                                        float*, cudaStream_t);
+template cudaError_t simp_kappa<float>(const Geom&, const float*, double, double, double, double*, float*, bf16*,
+                                       float*, cudaStream_t);
 
 __global__ void k_widen(const float* __restrict__ a, double* __restrict__ b, long long n) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -230,7 +236,11 @@ __global__ void k_dir_rhs(Geom g, const uint32_t* __restrict__ bits, const doubl
     const int y = (int)(t % g.ny), z = (int)(t / g.ny);
     const long long ni = nidx(g, x, y, z);
     if (is_dir(g, bits, x, y, z)) {
-      b[ni] = TD[ni];
+      b[ni] = TD ? TD[ni] : 0.0;
+      continue;
+    }
+    if (!TD) {  // T_D = 0: nothing to lift
+      b[ni] = f[ni];
       continue;
     }
     double s = 0.0;
@@ -499,7 +509,8 @@ cudaError_t vec_axpy_pad(const Geom& g, double a, const double* x, double* y, cu
 // ---------------------------------------------------------------------------
 // Sec. 2.3: dc_e = -p x_e^(p-1) (kmax - kmin) u_e^T K0 u_e, with
 // u_e^T K0 u_e = sum_{a<b} (-K0[a][b]) (u_a - u_b)^2 (rows of K0 sum to zero).
-__global__ void k_sens(Geom g, const double* __restrict__ u, const double* __restrict__ x, double p, double kmin,
+template <class X>
+__global__ void k_sens(Geom g, const double* __restrict__ u, const X* __restrict__ x, double p, double kmin,
                        double kmax, double* __restrict__ dc) {
   const long long M = (long long)g.Nx * g.Ny * g.Nz;
   for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < M; e += (long long)gridDim.x * blockDim.x) {
@@ -517,16 +528,21 @@ __global__ void k_sens(Geom g, const double* __restrict__ u, const double* __res
         const double d = ue[a] - ue[b];
         E -= g.c[a ^ b] * d * d;
       }
-    const double xe = x[e];
+    const double xe = (double)x[e];
     const double dk = p * ((p == 1.0) ? 1.0 : pow(xe, p - 1.0)) * (kmax - kmin);
     dc[e] = -dk * E;
   }
 }
-cudaError_t sensitivity(const Geom& g, const double* upad, const double* x, double p, double kmin, double kmax,
+template <class X>
+cudaError_t sensitivity(const Geom& g, const double* upad, const X* x, double p, double kmin, double kmax,
                         double* dc, cudaStream_t st) {
-  note_launch(), k_sens<<<grid1((long long)g.Nx * g.Ny * g.Nz), 256, 0, st>>>(g, upad, x, p, kmin, kmax, dc);
+  note_launch(), k_sens<X><<<grid1((long long)g.Nx * g.Ny * g.Nz), 256, 0, st>>>(g, upad, x, p, kmin, kmax, dc);
   return cudaGetLastError();
 }
+template cudaError_t sensitivity<double>(const Geom&, const double*, const double*, double, double, double, double*,
+                                         cudaStream_t);
+template cudaError_t sensitivity<float>(const Geom&, const double*, const float*, double, double, double, double*,
+                                        cudaStream_t);
 
 // ---------------------------------------------------------------------------
 // SIMP harness: hat-weight density filter and OC candidate (not in the paper)
@@ -650,8 +666,10 @@ cudaError_t vec_to_f64(const Geom& g, const void* src, int kind, double* dst, cu
   return cudaGetLastError();
 }
 
-// u_i += sum_j Phi_ij ec[B(i)][j]  (FP64 prolongation from level 1)
-__global__ void k_prolong_add(Geom g, const double* __restrict__ phi, int L, const double* __restrict__ ec,
+// u_i += sum_j Phi_ij ec[B(i)][j]  (prolongation from level 1 into an FP64 vector;
+// Phi and ec stored as C, FP64 sums)
+template <class C>
+__global__ void k_prolong_add(Geom g, const C* __restrict__ phi, int L, const C* __restrict__ ec,
                               double* __restrict__ u) {
   const long long n = (long long)g.nx * g.ny * g.nz;
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
@@ -661,14 +679,17 @@ __global__ void k_prolong_add(Geom g, const double* __restrict__ phi, int L, con
     const long long nd = nidx(g, x, y, z);
     const long long cell = blk_of(x, g.b, g.nbx) + (long long)g.nbx * (blk_of(y, g.b, g.nby) + (long long)g.nby * blk_of(z, g.b, g.nbz));
     double s = 0.0;
-    for (int a = 0; a < L; ++a) s += phi[nd * L + a] * ec[cell * L + a];
+    for (int a = 0; a < L; ++a) s += (double)phi[nd * L + a] * (double)ec[cell * L + a];
     u[nd] += s;
   }
 }
-cudaError_t fine_prolong_add(const Geom& g, const double* phi, int L1, const double* ec, double* u, cudaStream_t st) {
-  note_launch(), k_prolong_add<<<grid1((long long)g.nx * g.ny * g.nz), 256, 0, st>>>(g, phi, L1, ec, u);
+template <class C>
+cudaError_t fine_prolong_add(const Geom& g, const C* phi, int L1, const C* ec, double* u, cudaStream_t st) {
+  note_launch(), k_prolong_add<C><<<grid1((long long)g.nx * g.ny * g.nz), 256, 0, st>>>(g, phi, L1, ec, u);
   return cudaGetLastError();
 }
+template cudaError_t fine_prolong_add<double>(const Geom&, const double*, int, const double*, double*, cudaStream_t);
+template cudaError_t fine_prolong_add<float>(const Geom&, const float*, int, const float*, double*, cudaStream_t);
 
 // v = 0 on Dirichlet nodes (padded FP64)
 __global__ void k_mask_dir(Geom g, const uint32_t* __restrict__ bits, double* __restrict__ v) {

@@ -32,7 +32,8 @@ EXPORTED = ["thermo_default_options", "thermo_create", "thermo_set_density", "th
             "thermo_hierarchy", "thermo_export_level", "thermo_filter", "thermo_oc_update",
             "thermo_launch_count", "thermo_bench_kernel", "thermo_apply_dot",
             "thermo_kernel_timers", "thermo_kernel_time", "thermo_dot_noalloc", "thermo_residual_history",
-            "thermo_set_stage_wait", "thermo_dense_spd_inverse", "thermo_update_density"]
+            "thermo_set_stage_wait", "thermo_dense_spd_inverse", "thermo_update_density",
+            "thermo_plan_bytes"]
 
 
 class thermo_options(C.Structure):
@@ -43,7 +44,7 @@ class thermo_options(C.Structure):
                 ("smoother", C.c_int), ("cheb_degree", C.c_int), ("cheb_ratio", C.c_double),
                 ("power_iters", C.c_int), ("outer_apply", C.c_int),
                 ("nu_growth", C.c_int), ("w_from", C.c_int), ("restart_decades", C.c_double),
-                ("density_fp32", C.c_int), ("fine_engine", C.c_int)]
+                ("density_fp32", C.c_int), ("fine_engine", C.c_int), ("lean", C.c_int)]
 
 
 class thermo_solve_info(C.Structure):
@@ -119,6 +120,37 @@ def default_options(grid) -> thermo_options:
     return o
 
 
+def options(grid, **opts) -> thermo_options:
+    """thermo_default_options(grid) with keyword overrides (nvec: list per
+    level; group: list of sizes for levels 2..levels; other fields by name)."""
+    o = default_options(grid)
+    for k, v in opts.items():
+        if k == "nvec":
+            for j in range(MAX_LEVELS):
+                o.nvec[j] = int(v[j]) if j < len(v) else 0
+        elif k == "group":  # sizes for levels 2..levels
+            o.group[0] = 0
+            for j in range(1, MAX_LEVELS):
+                o.group[j] = int(v[j - 1]) if j - 1 < len(v) else 0
+        else:
+            if not hasattr(o, k):
+                raise AttributeError(f"unknown option {k}")
+            setattr(o, k, v)
+    return o
+
+
+def plan_bytes(grid, has_dirichlet_value=False, **opts) -> int:
+    """Device bytes a context for this grid and these options would allocate
+    (thermo_plan_bytes: the allocation plan run without a GPU)."""
+    o = options(grid, **opts)
+    g = (C.c_int * 3)(*[int(v) for v in grid])
+    n = C.c_longlong(0)
+    st = lib().thermo_plan_bytes(g, C.byref(o), int(bool(has_dirichlet_value)), C.byref(n))
+    if st != OK:
+        raise ThermoError(st, f"thermo_plan_bytes rejected grid {tuple(grid)} / options")
+    return int(n.value)
+
+
 def _ptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else None
 
@@ -142,32 +174,25 @@ class Solver:
 
     def __init__(self, grid, h, mask, source, dirichlet_value=None, stream=None, **opts):
         self.grid = tuple(int(v) for v in grid)
-        o = default_options(self.grid)
-        for k, v in opts.items():
-            if k == "nvec":
-                for j in range(MAX_LEVELS):
-                    o.nvec[j] = int(v[j]) if j < len(v) else 0
-            elif k == "group":  # sizes for levels 2..levels
-                o.group[0] = 0
-                for j in range(1, MAX_LEVELS):
-                    o.group[j] = int(v[j - 1]) if j - 1 < len(v) else 0
-            else:
-                setattr(o, k, v)
+        o = options(self.grid, **opts)
         self.options = o
         self.nnode = (self.grid[0] + 1) * (self.grid[1] + 1) * (self.grid[2] + 1)
         self.nelem = self.grid[0] * self.grid[1] * self.grid[2]
-        self.mask = _dev(mask, torch.uint8)
-        self.source = _dev(source, torch.float64)
-        self.dval = None if dirichlet_value is None else _dev(dirichlet_value, torch.float64)
-        if self.mask.numel() != self.nnode or self.source.numel() != self.nelem:
+        mask = _dev(mask, torch.uint8)
+        source = _dev(source, torch.float64)
+        dval = None if dirichlet_value is None else _dev(dirichlet_value, torch.float64)
+        if mask.numel() != self.nnode or source.numel() != self.nelem:
             raise ValueError("mask / source sizes do not match the grid")
         self.stream = stream if stream is not None else torch.cuda.current_stream()
         self._x = None
         ctx = C.c_void_p()
         g = (C.c_int * 3)(*self.grid)
         hh = (C.c_double * 3)(*[float(v) for v in h])
-        st = lib().thermo_create(g, hh, _ptr(self.mask), _ptr(self.dval), _ptr(self.source),
+        st = lib().thermo_create(g, hh, _ptr(mask), _ptr(dval), _ptr(source),
                                  C.c_void_p(self.stream.cuda_stream), C.byref(o), C.byref(ctx))
+        # the context keeps its own copies: the inputs are not retained
+        self.stream.synchronize()
+        del mask, source, dval
         self.ctx = ctx
         if st != OK:
             msg = self.last_error()

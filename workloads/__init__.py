@@ -131,7 +131,7 @@ def smooth_random_density(N: int, seed: int, lo: float = 0.05,
 
 
 def channel_tree_density(N: int, seed: int, volfrac: float,
-                         trunk_height: float = 0.6) -> np.ndarray:
+                         trunk_height: float = 0.6, dtype=np.float64) -> np.ndarray:
     """Binary tree of axis-aligned square tubes rooted at the heat sink.
 
     The trunk runs along z from the patch centre (x = y = 1/2) up to
@@ -140,7 +140,8 @@ def channel_tree_density(N: int, seed: int, volfrac: float,
     different from its parent's, in a seeded direction, with length
     U[0.1, 0.5] (domain units), clipped to the domain.  Tubes are added until
     the volume reaches round(volfrac * M); the last tube is trimmed in raster
-    order to hit that count exactly.
+    order to hit that count exactly.  ``dtype`` is the returned array's type
+    (the values are 0 and 1 in any type).
     """
     M = N ** 3
     target = int(np.floor(volfrac * M + 0.5))
@@ -198,7 +199,7 @@ def channel_tree_density(N: int, seed: int, volfrac: float,
         t = (ax, tuple(lo), tuple(hi))
         tubes.append(t)
         vol += paint(t, target - vol)
-    return x.reshape(-1).astype(np.float64)
+    return x.reshape(-1).astype(dtype)
 
 
 def uniform01_at(seed: int, i: int) -> float:
@@ -234,6 +235,10 @@ def problem(name: str) -> dict:
     * ``chan256_1e3|1e6|1e9``: 256^3, channel tree (V=0.2, seed 3).
     * ``smoothNN``: NN^3 continuous density in [0.05, 1] (seed 7), kmin=1e-3.
     * ``chanNN``: NN^3 channel tree (V=0.2, seed 3), kmin=1e-6.
+    * ``chanNNvFF``: NN^3 channel tree at volume fraction FF/100 (seed 5),
+      kmin=1e-6; the design as float32 and no source array (``source`` is
+      None: q = 1 everywhere, for callers that fill it on the device).  The
+      large configuration is ``chan1024v10``.
     All use q = 1 and T = 0 on the centred 0.2 x 0.2 patch of z = 0.
     """
     if name == "cube32":
@@ -252,6 +257,13 @@ def problem(name: str) -> dict:
     elif name.startswith("smooth"):
         N = int(name[len("smooth"):])
         x, kmin = smooth_random_density(N, 7), 1e-3
+    elif name.startswith("chan") and "v" in name:
+        N, vf = name[len("chan"):].split("v")
+        N = int(N)
+        grid = (N, N, N)
+        x = channel_tree_density(N, 5, int(vf) / 100.0, dtype=np.float32)
+        return dict(name=name, grid=grid, h=(1.0 / N,) * 3, mask=dirichlet_patch_mask(grid), source=None,
+                    x=x, p=3.0, kmin=1e-6, kmax=1.0)
     elif name.startswith("chan"):
         N = int(name[len("chan"):])
         x, kmin = channel_tree_density(N, 3, 0.2), 1e-6
