@@ -169,6 +169,41 @@ def operator_rows(grid, h, kappa, mask, u, rows, absolute=False, chunk=1 << 21) 
     return out
 
 
+def load_rows(grid, h, source, rows) -> np.ndarray:
+    """f_i of load_vector on the listed nodes only, summed over the (up to) eight
+    elements that contain node i; for spot checks of grids too large for f."""
+    Nx, Ny, Nz = grid
+    nx, ny = Nx + 1, Ny + 1
+    vol = float(h[0]) * float(h[1]) * float(h[2])
+    src = np.asarray(source, dtype=np.float64)
+    r = np.asarray(rows, dtype=np.int64).reshape(-1)
+    ix, iy, iz = r % nx, (r // nx) % ny, r // (nx * ny)
+    out = np.zeros(r.size)
+    for a in range(8):
+        ex, ey, ez = ix - (a & 1), iy - ((a >> 1) & 1), iz - (a >> 2)
+        ok = (ex >= 0) & (ey >= 0) & (ez >= 0) & (ex < Nx) & (ey < Ny) & (ez < Nz)
+        e = np.where(ok, ex + Nx * (ey + Ny * ez), 0)
+        out += np.where(ok, src[e] * vol / 8.0, 0.0) if src.ndim else np.where(ok, float(src) * vol / 8.0, 0.0)
+    return out
+
+
+def sensitivity_at(grid, h, x_e, p, kmin, kmax, u, elems) -> np.ndarray:
+    """sensitivity() on the listed elements only: x_e are those elements'
+    densities, u the whole nodal solution; for spot checks of large grids."""
+    Nx, Ny, _ = grid
+    nx, ny = Nx + 1, Ny + 1
+    K0 = element_matrix(h)
+    e = np.asarray(elems, dtype=np.int64).reshape(-1)
+    ex, ey, ez = e % Nx, (e // Nx) % Ny, e // (Nx * Ny)
+    base = ex + nx * (ey + ny * ez)
+    ue = np.empty((e.size, 8))
+    for a in range(8):
+        ue[:, a] = np.asarray(u, float)[base + (a & 1) + nx * (((a >> 1) & 1) + ny * (a >> 2))]
+    E = np.einsum("ea,ab,eb->e", ue, K0, ue)
+    x = np.asarray(x_e, float)
+    return -p * x ** (p - 1.0) * (kmax - kmin) * E
+
+
 def compliance(f, u) -> float:
     """c = f^T u; for q = 1 on the unit cube this equals int u_h dV, the mean
     temperature of Sec. 2.3 Eq. (6) (sum_i phi_i = 1)."""

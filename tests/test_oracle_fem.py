@@ -229,3 +229,26 @@ def test_row_evaluator_equals_assembled_operator(grid, h):
     np.testing.assert_allclose(ya, scale, rtol=1e-14, atol=0)
     sub = np.array([0, n - 1, n // 2, 17])
     np.testing.assert_array_equal(fem.operator_rows(grid, h, P["kappa"], mask, u, sub), y[sub])
+
+
+@pytest.mark.parametrize("grid,h", [((8, 8, 8), (1 / 8,) * 3), ((6, 4, 5), (0.3, 0.5, 0.7))])
+def test_sampled_load_and_sensitivity_equal_the_full_ones(grid, h):
+    """The listed-nodes load (load_rows) and listed-elements sensitivity
+    (sensitivity_at), used for spot checks of grids too large for whole
+    vectors, equal load_vector (pinned by the integral of the source above)
+    and sensitivity (pinned by the Euler identity and central differences)
+    on every node and element, for a varying source and a scalar one."""
+    M = grid[0] * grid[1] * grid[2]
+    n = fem.n_nodes(grid)
+    q = W.uniform01(43, M) + 0.5
+    f = fem.load_vector(grid, h, q)
+    np.testing.assert_allclose(fem.load_rows(grid, h, q, np.arange(n)), f, rtol=1e-15, atol=0)
+    np.testing.assert_allclose(fem.load_rows(grid, h, 1.0, np.arange(n)),
+                               fem.load_vector(grid, h, np.ones(M)), rtol=1e-15, atol=0)
+    x = W.uniform01(44, M)
+    u = W.uniform01(45, n) - 0.3
+    dc = fem.sensitivity(grid, h, x, 3.0, 1e-3, 1.0, u)
+    e = np.array([0, M - 1, M // 2, 5, 5])
+    np.testing.assert_allclose(fem.sensitivity_at(grid, h, x[e], 3.0, 1e-3, 1.0, u, e), dc[e], rtol=1e-13, atol=0)
+    np.testing.assert_allclose(fem.sensitivity_at(grid, h, x, 3.0, 1e-3, 1.0, u, np.arange(M)), dc,
+                               rtol=1e-13, atol=1e-300)
