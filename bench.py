@@ -289,6 +289,70 @@ def run_topopt(args, pr, mask_d, q_d):
     return 0
 
 
+def run_multires(args):
+    """SIMP / OC across resolutions with the interpolation technique of Sec. 3
+    (Sec. 4.1: 128^3 -> 256^3 -> 512^3): stage k runs its design iterations on
+    an N_k^3 grid; the next stage starts from the design carried by trilinear
+    interpolation between cell centres (thermo_resample kind 1) and from the
+    solution carried as the same Q1 function (kind 2, warm start).  Same
+    harness as --topopt (filter radius 1.5 elements of each grid, V = 0.3,
+    q = 1, T = 0 on the centred patch).  For every stage after the first, the
+    first solve is also run from the coarse guess alone, so that the carried
+    warm start's iteration saving is measured."""
+    import torch
+    import __graft_entry__ as ge
+    ge.build()
+    import workloads as W
+    from paper_2410_06850_gb300 import Solver, thermo
+
+    stages = [tuple(int(v) for v in t.split(":")) for t in args.multires.split(",")]
+    p, kmin, kmax, rmin, vf = 3.0, 1e-3, 1.0, 1.5, 0.3
+    x = u = None
+    prev = None
+    out = {"mode": "multires", "stages": [], "filter_rmin": rmin, "volfrac": vf, "kmin": kmin}
+    t_all = time.perf_counter()
+    for N, iters in stages:
+        grid = (N, N, N)
+        M = N ** 3
+        mask_d = torch.as_tensor(W.dirichlet_patch_mask(grid)).cuda()
+        q_d = torch.ones(M, dtype=torch.float64, device="cuda")
+        s = Solver(grid, (1.0 / N,) * 3, mask_d, q_d, prec=thermo.MIXED, guess=3)
+        rec = {"N": N, "design_iterations": iters, "history": []}
+        if prev is None:
+            x = torch.full((M,), vf, dtype=torch.float64, device="cuda")
+            u = torch.zeros(s.nnode, dtype=torch.float64, device="cuda")
+        else:
+            x = thermo.resample(prev, x, grid, 1)
+            u = thermo.resample(prev, u, grid, 2)
+        dv = s.filter(torch.ones(M, dtype=torch.float64, device="cuda"), rmin, transpose=True)
+        t_stage = time.perf_counter()
+        for it in range(iters):
+            t0 = time.perf_counter()
+            xp = s.filter(x, rmin)
+            s.set_density(xp, p, kmin, kmax)
+            s.setup_precond()
+            if it == 0 and prev is not None:
+                # the warm coarse guess from u = 0 is the coarse guess alone: the comparison
+                _, cold = s.solve(u=torch.zeros_like(u), tol=args.tol)
+                rec["first_solve_iters_coarse_guess_only"] = cold["iters"]
+            u, info = s.solve(u=u, tol=args.tol)
+            c = s.compliance(u)
+            dc = s.filter(s.sensitivity(u), rmin, transpose=True)
+            change = s.oc_update(x, dc, dv, vf, 0.2, rmin)
+            torch.cuda.synchronize()
+            if it == 0 and prev is not None:
+                rec["first_solve_iters_carried_warm_start"] = info["iters"]
+            rec["history"].append({"it": it, "compliance": c, "iters": info["iters"], "change": change,
+                                   "step_s": time.perf_counter() - t0})
+        rec["stage_s"] = time.perf_counter() - t_stage
+        out["stages"].append(rec)
+        prev = grid
+        s.close()
+    out["total_s"] = time.perf_counter() - t_all
+    print(json.dumps(out))
+    return 0
+
+
 def fd_check(s, xp, u, p, kmin, kmax, count, seed=4, rel_step=1e-4, tol=1e-10):
     """Central finite differences of the compliance c = f^T u on `count` seeded
     elements (partial Fisher-Yates draw, stream `seed`), against the adjoint
@@ -522,6 +586,8 @@ def main():
     ap.add_argument("--kernels-only", action="store_true", help="only time the kernels and one solve per form")
     ap.add_argument("--fd-check", type=int, default=0,
                     help="with --topopt: central finite differences on N seeded elements of the final design")
+    ap.add_argument("--multires", default="",
+                    help="SIMP/OC across resolutions, e.g. 128:40,256:20 (N:design iterations per stage)")
     ap.add_argument("--large", type=int, default=0,
                     help="the large configuration at N^3 (1024: the full size) in the lean form; one JSON line")
     ap.add_argument("--compare", action="store_true",
@@ -535,6 +601,8 @@ def main():
         return run_reference(args, rank, world)
     if args.large:
         return run_large(args)
+    if args.multires:
+        return run_multires(args)
 
     import torch
     import __graft_entry__ as ge

@@ -361,6 +361,27 @@ thermo_status thermo_hierarchy(const thermo_ctx *ctx, int *nlevels, int *cells,
 thermo_status thermo_export_level(thermo_ctx *ctx, int level, int what,
                                   double *out, long long count);
 
+/* Resolution change of a field between two grids of the same box (the
+ * interpolation technique of Sec. 3: a design optimised at low resolution is
+ * carried to the next resolution as its start, 128^3 -> 256^3 -> 512^3 in
+ * Sec. 4.1; the solution can be carried alongside as a warm start).
+ *   grid_c, grid_f  host int[3]; grid_f[k] = r_k grid_c[k], integer r_k >= 1
+ *   in              device double[]: the coarse field (x fastest)
+ *   out             device double[]: the fine field (in != out)
+ *   kind 0          element field, piecewise constant (each coarse element's
+ *                   value on its r_x r_y r_z children; mean preserved)
+ *   kind 1          element field, trilinear between cell centres (fine centre
+ *                   at (i + 1/2)/r - 1/2 in coarse-centre units), constant beyond
+ *                   the outermost centres; stays within the input's range
+ *   kind 2          nodal field (grid + 1 values per axis): the coarse trilinear
+ *                   (Q1) function evaluated at the fine nodes
+ * Products and sums are rounded separately, x then y then z.  Needs no
+ * context; enqueued on `stream`.  EINVAL for non-integer ratios, kind out of
+ * range or in == out; ECUDA if the launch fails. */
+thermo_status thermo_resample(const int grid_c[3], const double *in,
+                              const int grid_f[3], double *out, int kind,
+                              void *stream);
+
 /* Density filter (textbook SIMP harness, not in the paper):
  * out_e = sum_j w_ej in_j / sum_j w_ej with w_ej = max(0, rmin - |c_e - c_j|)
  * in element units, truncated at the domain boundary; transpose = 1 applies

@@ -61,3 +61,76 @@ def oc_update(x, dc, dv, volfrac, H=None, move=0.2, eta=0.5,
         else:
             l2 = lmid
     return xn
+
+
+def _axis_weights_cells(N: int, r: int):
+    """Per fine cell i of an axis refined r times: the coarse cells i0, i1 and the
+    weight t of i1 for linear interpolation between coarse cell centres (fine
+    centre at (i + 1/2)/r - 1/2 in coarse-centre units), constant beyond the
+    outer centres."""
+    i = np.arange(N * r)
+    s = (i + 0.5) / r - 0.5
+    i0 = np.floor(s).astype(np.int64)
+    t = s - i0
+    lo = i0 < 0
+    hi = i0 >= N - 1
+    i0 = np.where(lo, 0, np.where(hi, N - 1, i0))
+    t = np.where(lo | hi, 0.0, t)
+    i1 = np.minimum(i0 + 1, N - 1)
+    return i0, i1, t
+
+
+def _axis_weights_nodes(N: int, r: int):
+    """Per fine node i (0..rN) of an axis: coarse nodes i0, i0 + 1 and the weight
+    t of i0 + 1 (fine node at coarse coordinate i / r)."""
+    i = np.arange(N * r + 1)
+    i0 = np.minimum(i // r, N - 1)
+    t = i / r - i0
+    return i0, i0 + 1, t
+
+
+def resample(grid_c, v, grid_f, kind: int) -> np.ndarray:
+    """Carry a field from grid_c to grid_f = r * grid_c (integer r >= 1 per axis):
+    the resolution change of the interpolation technique of Sec. 3 (a design
+    optimised at low resolution becomes the start of the high-resolution run;
+    Sec. 4.1 goes 128^3 -> 256^3 -> 512^3).  The paper does not state the
+    interpolant; three are defined here:
+
+    kind 0: element field, piecewise constant (each coarse element's value on its
+            r^3 children; the mean is preserved exactly);
+    kind 1: element field, trilinear between coarse cell centres, constant beyond
+            the outermost centres (values stay in the range of the input);
+    kind 2: nodal field, the coarse trilinear (Q1) function evaluated at the fine
+            nodes (an exact embedding of the coarse finite-element space).
+    Flat x-fastest arrays in the workloads' layout; FP64."""
+    Nc = [int(g) for g in grid_c]
+    Nf = [int(g) for g in grid_f]
+    r = [f // c for f, c in zip(Nf, Nc)]
+    if any(f != c * q or q < 1 for f, c, q in zip(Nf, Nc, r)):
+        raise ValueError("grid_f must be an integer multiple of grid_c per axis")
+    v = np.asarray(v, dtype=np.float64)
+    if kind == 0:
+        a = v.reshape(Nc[2], Nc[1], Nc[0])
+        return np.repeat(np.repeat(np.repeat(a, r[2], axis=0), r[1], axis=1), r[0], axis=2).reshape(-1)
+    if kind == 1:
+        w = [_axis_weights_cells(Nc[k], r[k]) for k in range(3)]
+        a = v.reshape(Nc[2], Nc[1], Nc[0])
+    elif kind == 2:
+        w = [_axis_weights_nodes(Nc[k], r[k]) for k in range(3)]
+        a = v.reshape(Nc[2] + 1, Nc[1] + 1, Nc[0] + 1)
+    else:
+        raise ValueError("kind must be 0, 1 or 2")
+    (x0, x1, tx), (y0, y1, ty), (z0, z1, tz) = w
+    tx, ty, tz = tx[None, None, :], ty[None, :, None], tz[:, None, None]
+
+    def at(zi, yi, xi):
+        return a[np.ix_(zi, yi, xi)]
+
+    # nested linear interpolation: x, then y, then z
+    c00 = at(z0, y0, x0) * (1.0 - tx) + at(z0, y0, x1) * tx
+    c10 = at(z0, y1, x0) * (1.0 - tx) + at(z0, y1, x1) * tx
+    c01 = at(z1, y0, x0) * (1.0 - tx) + at(z1, y0, x1) * tx
+    c11 = at(z1, y1, x0) * (1.0 - tx) + at(z1, y1, x1) * tx
+    c0 = c00 * (1.0 - ty) + c10 * ty
+    c1 = c01 * (1.0 - ty) + c11 * ty
+    return (c0 * (1.0 - tz) + c1 * tz).reshape(-1)

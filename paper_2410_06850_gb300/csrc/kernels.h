@@ -101,6 +101,8 @@ cudaError_t vec_axpy_pad(const Geom& g, double a, const double* x, double* y, cu
 template <class X>
 cudaError_t sensitivity(const Geom& g, const double* upad, const X* x, double p, double kmin, double kmax,
                         double* dc, cudaStream_t st);
+cudaError_t resample_field(const int gc[3], const double* in, const int gf[3], double* out, int kind,
+                           cudaStream_t st);
 cudaError_t density_filter(int Nx, int Ny, int Nz, const double* in, double* out, double rmin, int transpose,
                            cudaStream_t st);
 cudaError_t oc_candidate(long long M, const double* x, const double* dc, const double* dv, const double* colsum,

@@ -1397,6 +1397,18 @@ extern "C" thermo_status thermo_export_level(thermo_ctx* ctx, int level, int wha
   return THERMO_OK;
 }
 
+extern "C" thermo_status thermo_resample(const int grid_c[3], const double* in, const int grid_f[3], double* out,
+                                         int kind, void* stream) {
+  if (!grid_c || !grid_f || !in || !out || in == out) return THERMO_EINVAL;
+  if (kind < 0 || kind > 2) return THERMO_EINVAL;
+  for (int k = 0; k < 3; ++k) {
+    if (grid_c[k] < 1 || grid_f[k] < grid_c[k] || grid_f[k] % grid_c[k]) return THERMO_EINVAL;
+    if (grid_f[k] > (1 << 20)) return THERMO_EINVAL;
+  }
+  const cudaError_t e = resample_field(grid_c, in, grid_f, out, kind, (cudaStream_t)stream);
+  return e == cudaSuccess ? THERMO_OK : THERMO_ECUDA;
+}
+
 extern "C" thermo_status thermo_filter(thermo_ctx* ctx, const double* in, double* out, double rmin, int transpose) {
   if (!ctx) return THERMO_EINVAL;
   if (!in || !out || in == out || !(rmin > 0.0)) return fail(ctx, THERMO_EINVAL, "bad filter arguments");

@@ -584,6 +584,76 @@ __global__ void k_filter(int Nx, int Ny, int Nz, const double* __restrict__ in, 
     out[e] = transpose ? s : s / ws;
   }
 }
+// ---------------------------------------------------------------------------
+// Resolution change of a field (Sec. 3 interpolation technique: a design, or a
+// solution, carried from an N^3 run to an (rN)^3 one).  kind 0: element field,
+// piecewise constant; 1: element field, trilinear between cell centres (fine
+// centre at (i + 1/2)/r - 1/2 in coarse-centre units), constant beyond the
+// outermost centres; 2: nodal field, the coarse trilinear function at the fine
+// nodes.  Products and sums are rounded one by one (no fused multiply-add) in
+// the order x, y, z, so that the result does not depend on contraction.
+struct RsAxis {
+  int i0, i1;
+  double t;
+};
+__device__ __forceinline__ RsAxis rs_axis(int i, int N, int r, int kind) {
+  RsAxis a;
+  if (kind == 1) {
+    const double s = __dsub_rn(__ddiv_rn((double)i + 0.5, (double)r), 0.5);
+    int k = (int)floor(s);
+    double t = __dsub_rn(s, (double)k);
+    if (k < 0) {
+      k = 0;
+      t = 0.0;
+    } else if (k >= N - 1) {
+      k = N - 1;
+      t = 0.0;
+    }
+    a.i0 = k;
+    a.i1 = k + 1 < N ? k + 1 : N - 1;
+    a.t = t;
+  } else {  // nodal
+    int k = i / r;
+    if (k > N - 1) k = N - 1;
+    a.i0 = k;
+    a.i1 = k + 1;
+    a.t = __dsub_rn(__ddiv_rn((double)i, (double)r), (double)k);
+  }
+  return a;
+}
+__device__ __forceinline__ double rs_lerp(double a, double b, double t) {
+  return __dadd_rn(__dmul_rn(a, __dsub_rn(1.0, t)), __dmul_rn(b, t));
+}
+__global__ void k_resample(int3 nc, int3 nf, int3 r, int kind, const double* __restrict__ in, double* __restrict__ out) {
+  // nc / nf: extents of the coarse / fine arrays (elements, or nodes for kind 2)
+  const long long n = (long long)nf.x * nf.y * nf.z;
+  for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < n; o += (long long)gridDim.x * blockDim.x) {
+    const int ix = (int)(o % nf.x);
+    const long long t = o / nf.x;
+    const int iy = (int)(t % nf.y), iz = (int)(t / nf.y);
+    if (kind == 0) {
+      out[o] = in[(ix / r.x) + (long long)nc.x * ((iy / r.y) + (long long)nc.y * (iz / r.z))];
+      continue;
+    }
+    const int Nx = kind == 2 ? nc.x - 1 : nc.x, Ny = kind == 2 ? nc.y - 1 : nc.y, Nz = kind == 2 ? nc.z - 1 : nc.z;
+    const RsAxis ax = rs_axis(ix, Nx, r.x, kind), ay = rs_axis(iy, Ny, r.y, kind), az = rs_axis(iz, Nz, r.z, kind);
+    auto at = [&](int z, int y, int x) { return in[x + (long long)nc.x * (y + (long long)nc.y * z)]; };
+    const double c00 = rs_lerp(at(az.i0, ay.i0, ax.i0), at(az.i0, ay.i0, ax.i1), ax.t);
+    const double c10 = rs_lerp(at(az.i0, ay.i1, ax.i0), at(az.i0, ay.i1, ax.i1), ax.t);
+    const double c01 = rs_lerp(at(az.i1, ay.i0, ax.i0), at(az.i1, ay.i0, ax.i1), ax.t);
+    const double c11 = rs_lerp(at(az.i1, ay.i1, ax.i0), at(az.i1, ay.i1, ax.i1), ax.t);
+    out[o] = rs_lerp(rs_lerp(c00, c10, ay.t), rs_lerp(c01, c11, ay.t), az.t);
+  }
+}
+cudaError_t resample_field(const int gc[3], const double* in, const int gf[3], double* out, int kind, cudaStream_t st) {
+  const int e = kind == 2 ? 1 : 0;
+  const int3 nc = make_int3(gc[0] + e, gc[1] + e, gc[2] + e), nf = make_int3(gf[0] + e, gf[1] + e, gf[2] + e);
+  const int3 r = make_int3(gf[0] / gc[0], gf[1] / gc[1], gf[2] / gc[2]);
+  const long long n = (long long)nf.x * nf.y * nf.z;
+  note_launch(), k_resample<<<grid1(n), 256, 0, st>>>(nc, nf, r, kind, in, out);
+  return cudaGetLastError();
+}
+
 cudaError_t density_filter(int Nx, int Ny, int Nz, const double* in, double* out, double rmin, int transpose,
                            cudaStream_t st) {
   note_launch(), k_filter<<<grid1((long long)Nx * Ny * Nz), 256, 0, st>>>(Nx, Ny, Nz, in, out, rmin, transpose);

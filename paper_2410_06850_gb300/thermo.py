@@ -33,7 +33,7 @@ EXPORTED = ["thermo_default_options", "thermo_create", "thermo_set_density", "th
             "thermo_launch_count", "thermo_bench_kernel", "thermo_apply_dot",
             "thermo_kernel_timers", "thermo_kernel_time", "thermo_dot_noalloc", "thermo_residual_history",
             "thermo_set_stage_wait", "thermo_dense_spd_inverse", "thermo_update_density",
-            "thermo_plan_bytes"]
+            "thermo_plan_bytes", "thermo_resample"]
 
 
 class thermo_options(C.Structure):
@@ -370,6 +370,23 @@ def dense_spd_inverse(A):
     st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
     rc = lib().thermo_dense_spd_inverse(int(A.shape[0]), _ptr(A), _ptr(X), st, C.byref(piv), msg, 256)
     return X, rc, piv.value, msg.value.decode()
+
+
+def resample(grid_c, v, grid_f, kind):
+    """thermo_resample: carry a field from grid_c to grid_f = r * grid_c (kind 0:
+    element field, piecewise constant; 1: element field, trilinear between cell
+    centres; 2: nodal field, the coarse Q1 function at the fine nodes)."""
+    v = _dev(v, torch.float64)
+    e = 1 if kind == 2 else 0
+    n = (int(grid_f[0]) + e) * (int(grid_f[1]) + e) * (int(grid_f[2]) + e)
+    out = torch.empty(n, dtype=torch.float64, device="cuda")
+    gc = (C.c_int * 3)(*[int(g) for g in grid_c])
+    gf = (C.c_int * 3)(*[int(g) for g in grid_f])
+    st = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = lib().thermo_resample(gc, _ptr(v), gf, _ptr(out), int(kind), st)
+    if rc != OK:
+        raise ThermoError(rc, f"thermo_resample rejected {tuple(grid_c)} -> {tuple(grid_f)} kind {kind}")
+    return out
 
 
 def launch_count() -> int:
