@@ -138,6 +138,15 @@ typedef struct {
                                        memory of the CG and cycle vectors, which set-up
                                        does not use; the coarse initial guess runs the FP32
                                        chain.  Roughly halves the context's device memory. */
+  double eig_threshold;             /* 0 (default): every cell of level l keeps nvec[l-1]
+                                       local eigenvectors (the paper's fixed L_c, L_cc).
+                                       tau > 0: adaptive count (the GMsFEM-style
+                                       alternative): a cell keeps its eigenpairs with
+                                       lambda H_l^2 <= tau, at most nvec[l-1] (the slot
+                                       capacity), at least one; H_l = block max(h) times
+                                       the group sizes of levels 2..l; lambda of Eq. (8)
+                                       (kappa-mass generalised) or Eq. (9).  Unused slots
+                                       are inactive (identity rows in A_l). */
 } thermo_options;
 
 typedef struct {

@@ -65,6 +65,7 @@ class MMGOptions:
     cheb_degree: int = 5                # Chebyshev: matrix-vector products per smoothing
     cheb_ratio: float = 30.0            # interval [lmax / ratio, 1.1 lmax] of D^-1 A
     power_iters: int = 15               # power iterations for lmax(D^-1 A)
+    eig_threshold: float = 0.0          # > 0: adaptive basis count (see kept_count); 0: L_l per cell
 
     def __post_init__(self):
         self.nvec = tuple(int(v) for v in self.nvec)
@@ -181,6 +182,33 @@ def _mgs(V, W=None):
     return V
 
 
+def cell_size(prob, opts: MMGOptions, level: int) -> float:
+    """Edge H_l of a level-l cell: b max(h) on level 1, times g_2 ... g_l below."""
+    H = opts.block * max(prob["h"])
+    for g in opts.group[:level - 1]:
+        H *= g
+    return H
+
+
+def kept_count(w, L: int, thr: float) -> int:
+    """Adaptive local basis (the GMsFEM-style alternative to a fixed L): of the
+    ascending local eigenvalues w, keep those with w H^2 <= tau (thr = tau / H^2),
+    at most L (the cell's capacity) and at least one; thr <= 0 keeps
+    min(L, len(w)).  In a high-contrast cell the eigenvalues of the
+    kappa-weighted Neumann problem split into one near zero per high-conductivity
+    component (kappa_min / kappa_max times the cell scale) and the rest above
+    about pi^2 / H^2 (in the kappa-mass norm the constant is a combination of
+    the components' indicators), so a threshold between the two keeps one
+    vector per component."""
+    k = min(L, len(w))
+    if thr <= 0.0 or k == 0:
+        return k
+    c = 0
+    while c < k and w[c] <= thr:
+        c += 1
+    return max(c, 1)
+
+
 def level1_basis(prob, opts: MMGOptions):
     """Eq. (8) on every block: returns (P1 (n0 x n1), active, eigvals, blk)."""
     A = prob["A"].tocsr()
@@ -207,7 +235,7 @@ def level1_basis(prob, opts: MMGOptions):
         s = 1.0 / np.sqrt(m)
         C = At * s[:, None] * s[None, :]
         w, V = np.linalg.eigh(C)
-        k = min(L, n)
+        k = kept_count(w, L, opts.eig_threshold / cell_size(prob, opts, 1) ** 2)
         Phi = V[:, :k] * s[:, None]
         Phi = _mgs(Phi, m)                           # Phi^T M Phi = I
         for j in range(k):
@@ -232,11 +260,12 @@ def _galerkin(A, P, active):
 
 
 def coarse_level_basis(prob, Pcomp, fine_cell, prev_shape, prev_L, prev_active,
-                       g, L):
+                       g, L, thr=0.0):
     """Eq. (9) on every group of g^3 previous-level cells.
 
     fine_cell: previous-level cell id of each fine node (-1 for Dirichlet).
     Pcomp: composite prolongation fine <- previous level (n0 x n_prev).
+    thr: the adaptive basis threshold tau / H^2 of this level (kept_count).
     Returns (Psi (n_prev x n_new), active_new, eigvals, new fine_cell, shape).
     """
     A = prob["A"].tocsr()
@@ -278,7 +307,7 @@ def coarse_level_basis(prob, Pcomp, fine_cell, prev_shape, prev_L, prev_active,
         Ata = At[np.ix_(ia, ia)]
         Ata = 0.5 * (Ata + Ata.T)
         w, V = np.linalg.eigh(Ata)
-        k = min(L, ia.size)
+        k = kept_count(w, L, thr)
         Vk = _mgs(V[:, :k])
         for j in range(k):
             v = _sign_fix(Vk[:, j])
@@ -352,8 +381,9 @@ class MMG:
         for li, (g, L) in enumerate(zip(o.group, o.nvec[1:])):
             prev = self.levels[-1]
             if bases is None:
+                thr = o.eig_threshold / cell_size(prob, o, li + 2) ** 2
                 Psi, act, eig, fine_cell, shape = coarse_level_basis(
-                    prob, Pcomp, fine_cell, prev.shape, prev.L, prev.active, g, L)
+                    prob, Pcomp, fine_cell, prev.shape, prev.L, prev.active, g, L, thr)
             else:
                 shape = tuple(m // g for m in prev.shape)
                 Psi, act, eig, shape = _given_level(bases[li + 1], shape, L)

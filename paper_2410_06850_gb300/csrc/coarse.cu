@@ -9,6 +9,7 @@
 // (mixed form); accumulation is in T.
 #include "common.cuh"
 #include "kernels.h"
+#include "coarse_dev.cuh"
 
 namespace thermo {
 
@@ -90,17 +91,9 @@ __global__ void k_cresidual(CLevel lv, const T* __restrict__ tiles, const T* __r
 // e = Dinv r  (first l1-block-Jacobi sweep from zero)
 template <class T>
 __global__ void k_csmooth0(CLevel lv, const T* __restrict__ Dinv, const T* __restrict__ r, T* __restrict__ e) {
-  const int L = lv.L;
-  const long long nrow = lv.ncell * L;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nrow; t += (long long)gridDim.x * blockDim.x) {
-    const long long c = t / L;
-    const int i = (int)(t - c * L);
-    const T* D = Dinv + (c * L + i) * (long long)L;
-    const T* rv = r + c * L;
-    T s = T(0);
-    for (int j = 0; j < L; ++j) s += D[j] * rv[j];
-    e[t] = s;
-  }
+  const long long nrow = lv.ncell * lv.L;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nrow; t += (long long)gridDim.x * blockDim.x)
+    csmooth0_item<T>(lv, Dinv, r, e, t);
 }
 
 // out = e + Dinv (r - A e): cells_per_cta cells, L threads each
@@ -123,92 +116,22 @@ __global__ void k_csmooth(CLevel lv, const T* __restrict__ tiles, const T* __res
   }
 }
 
-// Levels with many vectors per cell (L >= 12): one CTA per cell.  The cell's
-// 27 tiles (contiguous, 27 L^2 values) are staged into shared memory with
-// coalesced loads by all threads, the 27 neighbour vectors gathered beside
-// them; thread (n, i) forms the partial row sum of tile n, then the rows are
-// summed over the 27 neighbours in fixed order (deterministic).
+// Levels with many vectors per cell (L >= 12): one CTA per cell (ccell_cell in
+// coarse_dev.cuh: the cell's 27 tiles staged into shared memory with 16-byte
+// copies, the 27 neighbour vectors gathered beside them, partial row sums
+// combined over the neighbours in fixed order).
 //   MODE 0: out = A x;  MODE 1: out = r - A x;  MODE 2: out = x + Dinv (r - A x)
 template <class T, int MODE>
 __global__ void k_ccell(CLevel lv, const T* __restrict__ tiles, const T* __restrict__ Dinv, const T* __restrict__ r,
                         const T* __restrict__ x, T* __restrict__ out) {
   extern __shared__ __align__(16) unsigned char sm_raw[];
-  const int L = lv.L;
-  const int LL = L * L;
-  constexpr int V = 16 / sizeof(T);      // elements per 16-byte chunk
-  const long long c = blockIdx.x;
-  // the cell's 27 tiles start at element c * 27 L^2, generally not on a 16-byte
-  // boundary: copy the aligned 16-byte chunks that cover them (the allocation
-  // has slack past its end) and index the tiles from the head offset
-  const long long e0 = c * 27 * (long long)LL;
-  const long long a0 = e0 & ~(long long)(V - 1);
-  const int head = (int)(e0 - a0);
-  const int nchunk = (int)((e0 + 27 * LL - a0 + V - 1) / V);
-  T* buf = reinterpret_cast<T*>(sm_raw);  // nchunk * V elements
-  T* ts = buf + head;                     // [27][L][L]
-  T* xs = buf + ((nchunk * V + V - 1) / V) * V;  // [27][L] (zero outside the grid)
-  T* part = xs + 27 * L;                 // [27][L]
-  T* res = part + 27 * L;                // [L]
-  const int cx = (int)(c % lv.mx);
-  const long long tt = c / lv.mx;
-  const int cy = (int)(tt % lv.my), cz = (int)(tt / lv.my);
-  // asynchronous 16-byte copies (all in flight at once), completed before the barrier
-  for (int k = threadIdx.x; k < nchunk; k += blockDim.x) {
-    const unsigned dst = (unsigned)__cvta_generic_to_shared(buf + (long long)k * V);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(tiles + a0 + (long long)k * V)
-                 : "memory");
-  }
-  asm volatile("cp.async.commit_group;\n" ::: "memory");
-  for (int k = threadIdx.x; k < 27 * L; k += blockDim.x) {
-    const int n = k / L, j = k - n * L;
-    const int nx = cx + n % 3 - 1, ny = cy + (n / 3) % 3 - 1, nz = cz + n / 9 - 1;
-    T v = T(0);
-    if (nx >= 0 && ny >= 0 && nz >= 0 && nx < lv.mx && ny < lv.my && nz < lv.mz)
-      v = x[(nx + (long long)lv.mx * (ny + (long long)lv.my * nz)) * L + j];
-    xs[k] = v;
-  }
-  asm volatile("cp.async.wait_group 0;\n" ::: "memory");
-  __syncthreads();
-  for (int idx = threadIdx.x; idx < 27 * L; idx += blockDim.x) {
-    const int n = idx / L;
-    const T* row = ts + (long long)idx * L;  // tile n, row i
-    const T* xv = xs + n * L;
-    T s = T(0), s2 = T(0);
-    int j = 0;
-    for (; j + 1 < L; j += 2) {
-      s = fma(row[j], xv[j], s);
-      s2 = fma(row[j + 1], xv[j + 1], s2);
-    }
-    if (j < L) s = fma(row[j], xv[j], s);
-    part[idx] = s + s2;
-  }
-  __syncthreads();
-  for (int i = threadIdx.x; i < L; i += blockDim.x) {
-    T s = T(0);
-    for (int n = 0; n < 27; ++n) s += part[n * L + i];
-    if (MODE == 0)
-      out[c * L + i] = s;
-    else if (MODE == 1)
-      out[c * L + i] = r[c * L + i] - s;
-    else
-      res[i] = r[c * L + i] - s;
-  }
-  if (MODE == 2) {
-    __syncthreads();
-    for (int i = threadIdx.x; i < L; i += blockDim.x) {
-      const T* D = Dinv + (c * L + i) * (long long)L;
-      T s = T(0);
-      for (int j = 0; j < L; ++j) s = fma(D[j], res[j], s);
-      out[c * L + i] = x[c * L + i] + s;
-    }
-  }
+  ccell_cell<T, MODE>(lv, tiles, Dinv, r, x, out, blockIdx.x, sm_raw);
 }
 template <class T, int MODE>
 static void launch_ccell(const CLevel& lv, const T* tiles, const T* Dinv, const T* r, const T* x, T* out,
                          cudaStream_t st) {
   const int nt = ((27 * lv.L + 31) / 32) * 32;
-  const size_t V = 16 / sizeof(T);
-  const size_t sm = ((size_t)27 * lv.L * lv.L + 2 * V + (size_t)55 * lv.L) * sizeof(T);
+  const size_t sm = ccell_smem_bytes<T>(lv.L);
   if (sm > 48 * 1024) cudaFuncSetAttribute(k_ccell<T, MODE>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
   note_launch(), k_ccell<T, MODE><<<(unsigned)lv.ncell, nt > 1024 ? 1024 : nt, sm, st>>>(lv, tiles, Dinv, r, x, out);
 }
@@ -218,26 +141,9 @@ constexpr int CCELL_MIN_L = 12;
 template <class T>
 __global__ void k_crestrict(CLevel f, CLevel cs, const T* __restrict__ Psi, const T* __restrict__ res,
                             T* __restrict__ rc) {
-  const int g = cs.g, Lf = f.L, Lc = cs.L;
-  const int nloc = g * g * g * Lf;
-  const long long nout = cs.ncell * Lc;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nout; t += (long long)gridDim.x * blockDim.x) {
-    const long long G = t / Lc;
-    const int k = (int)(t - G * Lc);
-    const int gx = (int)(G % cs.mx);
-    const long long tt = G / cs.mx;
-    const int gy = (int)(tt % cs.my), gz = (int)(tt / cs.my);
-    const T* ps = Psi + G * (long long)nloc * Lc;
-    T s = T(0);
-    for (int lz = 0; lz < g; ++lz)
-      for (int ly = 0; ly < g; ++ly)
-        for (int lx = 0; lx < g; ++lx) {
-          const long long c = (gx * g + lx) + (long long)f.mx * ((gy * g + ly) + (long long)f.my * (gz * g + lz));
-          const int lc = lx + g * (ly + g * lz);
-          for (int i = 0; i < Lf; ++i) s += ps[(long long)(lc * Lf + i) * Lc + k] * res[c * Lf + i];
-        }
-    rc[t] = s;
-  }
+  const long long nout = cs.ncell * cs.L;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nout; t += (long long)gridDim.x * blockDim.x)
+    crestrict_item<T>(f, cs, Psi, res, rc, t);
 }
 
 // The same restriction with Q = g^3 <= 32 threads per output (one per cell of
@@ -247,51 +153,16 @@ __global__ void k_crestrict(CLevel f, CLevel cs, const T* __restrict__ Psi, cons
 template <class T, int Q>
 __global__ void k_crestrict_q(CLevel f, CLevel cs, const T* __restrict__ Psi, const T* __restrict__ res,
                               T* __restrict__ rc) {
-  const int g = cs.g, Lf = f.L, Lc = cs.L;
-  const int nloc = g * g * g * Lf;
-  const long long nout = cs.ncell * Lc;
-  const long long gt = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  const int lc = (int)(gt % Q);
-  const long long t = gt / Q;
-  T s = T(0);
-  if (t < nout) {
-    const long long G = t / Lc;
-    const int k = (int)(t - G * Lc);
-    const int gx = (int)(G % cs.mx);
-    const long long tt = G / cs.mx;
-    const int gy = (int)(tt % cs.my), gz = (int)(tt / cs.my);
-    const int lx = lc % g, ly = (lc / g) % g, lz = lc / (g * g);
-    const long long c = (gx * g + lx) + (long long)f.mx * ((gy * g + ly) + (long long)f.my * (gz * g + lz));
-    const T* ps = Psi + G * (long long)nloc * Lc + (long long)lc * Lf * Lc + k;
-    const T* rv = res + c * Lf;
-    for (int i = 0; i < Lf; ++i) s = fma(ps[(long long)i * Lc], rv[i], s);
-  }
-#pragma unroll
-  for (int o = Q / 2; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if (t < nout && lc == 0) rc[t] = s;
+  crestrict_q_item<T, Q>(f, cs, Psi, res, rc, blockIdx.x * (long long)blockDim.x + threadIdx.x);
 }
 
 // e[c][i] += sum_k Psi[G(c)][lc*Lf + i][k] ec[G][k]
 template <class T>
 __global__ void k_cprolong(CLevel f, CLevel cs, const T* __restrict__ Psi, const T* __restrict__ ec,
                            T* __restrict__ e) {
-  const int g = cs.g, Lf = f.L, Lc = cs.L;
-  const int nloc = g * g * g * Lf;
-  const long long nrow = f.ncell * Lf;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nrow; t += (long long)gridDim.x * blockDim.x) {
-    const long long c = t / Lf;
-    const int i = (int)(t - c * Lf);
-    const int cx = (int)(c % f.mx);
-    const long long tt = c / f.mx;
-    const int cy = (int)(tt % f.my), cz = (int)(tt / f.my);
-    const long long G = (cx / g) + (long long)cs.mx * ((cy / g) + (long long)cs.my * (cz / g));
-    const int lc = (cx % g) + g * ((cy % g) + g * (cz % g));
-    const T* ps = Psi + G * (long long)nloc * Lc + (long long)(lc * Lf + i) * Lc;
-    const T* ev = ec + G * Lc;
-    T s = T(0);
-    for (int k = 0; k < Lc; ++k) s += ps[k] * ev[k];
-    e[t] += s;
-  }
+  const long long nrow = f.ncell * f.L;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < nrow; t += (long long)gridDim.x * blockDim.x)
+    cprolong_item<T>(f, cs, Psi, ec, e, t);
 }
 
 // y = Ainv x (coarsest solve by the precomputed FP64 inverse), one warp per row
@@ -304,11 +175,7 @@ __global__ void k_gemv(int n, const double* __restrict__ A, const T* __restrict_
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int row = blockIdx.x * (blockDim.x >> 5) + warp;
   if (row >= n) return;
-  const double* a = A + (long long)row * n;
-  double s = 0.0;
-  for (int j = lane; j < n; j += 32) s += a[j] * xs[j];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  if (lane == 0) y[row] = (T)s;
+  gemv_row<T>(n, A, xs, y, row, lane);
 }
 
 static int cgrid(long long n, int nt = 256) {

@@ -136,8 +136,9 @@ cudaError_t dense_gemv(int n, const double* Ainv, const T* x, T* y, cudaStream_t
 
 // ---- setup.cu
 struct SetupWork;
+// thr > 0: adaptive count of basis vectors per cell (eigenvalues <= thr kept, at least one)
 cudaError_t level1_eigen(const Geom& g, const uint32_t* bits, const double* k64, int L1, double* phi64,
-                         double* eig, uint8_t* active, int* status, cudaStream_t st);
+                         double* eig, uint8_t* active, int* status, double thr, cudaStream_t st);
 cudaError_t level1_rowsum_corr(const Geom& g, const uint32_t* bits, const double* k64, int L1,
                                const double* phi64, int nt, const int* gcum, double* D, cudaStream_t st);
 template <class TO>  // TO: stored tile type (double or float); sums in FP64
@@ -146,7 +147,7 @@ cudaError_t level1_rap(const Geom& g, const uint32_t* bits, const double* k64, i
 template <class TI>  // TI: stored type of the previous level's tiles
 cudaError_t group_eigen(const CLevel& prev, const CLevel& cur, const TI* tiles_prev, const double* Dcorr,
                         const uint8_t* act_prev, double* Psi, double* eig, uint8_t* act_cur, int* status,
-                        cudaStream_t st);
+                        double thr, cudaStream_t st);
 cudaError_t group_project_corr(const CLevel& prev, const CLevel& cur, const double* Psi, const double* Dprev,
                                double* Dcur, int nt, cudaStream_t st);
 template <class TI, class TO>  // (double, double), (float, float), (float, double)

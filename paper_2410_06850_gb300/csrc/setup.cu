@@ -142,6 +142,17 @@ __device__ void select_smallest(const T* A, int n2, int k, int* sel) {
   __syncthreads();
 }
 
+// Adaptive local basis (the GMsFEM-style alternative to a fixed L): of the k
+// ascending Ritz values lam, the count with lam <= thr (thr = tau / H^2 of the
+// level), at least one; thr <= 0 keeps k.  Every thread computes the same count
+// from shared memory.
+__device__ __forceinline__ int kept_count(const double* lam, int k, double thr) {
+  if (!(thr > 0.0) || k == 0) return k;
+  int c = 0;
+  while (c < k && lam[c] <= thr) ++c;
+  return c > 0 ? c : 1;
+}
+
 // Rayleigh-Ritz finish on an FP64 basis X[n][ld] (k columns, M-orthonormal):
 // H = X^T W (W = Ã X) is diagonalised (FP64 Jacobi), X <- X Y sorted by
 // eigenvalue, sign-fixed.  Scratch in shared memory.
@@ -328,7 +339,7 @@ __host__ __device__ inline L1Smem l1_smem(int n2, int K, int nmap) {
 __global__ void __launch_bounds__(EIG_NT) k_level1_eigen(Geom g, const uint32_t* __restrict__ bits,
                                                          const double* __restrict__ k64, int L, int lx, int ly, int lz,
                                                          int n2, double* __restrict__ phi, double* __restrict__ eig,
-                                                         uint8_t* __restrict__ act, int* status) {
+                                                         uint8_t* __restrict__ act, int* status, double thr) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int b = g.b;
   const int cxn = lx ? 1 : g.nbx - 1, cyn = ly ? 1 : g.nby - 1;
@@ -383,7 +394,7 @@ __global__ void __launch_bounds__(EIG_NT) k_level1_eigen(Geom g, const uint32_t*
   }
   __syncthreads();
   const int n = (int)sh[34];
-  const int kk = n < L ? n : L;
+  int kk = n < L ? n : L;
   const int K = n < Kmax ? n : Kmax;
   // mass, its inverse square root, and the couplings to the 26 neighbours (FP64, once)
   for (int i = tid; i < n; i += nt) {
@@ -443,7 +454,8 @@ __global__ void __launch_bounds__(EIG_NT) k_level1_eigen(Geom g, const uint32_t*
   __syncthreads();
   // Rayleigh-Ritz on span(X): sorted Ritz pairs in X, lam (W reused as scratch)
   if (K > 0) rr_finish(X, W, n, K, K, H, Yr, cs64, sn64, pp, qq, sh, W, lam, sel);
-  // outputs: the L lowest
+  kk = kept_count(lam, kk, thr);
+  // outputs: the L lowest (the adaptive count of them when thr > 0)
   for (int k = tid; k < nmap; k += nt) {
     const int x = X0 + k % wx, y = Y0 + (k / wx) % wy, z = Z0 + k / (wx * wy);
     const int i = lmap[k];
@@ -457,7 +469,7 @@ __global__ void __launch_bounds__(EIG_NT) k_level1_eigen(Geom g, const uint32_t*
 }
 
 cudaError_t level1_eigen(const Geom& g, const uint32_t* bits, const double* k64, int L1, double* phi64, double* eig,
-                         uint8_t* active, int* status, cudaStream_t st) {
+                         uint8_t* active, int* status, double thr, cudaStream_t st) {
   for (int lz = 0; lz < 2; ++lz)
     for (int ly = 0; ly < 2; ++ly)
       for (int lx = 0; lx < 2; ++lx) {
@@ -472,8 +484,8 @@ cudaError_t level1_eigen(const Geom& g, const uint32_t* bits, const double* k64,
         cudaError_t e = cudaFuncSetAttribute(k_level1_eigen, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)S.total);
         if (e != cudaSuccess) return e;
-        note_launch(), k_level1_eigen<<<(unsigned)nb, EIG_NT, S.total, st>>>(g, bits, k64, L1, lx, ly, lz, n2, phi64, eig, active,
-                                                               status);
+        note_launch(), k_level1_eigen<<<(unsigned)nb, EIG_NT, S.total, st>>>(g, bits, k64, L1, lx, ly, lz, n2, phi64,
+                                                                             eig, active, status, thr);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
       }
@@ -668,7 +680,7 @@ template <class TI>
 __global__ void __launch_bounds__(EIG_NT) k_group_eigen(CLevel prev, CLevel cur, const TI* __restrict__ Tp,
                                                         const double* __restrict__ Dc, const uint8_t* __restrict__ actp,
                                                         int n2, double* __restrict__ Psi, double* __restrict__ eig,
-                                                        uint8_t* __restrict__ actc) {
+                                                        uint8_t* __restrict__ actc, double thr) {
   extern __shared__ __align__(16) unsigned char sm[];
   const int g = cur.g, Lp = prev.L, L = cur.L, ng = g * g * g, n = ng * Lp;
   const int Kmax = (L + EIG_EXTRA) < n2 ? (L + EIG_EXTRA) : n2;
@@ -705,7 +717,7 @@ __global__ void __launch_bounds__(EIG_NT) k_group_eigen(CLevel prev, CLevel cur,
   }
   __syncthreads();
   const int na = (int)sh[34];
-  const int kk = na < L ? na : L;
+  int kk = na < L ? na : L;
   const int K = na < Kmax ? na : Kmax;
   // row ia of Ã_G, one neighbouring cell lcj per thread item: the tile row and the
   // correction row are located once, then the Lp entries are read in order
@@ -768,7 +780,8 @@ __global__ void __launch_bounds__(EIG_NT) k_group_eigen(CLevel prev, CLevel cur,
   }
   __syncthreads();
   if (K > 0) rr_finish(X, W, na, K, K, H, Yr, cs64, sn64, pp, qq, sh, W, lam, sel);
-  // Psi rows in local dof order (inactive rows zero), the L lowest columns
+  kk = kept_count(lam, kk, thr);
+  // Psi rows in local dof order (inactive rows zero), the L lowest columns (adaptive count when thr > 0)
   double* out = Psi + G * (long long)n * L;
   for (int w = tid; w < n * L; w += nt) out[w] = 0.0;
   __syncthreads();
@@ -783,7 +796,7 @@ __global__ void __launch_bounds__(EIG_NT) k_group_eigen(CLevel prev, CLevel cur,
 }
 template <class TI>
 cudaError_t group_eigen(const CLevel& prev, const CLevel& cur, const TI* tiles_prev, const double* Dcorr,
-                        const uint8_t* act_prev, double* Psi, double* eig, uint8_t* act_cur, int* status,
+                        const uint8_t* act_prev, double* Psi, double* eig, uint8_t* act_cur, int* status, double thr,
                         cudaStream_t st) {
   const int n = cur.g * cur.g * cur.g * prev.L;
   const int n2 = (n + 1) & ~1;
@@ -793,13 +806,13 @@ cudaError_t group_eigen(const CLevel& prev, const CLevel& cur, const TI* tiles_p
   cudaError_t e = cudaFuncSetAttribute(k_group_eigen<TI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)S.total);
   if (e != cudaSuccess) return e;
   note_launch(), k_group_eigen<TI><<<(unsigned)cur.ncell, EIG_NT, S.total, st>>>(prev, cur, tiles_prev, Dcorr, act_prev,
-                                                                                 n2, Psi, eig, act_cur);
+                                                                                 n2, Psi, eig, act_cur, thr);
   return cudaGetLastError();
 }
 template cudaError_t group_eigen<double>(const CLevel&, const CLevel&, const double*, const double*, const uint8_t*,
-                                         double*, double*, uint8_t*, int*, cudaStream_t);
+                                         double*, double*, uint8_t*, int*, double, cudaStream_t);
 template cudaError_t group_eigen<float>(const CLevel&, const CLevel&, const float*, const double*, const uint8_t*,
-                                        double*, double*, uint8_t*, int*, cudaStream_t);
+                                        double*, double*, uint8_t*, int*, double, cudaStream_t);
 
 // D_G^(t) = Psi_G^T blockdiag_{c in G}(D_c^(t)) Psi_G for every later level t
 __global__ void k_group_corr(CLevel prev, CLevel cur, const double* __restrict__ Psi, const double* __restrict__ Dp,

@@ -67,6 +67,7 @@ struct thermo_ctx {
   thermo_options opt;
   Geom g;
   int L1 = 4;
+  double h[3] = {1.0, 1.0, 1.0};  // element edges
   long long nnode = 0, nelem = 0;
   std::vector<void*> allocs;
   bool dry = false;          // allocation plan only: count bytes, allocate nothing
@@ -239,6 +240,9 @@ static thermo_status build_context(thermo_ctx* ctx, const int grid[3], const dou
   if (opt.nvec[0] < 1 || opt.nvec[0] > 6) return fail(ctx, THERMO_EINVAL, "nvec[0] must be in 1..6");
   if (opt.density_fp32 != 0 && opt.density_fp32 != 1) return fail(ctx, THERMO_EINVAL, "density_fp32 must be 0 or 1");
   if (opt.fine_engine != 0 && opt.fine_engine != 1) return fail(ctx, THERMO_EINVAL, "fine_engine must be 0 or 1");
+  if (!(opt.eig_threshold >= 0.0) || !std::isfinite(opt.eig_threshold))
+    return fail(ctx, THERMO_EINVAL, "eig_threshold must be finite and >= 0");
+  for (int k = 0; k < 3; ++k) ctx->h[k] = h[k];
   Geom& g = ctx->g;
   memset(&g, 0, sizeof(g));
   g.Nx = grid[0];
@@ -675,7 +679,14 @@ extern "C" thermo_status thermo_setup_precond(thermo_ctx* ctx) {
   Lev& l1 = ctx->lev[1];
   // lean: FP64 Phi shares the CG vectors' slab; clear it (padding nodes included)
   if (ctx->lean) CK(cudaMemsetAsync(ctx->phi64, 0, g.nsize * L1 * sizeof(double), st));
-  CK(level1_eigen(g, ctx->bits, ctx->k64, L1, ctx->phi64, l1.eig, l1.act, ctx->status_dev, st));
+  // adaptive basis threshold of each level: tau / H_l^2, H_l the cell edge (b max(h), times the group sizes)
+  auto thr_of = [&](int l) -> double {
+    if (!(ctx->opt.eig_threshold > 0.0)) return 0.0;
+    double H = ctx->opt.block * std::max(ctx->h[0], std::max(ctx->h[1], ctx->h[2]));
+    for (int k = 2; k <= l; ++k) H *= ctx->lev[k].cl.g;
+    return ctx->opt.eig_threshold / (H * H);
+  };
+  CK(level1_eigen(g, ctx->bits, ctx->k64, L1, ctx->phi64, l1.eig, l1.act, ctx->status_dev, thr_of(1), st));
   CK(level1_rowsum_corr(g, ctx->bits, ctx->k64, L1, ctx->phi64, l1.ntc, ctx->gcum_dev, l1.Dc, st));
   if (ctx->lean) {
     // FP32 hierarchy: every level but the coarsest is rounded once where it is
@@ -693,7 +704,8 @@ extern "C" thermo_status thermo_setup_precond(thermo_ctx* ctx) {
     for (int l = 2; l <= top; ++l) {
       Lev& pv = ctx->lev[l - 1];
       Lev& cu = ctx->lev[l];
-      CK(group_eigen<float>(pv.cl, cu.cl, pv.T32, pv.Dc, pv.act, cu.Psi64, cu.eig, cu.act, ctx->status_dev, st));
+      CK(group_eigen<float>(pv.cl, cu.cl, pv.T32, pv.Dc, pv.act, cu.Psi64, cu.eig, cu.act, ctx->status_dev, thr_of(l),
+                            st));
       if (cu.ntc > 0) CK(group_project_corr(pv.cl, cu.cl, cu.Psi64, pv.Dc, cu.Dc, cu.ntc, st));
       if (l == top) {
         CK((group_rap<float, double>(pv.cl, cu.cl, cu.Psi64, pv.T32, cu.T64, st)));
@@ -716,7 +728,8 @@ extern "C" thermo_status thermo_setup_precond(thermo_ctx* ctx) {
     for (int l = 2; l <= ctx->nlev; ++l) {
       Lev& pv = ctx->lev[l - 1];
       Lev& cu = ctx->lev[l];
-      CK(group_eigen<double>(pv.cl, cu.cl, pv.T64, pv.Dc, pv.act, cu.Psi64, cu.eig, cu.act, ctx->status_dev, st));
+      CK(group_eigen<double>(pv.cl, cu.cl, pv.T64, pv.Dc, pv.act, cu.Psi64, cu.eig, cu.act, ctx->status_dev,
+                             thr_of(l), st));
       if (cu.ntc > 0) CK(group_project_corr(pv.cl, cu.cl, cu.Psi64, pv.Dc, cu.Dc, cu.ntc, st));
       CK((group_rap<double, double>(pv.cl, cu.cl, cu.Psi64, pv.T64, cu.T64, st)));
       CK(fix_inactive<double>(cu.cl, cu.act, cu.T64, st));

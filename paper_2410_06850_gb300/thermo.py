@@ -44,7 +44,8 @@ class thermo_options(C.Structure):
                 ("smoother", C.c_int), ("cheb_degree", C.c_int), ("cheb_ratio", C.c_double),
                 ("power_iters", C.c_int), ("outer_apply", C.c_int),
                 ("nu_growth", C.c_int), ("w_from", C.c_int), ("restart_decades", C.c_double),
-                ("density_fp32", C.c_int), ("fine_engine", C.c_int), ("lean", C.c_int)]
+                ("density_fp32", C.c_int), ("fine_engine", C.c_int), ("lean", C.c_int),
+                ("eig_threshold", C.c_double)]
 
 
 class thermo_solve_info(C.Structure):

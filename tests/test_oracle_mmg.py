@@ -414,3 +414,75 @@ def test_given_bases_reproduce_the_computed_hierarchy():
     r[P["mask"]] = 0.0
     assert np.array_equal(H(r), G(r))
     assert np.array_equal(H.coarse_guess(P["b"]), G.coarse_guess(P["b"]))
+
+
+def _inclusions_problem(kmin=1e-6):
+    """8^3 grid, blocks of 4^3: three single-element solid inclusions (x = 1)
+    that share no node, inside block 0, in void (x = 0) elsewhere; the
+    Dirichlet patch node lies in another block."""
+    N = 8
+    x = np.zeros((N, N, N))
+    for (ex, ey, ez) in [(0, 0, 0), (2, 0, 0), (0, 2, 2)]:
+        x[ez, ey, ex] = 1.0
+    grid = (N, N, N)
+    return fem.build_problem(grid, (1.0 / N,) * 3, x.ravel(), 3.0, kmin, 1.0, W.dirichlet_patch_mask(grid),
+                             W.uniform_source(grid))
+
+
+def test_adaptive_count_equals_high_conductivity_components():
+    """Adaptive local bases (eig_threshold tau): in a high-contrast block the
+    kappa-weighted Neumann problem has one eigenvalue near zero per
+    high-conductivity component (in the kappa-mass norm the constant is the sum
+    of their indicators: void-supported functions carry almost no mass), the
+    rest above about 1 / h^2.  So tau = 1 (a threshold 1 / H^2) keeps exactly
+    one vector per inclusion in block 0 and one (the constant) in the void
+    blocks -- fixed by the spectrum, checked against numpy's eigenvalues of
+    each block's dense problem."""
+    P = _inclusions_problem()
+    o = mmg.MMGOptions(block=4, nvec=(6,), group=(), eig_threshold=1.0)
+    P1, act, eigs, blk, shape = mmg.level1_basis(P, o)
+    counts = act.reshape(-1, 6).sum(axis=1)
+    assert counts[0] == 3, counts
+    assert np.all(counts[1:] == 1), counts
+    H = 4 * (1.0 / 8)
+    # the spectrum behind the count: three tiny eigenvalues in block 0, then a gap
+    w0 = eigs[0]
+    assert np.all(w0[:3] * H ** 2 < 1e-3) and len(w0) == 3
+    full = mmg.level1_basis(P, mmg.MMGOptions(block=4, nvec=(6,), group=()))[2][0]
+    assert full[3] * H ** 2 > 1.0, full
+
+
+def test_adaptive_with_a_huge_threshold_is_the_fixed_hierarchy():
+    """tau above every local eigenvalue keeps nvec vectors everywhere: the same
+    preconditioner as the fixed counts (bases, operators, cycle)."""
+    pr = W.problem("chan32")
+    P = fem.build_problem(pr["grid"], pr["h"], pr["x"], pr["p"], pr["kmin"], pr["kmax"], pr["mask"],
+                          pr["source"])
+    o0 = mmg.default_options(32)
+    o1 = mmg.default_options(32)
+    o1.eig_threshold = 1e300
+    H0, H1 = mmg.MMG(P, o0), mmg.MMG(P, o1)
+    for a, b in zip(H0.levels, H1.levels):
+        assert np.array_equal(a.active, b.active)
+        assert (a.A != b.A).nnz == 0
+    r = np.random.default_rng(7).standard_normal(P["A"].shape[0])
+    r[P["mask"]] = 0.0
+    assert np.array_equal(H0(r), H1(r))
+
+
+def test_adaptive_hierarchy_preconditions_cg():
+    """A moderate threshold gives a smaller coarse space that still makes
+    MMG-PCG reproduce the direct solve."""
+    pr = W.problem("chan32")
+    P = fem.build_problem(pr["grid"], pr["h"], pr["x"], pr["p"], pr["kmin"], pr["kmax"], pr["mask"],
+                          pr["source"])
+    o = mmg.default_options(32)
+    o.eig_threshold = 2.0
+    H = mmg.MMG(P, o)
+    kept = [int(l.active.sum()) for l in H.levels]
+    full = [l.active.size for l in H.levels]
+    assert kept[0] < full[0]
+    free = ~P["mask"]
+    u, info = krylov.pcg(P["A"], P["b"], precond=H, u0=H.coarse_guess(P["b"]), tol=1e-10, free=free)
+    ud = spla.spsolve(P["A"].tocsc(), P["b"])
+    assert info["converged"] and np.linalg.norm(u - ud) <= 1e-8 * np.linalg.norm(ud), info
