@@ -6,6 +6,7 @@
 #include "common.cuh"
 #include "kernels.h"
 #include "splitmix.h"
+#include "fconv.h"
 
 namespace thermo {
 
@@ -54,10 +55,17 @@ static Rows rows_of(const Geom& g) {
   return r;
 }
 __device__ __forceinline__ long long item_index(const Geom& g, long long it, long long ppr) {
+  if (it < (1LL << 32)) {  // 32-bit divisions (every grid this library accepts in practice)
+    const unsigned u = (unsigned)it, q = (unsigned)ppr;
+    const unsigned row = u / q, pr = u - row * q;
+    const unsigned z = row / (unsigned)g.ny, y = row - z * (unsigned)g.ny;
+    return g.base + ((long long)(z + 1) * g.RYn + (y + 1)) * g.P + 2 * (long long)pr;
+  }
   const long long row = it / ppr, pr = it - row * ppr;
   const long long z = row / g.ny, y = row - z * g.ny;
   return g.base + ((z + 1) * g.RYn + (y + 1)) * g.P + 2 * pr;
 }
+
 static int vec_blocks(long long items) {
   long long b = (items + VNT - 1) / VNT;
   if (b > VEC_BLOCKS_MAX) b = VEC_BLOCKS_MAX;
@@ -74,7 +82,7 @@ __device__ __forceinline__ double2 ld2<double>(const double* p) {
 template <>
 __device__ __forceinline__ double2 ld2<float>(const float* p) {
   float2 f = *reinterpret_cast<const float2*>(p);
-  return make_double2(f.x, f.y);
+  return make_double2(f2d_int(f.x), f2d_int(f.y));
 }
 template <>
 __device__ __forceinline__ double2 ld2<bf16>(const bf16* p) {
@@ -89,7 +97,7 @@ __device__ __forceinline__ void st2<double>(double* p, double2 v) {
 }
 template <>
 __device__ __forceinline__ void st2<float>(float* p, double2 v) {
-  *reinterpret_cast<float2*>(p) = make_float2((float)v.x, (float)v.y);
+  *reinterpret_cast<float2*>(p) = make_float2(d2f_int(v.x), d2f_int(v.y));
 }
 template <>
 __device__ __forceinline__ void st2<bf16>(bf16* p, double2 v) {
@@ -375,10 +383,12 @@ __global__ void __launch_bounds__(VNT) k_cg_update(Geom g, Rows R, double* __res
     rr.y -= alpha * qq.y;
     st2<double>(u + i, uu);
     st2<double>(r + i, rr);
-    v[0] += rr.x * rr.x + rr.y * rr.y;
+    v[0] = fma(rr.x, rr.x, v[0]);
+    v[0] = fma(rr.y, rr.y, v[0]);
     if (z) {
       double2 zz = ld2<Tz>(z + i);
-      v[1] += rr.x * zz.x + rr.y * zz.y;
+      v[1] = fma(rr.x, zz.x, v[1]);
+      v[1] = fma(rr.y, zz.y, v[1]);
     }
     if (rlp) st2<Tr>(rlp + i, rr);
   }
@@ -423,10 +433,12 @@ __global__ void __launch_bounds__(VNT) k_beta(Geom g, Rows R, const double* __re
   for (long long it = blockIdx.x * (long long)VNT + threadIdx.x; it < R.items; it += (long long)gridDim.x * VNT) {
     const long long i = item_index(g, it, R.ppr);
     double2 rr = ld2<double>(r + i), zz = ld2<Tz>(z + i);
-    v[0] += rr.x * zz.x + rr.y * zz.y;
+    v[0] = fma(rr.x, zz.x, v[0]);
+    v[0] = fma(rr.y, zz.y, v[0]);
     if (flexible == 1) {
       const double2 qq = ld2<double>(q + i);
-      v[1] += zz.x * qq.x + zz.y * qq.y;
+      v[1] = fma(zz.x, qq.x, v[1]);
+      v[1] = fma(zz.y, qq.y, v[1]);
     }
   }
   if (reduce_k<2>(v, red, res) && threadIdx.x == 0) {
