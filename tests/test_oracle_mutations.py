@@ -10,13 +10,16 @@ import scipy.sparse as sp
 
 import test_oracle_fem as F
 import test_oracle_mmg as G
+import test_oracle_resample as R
 import test_oracle_topopt as T
 from oracle import fem, mmg, topopt
 
 _K1 = np.array([[1.0, -1.0], [-1.0, 1.0]])
 _M1 = np.array([[1.0 / 3.0, 1.0 / 6.0], [1.0 / 6.0, 1.0 / 3.0]])
 _orig = {"element_matrix": fem.element_matrix, "simp_kappa": fem.simp_kappa, "load_vector": fem.load_vector,
-         "sensitivity": fem.sensitivity, "filter_matrix": topopt.filter_matrix}
+         "sensitivity": fem.sensitivity, "filter_matrix": topopt.filter_matrix,
+         "sensitivity_at": fem.sensitivity_at, "load_rows": fem.load_rows,
+         "cells": topopt._axis_weights_cells, "kept_count": mmg.kept_count}
 
 
 def k_dropped_term(h):
@@ -80,6 +83,31 @@ def l1_without_abs(A, shape, L):
     return out
 
 
+def cell_weights_swapped(N, r):
+    i0, i1, t = _orig["cells"](N, r)
+    return i0, i1, np.where(i0 == i1, t, 1.0 - t)  # the weight of the nearer centre on the farther one
+
+
+def node_weights_no_closing_node(N, r):
+    i = np.arange(N * r + 1)
+    i0 = np.minimum(i // r, N - 1)
+    return i0, i0 + 1, (i % r) / r  # the last node (i = rN) read as the start of cell N-1
+
+
+def kept_one_more(w, L, thr):
+    k = _orig["kept_count"](w, L, thr)
+    return min(k + 1, min(L, len(w))) if thr > 0 else k
+
+
+def sensitivity_at_wrong_power(grid, h, x_e, p, kmin, kmax, u, elems):
+    x = np.asarray(x_e, float)
+    return _orig["sensitivity_at"](grid, h, x, p, kmin, kmax, u, elems) * x  # x^p in place of x^(p-1)
+
+
+def load_rows_without_eighth(grid, h, source, rows):
+    return 8.0 * _orig["load_rows"](grid, h, source, rows)
+
+
 CASES = {
     "element matrix drops a term": (fem, "element_matrix", k_dropped_term,
                                     [lambda: F.test_element_matrix_matches_gauss_quadrature((0.3, 0.5, 0.7)),
@@ -101,6 +129,21 @@ CASES = {
                                     T.test_filter_rows_sum_to_one_and_transpose]),
     "l1 smoother without |a_ij|": (mmg, "l1_block_inverses", l1_without_abs,
                                    [G.test_l1_block_jacobi_is_convergent_without_damping]),
+    "resample: cell weights swapped": (topopt, "_axis_weights_cells", cell_weights_swapped,
+                                       [lambda: R.test_cell_trilinear_pointwise((3, 2, 4), (6, 4, 8)),
+                                        R.test_cell_trilinear_reproduces_linear_fields_inside]),
+    "resample: closing node misplaced": (topopt, "_axis_weights_nodes", node_weights_no_closing_node,
+                                         [lambda: R.test_nodal_embedding_pointwise((3, 2, 4), (6, 4, 8)),
+                                          lambda: R.test_nodal_embedding_keeps_integral_and_energy((3, 2, 4),
+                                                                                                   (6, 4, 8))]),
+    "adaptive count one too many": (mmg, "kept_count", kept_one_more,
+                                    [G.test_adaptive_count_equals_high_conductivity_components]),
+    "listed-element sensitivity power p": (fem, "sensitivity_at", sensitivity_at_wrong_power,
+                                           [lambda: F.test_sampled_load_and_sensitivity_equal_the_full_ones(
+                                               (6, 4, 5), (0.3, 0.5, 0.7))]),
+    "listed-node load without 1/8": (fem, "load_rows", load_rows_without_eighth,
+                                     [lambda: F.test_sampled_load_and_sensitivity_equal_the_full_ones(
+                                         (6, 4, 5), (0.3, 0.5, 0.7))]),
 }
 
 
