@@ -160,7 +160,9 @@ typedef struct {
 } thermo_solve_info;
 
 /* Fill *opt with the defaults for an Nx x Ny x Nz grid: b = 4, L_1 = 4, then
- * groups of 2^3 cells down to a 4^3-cell coarsest level with L = 17 (the
+ * groups of 2^3 cells down to a coarsest level of 4^3 cells (8^3 cells when
+ * the smallest axis has more than 32 level-1 cells, i.e. grids above 128 per
+ * axis: an exact coarse-coarse solve of 8,704 unknowns) with L = 17 (the
  * second level keeps 8 vectors when there are more than two coarse levels),
  * Chebyshev fine smoother of degree 5 on [lmax/30, 1.1 lmax] (15 power
  * iterations), nu_fine = 2 / omega = 2/3 for the Jacobi alternative,

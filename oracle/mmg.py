@@ -76,13 +76,15 @@ class MMGOptions:
 
 def default_options(N: int, smoother: str = "chebyshev") -> MMGOptions:
     """Hierarchy used for an N^3 grid: b = 4, L_1 = 4, then groups of 2^3
-    cells down to a 4^3-cell coarsest level with L = 17 (1,088 unknowns);
-    the second level keeps L = 8 when the hierarchy has more than three grids
-    and L = 17 from the third level on."""
+    cells down to a coarsest level of 4^3 cells (8^3 cells when there are more
+    than 32^3 blocks) with L = 17 (1,088 or 8,704 unknowns); the second level
+    keeps L = 8 when the hierarchy has more than three grids and L = 17 from
+    the third level on."""
     nb = N // 4
     levels = []
     m = nb
-    while m > 4:
+    stop = 8 if nb > 32 else 4
+    while m > stop:
         m //= 2
         levels.append(m)
     if not levels:

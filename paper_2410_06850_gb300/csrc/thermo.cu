@@ -179,7 +179,11 @@ extern "C" thermo_status thermo_default_options(const int grid[3], thermo_option
   for (int k = 1; k < 3; ++k) m = grid[k] / 4 < m ? grid[k] / 4 : m;
   int lv = 1;
   std::vector<int> groups;
-  while (m > 4 && m % 2 == 0 && lv < THERMO_MAX_LEVELS) {
+  // coarsest level: 4^3 cells (1,088 unknowns) up to 32^3 level-1 cells; above
+  // that 8^3 cells (8,704 unknowns), the exact coarse-coarse solve that keeps the
+  // iteration count flat in the contrast
+  const int stop = m > 32 ? 8 : 4;
+  while (m > stop && m % 2 == 0 && lv < THERMO_MAX_LEVELS) {
     m /= 2;
     ++lv;
   }

@@ -61,10 +61,14 @@ def test_struct_layouts_match_c(tmp_path):
 
 def test_default_options_host_only(L):
     from paper_2410_06850_gb300 import thermo
-    o = thermo.default_options((256, 256, 256))
-    assert o.levels == 5 and o.block == 4
-    assert list(o.nvec)[:5] == [4, 8, 17, 17, 17]
-    assert list(o.group)[1:5] == [2, 2, 2, 2]
+    o = thermo.default_options((256, 256, 256))  # coarsest 8^3 cells x 17 = 8,704 unknowns
+    assert o.levels == 4 and o.block == 4
+    assert list(o.nvec)[:4] == [4, 8, 17, 17]
+    assert list(o.group)[1:4] == [2, 2, 2]
+    o = thermo.default_options((128, 128, 128))  # coarsest 4^3 cells x 17 = 1,088 unknowns
+    assert o.levels == 4 and list(o.nvec)[:4] == [4, 8, 17, 17]
+    o = thermo.default_options((1024, 1024, 1024))
+    assert o.levels == 6 and list(o.nvec)[:6] == [4, 8, 17, 17, 17, 17]
     o = thermo.default_options((32, 32, 32))
     assert o.levels == 2 and list(o.nvec)[:2] == [4, 17]
     with pytest.raises(thermo.ThermoError):
