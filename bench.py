@@ -11,7 +11,7 @@ CG), and the adjoint sensitivity.  `value` is the mean solve time in seconds
 (the headline metric); set-up, iterations, the FP64 form and the BF16
 smoother variant, per-kernel timings and the roofline of the dominant kernel
 are reported beside it.  Inputs are resident in HBM; the working set
-(~7 GB per context) is far larger than L2, so no flush is needed.
+(~8 GB per context) is far larger than L2, so no flush is needed.
 
 --impl reference times the FP64 CPU oracle (test infrastructure) on a
 bounded sample of the same workload family and scales it to the metric.
@@ -570,8 +570,9 @@ def main():
     ap.add_argument("--workload", default=WORKLOAD)
     ap.add_argument("--tol", type=float, default=1e-8)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--ref-iters", type=int, default=86,
-                    help="iterations of the FP64 solve at 256^3 used to scale the oracle sample")
+    ap.add_argument("--ref-iters", type=int, default=66,
+                    help="iterations of the FP64 solve at 256^3 used to scale the oracle sample (the FP64 form's "
+                         "measured count with the default hierarchy)")
     ap.add_argument("--profile-kernel", type=int, default=None,
                     help="only build the workload and launch thermo_bench_kernel(K) three times (for ncu)")
     ap.add_argument("--profile-solve", action="store_true",
