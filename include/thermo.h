@@ -121,7 +121,8 @@ typedef struct {
                                        dropped by this many decades (iterative refinement
                                        around the low-precision cycle); 0: never */
   int density_fp32;                 /* 0: thermo_set_density's x is double[M]; 1: float[M]
-                                       (widened to FP64 on the device; default 0) */
+                                       (stored as given, widened where it is used;
+                                       default 0) */
   int fine_engine;                  /* FP32 fine sweeps and applies on cubic elements:
                                        0 (default) the separable engine (box sums of the
                                        Q1 operator, one x column per warp, rows in
@@ -202,9 +203,11 @@ thermo_status thermo_plan_bytes(const int grid[3], const thermo_options *opt,
                                 int has_dirichlet_value, long long *bytes);
 
 /* Set the design (Sec. 2.1 Eq. (1)): x device double[M] (float[M] when
- * opt.density_fp32 = 1) in [0,1] (not checked), p >= 1, 0 < kmin <= kmax.
- * kappa is evaluated once per element here and kept in FP64/FP32/BF16
- * copies.  Marks the preconditioner stale. */
+ * opt.density_fp32 = 1, kept in FP32 as given) in [0,1] (not checked), p >= 1,
+ * 0 < kmin <= kmax.  The context copies x (the caller's array may be freed).
+ * kappa is evaluated once per element here and kept in FP64, FP32 plus the
+ * float-float low part, and BF16 for the MIXED_BF16S form.  Marks the
+ * preconditioner stale. */
 thermo_status thermo_set_density(thermo_ctx *ctx, const void *x, double p,
                                  double kmin, double kmax);
 
