@@ -12,14 +12,16 @@ import test_oracle_fem as F
 import test_oracle_mmg as G
 import test_oracle_resample as R
 import test_oracle_topopt as T
-from oracle import fem, mmg, topopt
+import test_oracle_tpfa as TP
+from oracle import fem, mmg, topopt, tpfa
 
 _K1 = np.array([[1.0, -1.0], [-1.0, 1.0]])
 _M1 = np.array([[1.0 / 3.0, 1.0 / 6.0], [1.0 / 6.0, 1.0 / 3.0]])
 _orig = {"element_matrix": fem.element_matrix, "simp_kappa": fem.simp_kappa, "load_vector": fem.load_vector,
          "sensitivity": fem.sensitivity, "filter_matrix": topopt.filter_matrix,
          "sensitivity_at": fem.sensitivity_at, "load_rows": fem.load_rows,
-         "cells": topopt._axis_weights_cells, "kept_count": mmg.kept_count}
+         "cells": topopt._axis_weights_cells, "kept_count": mmg.kept_count,
+         "tpfa_assemble": tpfa.assemble, "tpfa_sensitivity": tpfa.sensitivity}
 
 
 def k_dropped_term(h):
@@ -108,6 +110,19 @@ def load_rows_without_eighth(grid, h, source, rows):
     return 8.0 * _orig["load_rows"](grid, h, source, rows)
 
 
+def tpfa_full_cell_dirichlet(grid, h, kappa, dfaces):
+    # the Dirichlet face's distance taken as a whole cell instead of half of one
+    A, tauD = _orig["tpfa_assemble"](grid, h, kappa, dfaces)
+    half = {k: 0.5 * v for k, v in tauD.items()}
+    corr = sum(half.values())
+    return (A - sp.diags(corr)).tocsr(), half
+
+
+def tpfa_sensitivity_no_source(P, t, u):
+    Q = dict(P, source_given=True)  # drops the -f0 p x^(p-1) |K| u term
+    return _orig["tpfa_sensitivity"](Q, t, u)
+
+
 CASES = {
     "element matrix drops a term": (fem, "element_matrix", k_dropped_term,
                                     [lambda: F.test_element_matrix_matches_gauss_quadrature((0.3, 0.5, 0.7)),
@@ -144,6 +159,11 @@ CASES = {
     "listed-node load without 1/8": (fem, "load_rows", load_rows_without_eighth,
                                      [lambda: F.test_sampled_load_and_sensitivity_equal_the_full_ones(
                                          (6, 4, 5), (0.3, 0.5, 0.7))]),
+    "TPFA: full-cell Dirichlet distance": (tpfa, "assemble", tpfa_full_cell_dirichlet,
+                                           [lambda: TP.test_series_conduction_is_exact(8)]),
+    "TPFA: sensitivity without the source term": (tpfa, "sensitivity", tpfa_sensitivity_no_source,
+                                                  [lambda: TP.test_adjoint_identity_and_central_differences(
+                                                      "z0_full", 0.0)]),
 }
 
 
@@ -158,3 +178,26 @@ def test_pins_catch_a_planted_mistake(monkeypatch, name):
         except (AssertionError, np.linalg.LinAlgError):
             caught += 1
     assert caught >= 1, f"no pin caught: {name}"
+
+
+def test_tpfa_arithmetic_face_mean_is_caught():
+    """The arithmetic instead of the harmonic face mean (computed here directly,
+    not by patching) breaks the 1-D series-conduction exactness."""
+    grid = (1, 1, 6)
+    kz = np.array([1e-3, 1.0, 1e-2, 1.0, 1e-1, 1.0])
+    dfaces = tpfa.dirichlet_faces(grid, "z0z1_full")
+    P = tpfa.build(grid, (1.0, 1.0, 1 / 6), kz, 1.0, 0.0, 1.0, 0.0, dfaces, TD={(2, 0): 0.0, (2, 1): 1.0})
+    A = P["A"].toarray()
+    h = 1 / 6
+    for k in range(5):  # replace every harmonic face transmissibility by the arithmetic one
+        harm = -A[k, k + 1]
+        arith = 0.5 * (kz[k] + kz[k + 1]) / h
+        A[k, k + 1] = A[k + 1, k] = -arith
+        A[k, k] += arith - harm
+        A[k + 1, k + 1] += arith - harm
+    t_bad = np.linalg.solve(A, P["b"])
+    R = np.cumsum(h / kz) - 0.5 * h / kz
+    exact = R / np.sum(h / kz)
+    assert np.max(np.abs(t_bad - exact)) > 1e-3
+    t_ok = np.linalg.solve(P["A"].toarray(), P["b"])
+    assert np.max(np.abs(t_ok - exact)) < 1e-12
