@@ -396,6 +396,44 @@ thermo_status thermo_resample(const int grid_c[3], const double *in,
                               const int grid_f[3], double *out, int kind,
                               void *stream);
 
+/* The paper's own discretisation (Sec. 2.2 Eqs. (4)-(5)): the cell-centred
+ * two-point flux approximation, one temperature per element in natural cell
+ * order c = i + Nx (j + Ny k), FP64.  An internal face between cells a and b
+ * has the transmissibility kappa_F |F| / h with the harmonic mean
+ * kappa_F = 2 / (1/kappa_a + 1/kappa_b); a face on Gamma_D reaches the
+ * prescribed T_D over half a cell (2 kappa_c |F| / h); other boundary faces
+ * are adiabatic.  dirichlet_faces: device uint8[M], bit 0/1 the -x/+x face of
+ * the cell, 2/3 -y/+y, 4/5 -z/+z (set only on the box boundary).  These are
+ * context-free kernels on caller-owned device arrays, enqueued on `stream`;
+ * EINVAL for NULL arrays, non-positive sizes or p < 1, ECUDA if a launch fails.
+ *
+ *   thermo_tpfa_conductivity  kappa_c = kmin + x_c^p (kmax - kmin)   (Eq. (1))
+ *   thermo_tpfa_apply         y = A t   (t != y)
+ *   thermo_tpfa_rhs           b = f0 (1 - x^p) |K| + tau_D T_D      (Eq. (1) source)
+ *   thermo_tpfa_sensitivity   dc/dx_e = u^T (df/dx_e - dA/dx_e t + db/dx_e) for the
+ *                             mean temperature c = sum(t) / M (Eq. (6)), with t the
+ *                             state (A t = b) and u the adjoint, A u = 1/M (Eq. (7)) */
+thermo_status thermo_tpfa_conductivity(long long M, const double *x, double p,
+                                       double kmin, double kmax, double *kappa,
+                                       void *stream);
+thermo_status thermo_tpfa_apply(const int grid[3], const double h[3],
+                                const double *kappa,
+                                const uint8_t *dirichlet_faces,
+                                const double *t, double *y, void *stream);
+thermo_status thermo_tpfa_rhs(const int grid[3], const double h[3],
+                              const double *x, double p, double f0,
+                              const double *kappa,
+                              const uint8_t *dirichlet_faces, double TD,
+                              double *b, void *stream);
+thermo_status thermo_tpfa_sensitivity(const int grid[3], const double h[3],
+                                      const double *x, double p, double kmin,
+                                      double kmax, double f0,
+                                      const double *kappa,
+                                      const uint8_t *dirichlet_faces,
+                                      double TD, const double *t,
+                                      const double *u, double *dc,
+                                      void *stream);
+
 /* Density filter (textbook SIMP harness, not in the paper):
  * out_e = sum_j w_ej in_j / sum_j w_ej with w_ej = max(0, rmin - |c_e - c_j|)
  * in element units, truncated at the domain boundary; transpose = 1 applies

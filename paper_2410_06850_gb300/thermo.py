@@ -33,7 +33,8 @@ EXPORTED = ["thermo_default_options", "thermo_create", "thermo_set_density", "th
             "thermo_launch_count", "thermo_bench_kernel", "thermo_apply_dot",
             "thermo_kernel_timers", "thermo_kernel_time", "thermo_dot_noalloc", "thermo_residual_history",
             "thermo_set_stage_wait", "thermo_dense_spd_inverse", "thermo_update_density",
-            "thermo_plan_bytes", "thermo_resample"]
+            "thermo_plan_bytes", "thermo_resample", "thermo_tpfa_conductivity", "thermo_tpfa_apply",
+            "thermo_tpfa_rhs", "thermo_tpfa_sensitivity"]
 
 
 class thermo_options(C.Structure):
@@ -105,6 +106,11 @@ def lib():
         L.thermo_kernel_time.argtypes = [vp, i, dp, C.POINTER(C.c_longlong), dp, dp]
         L.thermo_set_stage_wait.argtypes = [vp, C.c_longlong]
         L.thermo_dense_spd_inverse.argtypes = [i, vp, vp, vp, ip, C.c_char_p, i]
+        d_ = C.c_double
+        L.thermo_tpfa_conductivity.argtypes = [C.c_longlong, vp, d_, d_, d_, vp, vp]
+        L.thermo_tpfa_apply.argtypes = [ip, dp, vp, vp, vp, vp, vp]
+        L.thermo_tpfa_rhs.argtypes = [ip, dp, vp, d_, d_, vp, vp, d_, vp, vp]
+        L.thermo_tpfa_sensitivity.argtypes = [ip, dp, vp, d_, d_, d_, d_, vp, vp, d_, vp, vp, vp, vp]
         for n in EXPORTED:
             if n not in ("thermo_last_error", "thermo_destroy", "thermo_launch_count"):
                 getattr(L, n).restype = C.c_int
@@ -388,6 +394,59 @@ def resample(grid_c, v, grid_f, kind):
     if rc != OK:
         raise ThermoError(rc, f"thermo_resample rejected {tuple(grid_c)} -> {tuple(grid_f)} kind {kind}")
     return out
+
+
+class Tpfa:
+    """The paper's cell-centred TPFA operator (thermo_tpfa_*): conductivity,
+    A t, the right-hand side with the source f0 (1 - x^p) and the
+    mean-temperature adjoint sensitivity, on device arrays in natural cell
+    order.  dirichlet_faces: uint8 per cell, bit 2 axis + side."""
+
+    def __init__(self, grid, h, dirichlet_faces):
+        self.grid = tuple(int(v) for v in grid)
+        self.h = tuple(float(v) for v in h)
+        self.M = self.grid[0] * self.grid[1] * self.grid[2]
+        self.dface = _dev(dirichlet_faces, torch.uint8)
+        if self.dface.numel() != self.M:
+            raise ValueError("dirichlet_faces must have one byte per cell")
+        self._g = (C.c_int * 3)(*self.grid)
+        self._h = (C.c_double * 3)(*self.h)
+
+    def _st(self):
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+
+    def _check(self, rc, what):
+        if rc != OK:
+            raise ThermoError(rc, f"{what} rejected its arguments")
+
+    def conductivity(self, x, p, kmin, kmax):
+        x = _dev(x, torch.float64)
+        k = torch.empty_like(x)
+        self._check(lib().thermo_tpfa_conductivity(self.M, _ptr(x), float(p), float(kmin), float(kmax), _ptr(k),
+                                                   self._st()), "thermo_tpfa_conductivity")
+        return k
+
+    def apply(self, kappa, t):
+        y = torch.empty(self.M, dtype=torch.float64, device="cuda")
+        self._check(lib().thermo_tpfa_apply(self._g, self._h, _ptr(_dev(kappa, torch.float64)), _ptr(self.dface),
+                                            _ptr(_dev(t, torch.float64)), _ptr(y), self._st()), "thermo_tpfa_apply")
+        return y
+
+    def rhs(self, x, p, f0, kappa, TD):
+        b = torch.empty(self.M, dtype=torch.float64, device="cuda")
+        self._check(lib().thermo_tpfa_rhs(self._g, self._h, _ptr(_dev(x, torch.float64)), float(p), float(f0),
+                                          _ptr(_dev(kappa, torch.float64)), _ptr(self.dface), float(TD), _ptr(b),
+                                          self._st()), "thermo_tpfa_rhs")
+        return b
+
+    def sensitivity(self, x, p, kmin, kmax, f0, kappa, TD, t, u):
+        dc = torch.empty(self.M, dtype=torch.float64, device="cuda")
+        self._check(lib().thermo_tpfa_sensitivity(self._g, self._h, _ptr(_dev(x, torch.float64)), float(p),
+                                                  float(kmin), float(kmax), float(f0),
+                                                  _ptr(_dev(kappa, torch.float64)), _ptr(self.dface), float(TD),
+                                                  _ptr(_dev(t, torch.float64)), _ptr(_dev(u, torch.float64)),
+                                                  _ptr(dc), self._st()), "thermo_tpfa_sensitivity")
+        return dc
 
 
 def launch_count() -> int:

@@ -86,3 +86,25 @@ def test_host_argument_checks_need_no_gpu(L):
     L.thermo_destroy(None)
     assert L.thermo_set_density(None, None, 3.0, 1e-3, 1.0) == thermo.EINVAL
     assert L.thermo_solve(None, None, None, 1e-8, None) == thermo.EINVAL
+
+
+def test_tpfa_and_resample_argument_checks_need_no_gpu(L):
+    """The context-free entry points reject bad arguments before any launch."""
+    from paper_2410_06850_gb300 import thermo
+    g = (C.c_int * 3)(4, 4, 4)
+    bad = (C.c_int * 3)(4, 0, 4)
+    h = (C.c_double * 3)(0.25, 0.25, 0.25)
+    fake = C.c_void_p(256)  # never dereferenced: every call below fails its checks first
+    assert L.thermo_tpfa_apply(g, h, None, fake, fake, fake, None) == thermo.EINVAL
+    assert L.thermo_tpfa_apply(bad, h, fake, fake, fake, C.c_void_p(512), None) == thermo.EINVAL
+    assert L.thermo_tpfa_apply(g, h, fake, fake, fake, fake, None) == thermo.EINVAL  # t == y
+    assert L.thermo_tpfa_rhs(g, h, fake, 0.5, 1.0, fake, fake, 0.0, fake, None) == thermo.EINVAL  # p < 1
+    assert L.thermo_tpfa_sensitivity(g, h, fake, 3.0, 1e-3, 1.0, 1.0, fake, fake, 0.0, None, fake, fake,
+                                     None) == thermo.EINVAL
+    assert L.thermo_tpfa_conductivity(0, fake, 3.0, 1e-3, 1.0, fake, None) == thermo.EINVAL
+    assert L.thermo_tpfa_conductivity(8, fake, 3.0, 0.0, 1.0, fake, None) == thermo.EINVAL  # kmin = 0
+    gf = (C.c_int * 3)(6, 8, 8)
+    assert L.thermo_resample(g, fake, gf, C.c_void_p(512), 0, None) == thermo.EINVAL  # 6 / 4 not an integer
+    gf2 = (C.c_int * 3)(8, 8, 8)
+    assert L.thermo_resample(g, fake, gf2, C.c_void_p(512), 3, None) == thermo.EINVAL  # kind
+    assert L.thermo_resample(g, fake, gf2, fake, 0, None) == thermo.EINVAL  # in == out
