@@ -184,6 +184,17 @@ def _mgs(V, W=None):
     return V
 
 
+def _blocks(prob, opts: MMGOptions):
+    """Level-1 cells of the unknowns: the Q1 node blocks (R4), or the partition a
+    problem supplies as prob["blocks"] = (block id per unknown, -1 for none;
+    block grid shape) -- e.g. blocks of b^3 cells for the cell-centred TPFA
+    unknowns (oracle.tpfa.mmg_problem).  Everything after the partition is
+    algebraic: the Neumann form of each block, the mass, the groups."""
+    if "blocks" in prob:
+        return prob["blocks"]
+    return node_blocks(prob["grid"], opts.block, prob["mask"])
+
+
 def cell_size(prob, opts: MMGOptions, level: int) -> float:
     """Edge H_l of a level-l cell: b max(h) on level 1, times g_2 ... g_l below."""
     H = opts.block * max(prob["h"])
@@ -215,7 +226,7 @@ def level1_basis(prob, opts: MMGOptions):
     """Eq. (8) on every block: returns (P1 (n0 x n1), active, eigvals, blk)."""
     A = prob["A"].tocsr()
     mass = prob["mass"]
-    blk, shape = node_blocks(prob["grid"], opts.block, prob["mask"])
+    blk, shape = _blocks(prob, opts)
     nblk = shape[0] * shape[1] * shape[2]
     L = opts.nvec[0]
     order = np.argsort(blk, kind="stable")
@@ -370,7 +381,7 @@ class MMG:
         if bases is None:
             P1, act, eig, fine_cell, shape = level1_basis(prob, o)
         else:
-            _, shape = node_blocks(prob["grid"], o.block, prob["mask"])
+            _, shape = _blocks(prob, o)
             P1, act, eig, shape = _given_level(bases[0], shape, o.nvec[0])
             fine_cell = None
         if o.smoother == "chebyshev":

@@ -166,3 +166,24 @@ def sensitivity(P, t, u) -> np.ndarray:
     vol = float(h[0]) * float(h[1]) * float(h[2])
     src = 0.0 if P["source_given"] else P["f0"] * p * xp1 * vol * u
     return dk * g - src
+
+
+def mmg_problem(P, b: int = 4) -> dict:
+    """The TPFA system as a problem for oracle.mmg.MMG (the algebraic
+    construction of Sec. 3 on the paper's own discretisation): unknowns are the
+    cells, level-1 blocks are b^3 cells (the block grid must divide), the mass of
+    Eq. (8) is the kappa-weighted cell volume kappa_c |K| (the cell-centred
+    counterpart of the lumped nodal mass), no unknown is eliminated (Dirichlet
+    data enter through the faces), and the internal Neumann form of a block is
+    its diagonal block of A minus the row sums -- exactly the flux over the
+    block's internal faces, as Eq. (8) states for TPFA."""
+    Nx, Ny, Nz = P["grid"]
+    if Nx % b or Ny % b or Nz % b:
+        raise ValueError("the grid must be a multiple of the block size")
+    c = np.arange(Nx * Ny * Nz)
+    i, j, k = c % Nx, (c // Nx) % Ny, c // (Nx * Ny)
+    sx, sy, sz = Nx // b, Ny // b, Nz // b
+    blk = (i // b) + sx * ((j // b) + sy * (k // b))
+    vol = P["h"][0] * P["h"][1] * P["h"][2]
+    return dict(grid=P["grid"], h=P["h"], A=P["A"], b=P["b"], mask=np.zeros(c.size, dtype=bool),
+                mass=P["kappa"] * vol, blocks=(blk, (sx, sy, sz)))
