@@ -76,7 +76,7 @@ def pcg(A, b, precond=None, u0=None, tol=1e-8, maxit=10000, flexible=False,
         rz = rz_new
         p = z + beta * p
     rt = b - A @ u
-    return u, dict(iters=it, converged=converged,
+    return u, dict(iters=it, converged=converged, restarts=restarts,
                    relres_recursive=hist[-1],
                    relres_true=float(np.linalg.norm(rt)) / bnorm, history=hist)
 

@@ -71,3 +71,27 @@ def test_energy_norm_error_is_monotone():
         e = u - us
         errs.append(float(e @ A @ e))
     assert all(errs[i + 1] <= errs[i] * (1 + 1e-10) for i in range(len(errs) - 1))
+
+
+def test_restart_branch_replaces_the_recursive_residual():
+    """Below the attainable accuracy the recursive residual keeps falling while
+    the true one stalls: the solver replaces the residual by the true one and
+    restarts, at most max_restarts times, then reports converged = False with
+    the true relative residual of the returned iterate.  With an attainable
+    tolerance the same system converges without a restart."""
+    import scipy.sparse as sp
+    n = 60
+    rng = np.random.default_rng(3)
+    Q, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    lam = np.repeat(np.logspace(0, 12, 6), n // 6)  # six clusters, condition 1e12
+    A = sp.csr_matrix((Q * lam) @ Q.T)
+    A = 0.5 * (A + A.T)
+    b = rng.standard_normal(n)
+    u, info = krylov.pcg(A, b, tol=1e-12, maxit=2000, max_restarts=3)
+    assert info["relres_recursive"] <= 1e-12  # the recursion met the tolerance ...
+    assert info["restarts"] == 3 and not info["converged"], info["restarts"]
+    true = np.linalg.norm(b - A @ u) / np.linalg.norm(b)
+    assert abs(info["relres_true"] - true) <= 1e-12 * true
+    assert info["relres_true"] > 1e-12  # ... the true residual did not
+    u2, info2 = krylov.pcg(A, b, tol=1e-2, maxit=5000)
+    assert info2["converged"] and info2["restarts"] == 0
