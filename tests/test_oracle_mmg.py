@@ -486,3 +486,12 @@ def test_adaptive_hierarchy_preconditions_cg():
     u, info = krylov.pcg(P["A"], P["b"], precond=H, u0=H.coarse_guess(P["b"]), tol=1e-10, free=free)
     ud = spla.spsolve(P["A"].tocsc(), P["b"])
     assert info["converged"] and np.linalg.norm(u - ud) <= 1e-8 * np.linalg.norm(ud), info
+
+
+def test_sign_convention():
+    """R13: the entry of largest magnitude (lowest index on ties) is positive."""
+    v = np.array([0.1, -0.7, 0.7, 0.2])
+    np.testing.assert_array_equal(mmg._sign_fix(v), -v)  # tie: index 1 wins, it is negative
+    w = np.array([0.1, 0.3, -0.2])
+    np.testing.assert_array_equal(mmg._sign_fix(w), w)
+    np.testing.assert_array_equal(mmg._sign_fix(-w), w)
